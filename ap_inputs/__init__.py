@@ -1,0 +1,262 @@
+"""Seeded synthetic workloads for the adaptive-precision EAM/ACE force evaluation.
+
+This module is shared by the CUDA path, the CPU oracle and the tests.  It only
+builds inputs: lattices, displacements, masks, velocities and the random
+potential parameters.  It contains none of the method's arithmetic (no
+neighbour search, no centro-symmetry, no switching function, no potential).
+
+Units: eV, Angstrom, fs, amu.  Every random draw uses numpy's PCG64 generator
+seeded with ``seed_for(config, k) = 2411030020 + 100*config + k``.
+
+Workloads (all copper-like FCC, a = 3.615 A):
+  * c1  4x4x4 periodic cell, sigma = 0.05 A, spherical void r = 4 A -> 237 atoms.
+  * c2  20x20x20 slab (x/y periodic, z free), hemispherical 0.3 A disorder of
+        radius 15 A under the top surface, 300 K Maxwell-Boltzmann velocities.
+  * c3  8x8x8 periodic cell, sigma = 0.1 A, lambda forced to a seeded mix of
+        0, 1 and U(0,1); plus a batch of 64 cells of 4*n1*n2*n3 atoms.
+  * c5  100x100x100 slab (4,000,000 atoms), bottom 3 (200) layers fixed, a
+        spherical indenter (R = 50 A, k = 10 eV/A^3, 20 m/s) above the top surface.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+SEED_BASE = 2411030020
+A_CU = 3.615            # lattice parameter (A)
+MASS_CU = 63.546        # amu
+KB_EV = 8.617333262e-5  # eV/K
+# 1 eV/(A amu) expressed in A/fs^2, from 1 eV = 1.602176634e-19 J, 1 amu = 1.66053906660e-27 kg
+ACC_EV_A_AMU = 1.602176634e-19 / 1.66053906660e-27 * 1e-20 / 1e-10
+
+
+def seed_for(config: int, k: int = 0) -> int:
+    return SEED_BASE + 100 * config + k
+
+
+def rng_for(config: int, k: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed_for(config, k)))
+
+
+@dataclasses.dataclass
+class Box:
+    lo: np.ndarray          # (3,) float64
+    hi: np.ndarray          # (3,) float64
+    periodic: np.ndarray    # (3,) bool
+
+    @property
+    def length(self) -> np.ndarray:
+        return self.hi - self.lo
+
+
+@dataclasses.dataclass
+class HybridParams:
+    """Switching-function parameters (Table 'model_parameters' of the paper)."""
+    csp_lo: float = 2.5
+    csp_hi: float = 3.0
+    r_lo: float = 4.0
+    r_hi: float = 12.0
+    n_csp_avg: int = 11          # samples in the CSP window
+    n_lam_avg: int = 11          # samples in the lambda window
+    dlam_min: float = 1.0 / 110.0
+    sample_every: int = 10       # lambda update period (MD steps)
+    fcut_mode: int = 0           # 0 = polynomial as printed, 1 = C2-symmetric reading
+
+
+HYB1 = HybridParams()
+HYB2 = HybridParams(r_lo=8.0, r_hi=20.0)
+# Single-evaluation parameter set used for the 237-atom cell (r_hi < L/2).
+SINGLE_EVAL = HybridParams(r_lo=2.0, r_hi=3.5, n_csp_avg=1, n_lam_avg=1, sample_every=1)
+
+
+@dataclasses.dataclass
+class EAMParams:
+    """Analytic EAM: exponential density, square-root embedding, Morse pair."""
+    beta: float
+    alpha: float
+    A: float
+    D: float
+    rp: float
+    r0: float = A_CU / math.sqrt(2.0)
+    rc: float = 5.5
+    h: float = 0.5
+
+    def as_array(self) -> np.ndarray:
+        return np.array([self.beta, self.alpha, self.A, self.D, self.rp, self.r0, self.rc, self.h])
+
+
+EAM_NOMINAL = EAMParams(beta=3.0, alpha=1.6, A=0.42398, D=0.23925, rp=2.81322)
+
+
+@dataclasses.dataclass
+class ACEParams:
+    """Linear single-species ACE: radial mixing W[l][n][k] and coefficients c[v]."""
+    W: np.ndarray            # (5, 8, 8) float64, indexed [l][n][k]
+    c: np.ndarray            # (512,) float64; the first n_basis entries are used
+    rc: float = 7.0
+    n0: float = 10.0         # A-basis normalisation N0
+
+
+@dataclasses.dataclass
+class Indenter:
+    center0: np.ndarray      # (3,) initial centre (A)
+    velocity: np.ndarray     # (3,) A/fs
+    radius: float = 50.0
+    k: float = 10.0          # eV/A^3
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    x: np.ndarray                    # (N,3) float64
+    box: Box
+    mass: np.ndarray                 # (N,) float64
+    fixed: np.ndarray                # (N,) uint8: 1 = fixed atom (lambda = 1, v = 0)
+    v: Optional[np.ndarray] = None   # (N,3) float64, A/fs
+    lam: Optional[np.ndarray] = None # (N,) float64 forced lambda, or None
+    indenter: Optional[Indenter] = None
+    dt: float = 1.0
+    hyb: HybridParams = dataclasses.field(default_factory=HybridParams)
+
+    @property
+    def n(self) -> int:
+        return self.x.shape[0]
+
+
+# ----------------------------------------------------------------------------- lattices
+_FCC_BASIS = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]])
+
+
+def fcc_lattice(nx: int, ny: int, nz: int, a: float = A_CU) -> np.ndarray:
+    """FCC positions, z-layer-major order (k outer, j, i, basis inner)."""
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cells = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(np.float64)
+    pos = (cells[:, None, :] + _FCC_BASIS[None, :, :]).reshape(-1, 3) * a
+    return pos
+
+
+def eam_params(seed_config: int = 0, k: int = 1) -> EAMParams:
+    """Nominal parameters times (1 + 0.02 N(0,1)), seeded."""
+    if seed_config < 0:
+        return dataclasses.replace(EAM_NOMINAL)
+    g = rng_for(seed_config, k)
+    f = 1.0 + 0.02 * g.standard_normal(5)
+    n = EAM_NOMINAL
+    return EAMParams(beta=n.beta * f[0], alpha=n.alpha * f[1], A=n.A * f[2], D=n.D * f[3], rp=n.rp * f[4])
+
+
+def ace_params(seed_config: int = 0, k: int = 2, c_std: float = 0.01) -> ACEParams:
+    """W_l = I + 0.1 N(0,1) for l = 0..4, and c ~ N(0, c_std^2) (512 draws)."""
+    g = rng_for(seed_config, k)
+    W = np.eye(8)[None, :, :] + 0.1 * g.standard_normal((5, 8, 8))
+    c = c_std * g.standard_normal(512)
+    return ACEParams(W=W, c=c)
+
+
+def maxwell_boltzmann(mass: np.ndarray, mobile: np.ndarray, T: float, g: np.random.Generator) -> np.ndarray:
+    """v ~ N(0, kT/m) per component, COM removed, rescaled to T with 3N_mobile - 3 DOF."""
+    n = mass.shape[0]
+    sig = np.sqrt(KB_EV * T * ACC_EV_A_AMU / mass)
+    v = g.standard_normal((n, 3)) * sig[:, None]
+    v[~mobile] = 0.0
+    m = mass[mobile]
+    vcm = (m[:, None] * v[mobile]).sum(0) / m.sum()
+    v[mobile] -= vcm
+    ke = 0.5 * (m[:, None] * v[mobile] ** 2).sum() / ACC_EV_A_AMU
+    dof = 3 * int(mobile.sum()) - 3
+    t_now = 2.0 * ke / (dof * KB_EV)
+    v[mobile] *= math.sqrt(T / t_now)
+    return v
+
+
+def _periodic_box(nx: int, ny: int, nz: int, a: float = A_CU) -> Box:
+    return Box(lo=np.zeros(3), hi=np.array([nx, ny, nz], float) * a, periodic=np.array([True, True, True]))
+
+
+def _slab_box(nx: int, ny: int, nz: int, a: float = A_CU, pad: float = 10.0) -> Box:
+    ztop = (nz - 0.5) * a
+    return Box(lo=np.array([0.0, 0.0, -pad]), hi=np.array([nx * a, ny * a, ztop + pad]),
+               periodic=np.array([True, True, False]))
+
+
+# ----------------------------------------------------------------------------- configs
+def config_c1() -> Workload:
+    """237-atom periodic cell with a 4 A void at a lattice site, sigma = 0.05 A."""
+    g = rng_for(1, 0)
+    x = fcc_lattice(4, 4, 4)
+    box = _periodic_box(4, 4, 4)
+    centre = np.array([2.0, 2.0, 2.0]) * A_CU          # a lattice site
+    keep = np.linalg.norm(x - centre, axis=1) >= 4.0
+    x = x[keep]
+    x = x + 0.05 * g.standard_normal(x.shape)
+    n = x.shape[0]
+    return Workload("c1_fcc4_void", x, box, np.full(n, MASS_CU), np.zeros(n, np.uint8), hyb=SINGLE_EVAL)
+
+
+def config_c2(hyb: HybridParams = HYB1) -> Workload:
+    """32,000-atom slab with a hemispherical 0.3 A disordered region; 300 K velocities."""
+    g = rng_for(2, 0)
+    nx = ny = nz = 20
+    x = fcc_lattice(nx, ny, nz)
+    box = _slab_box(nx, ny, nz)
+    ztop = (nz - 0.5) * A_CU
+    centre = np.array([nx * A_CU / 2, ny * A_CU / 2, ztop])
+    dis = (np.linalg.norm(x - centre, axis=1) < 15.0) & (x[:, 2] <= ztop + 1e-9)
+    x[dis] += 0.3 * g.standard_normal((int(dis.sum()), 3))
+    n = x.shape[0]
+    mass = np.full(n, MASS_CU)
+    v = maxwell_boltzmann(mass, np.ones(n, bool), 300.0, rng_for(2, 1))
+    return Workload("c2_slab20", x, box, mass, np.zeros(n, np.uint8), v=v, hyb=hyb)
+
+
+def config_c3() -> Workload:
+    """2,048-atom periodic cell, sigma = 0.1 A, lambda forced to {0, 1, U(0,1)} thirds."""
+    g = rng_for(3, 0)
+    x = fcc_lattice(8, 8, 8)
+    x = x + 0.1 * g.standard_normal(x.shape)
+    n = x.shape[0]
+    cat = g.integers(0, 3, n)
+    lam = np.where(cat == 0, 0.0, np.where(cat == 1, 1.0, g.uniform(0.0, 1.0, n)))
+    return Workload("c3_fcc8", x, _periodic_box(8, 8, 8), np.full(n, MASS_CU), np.zeros(n, np.uint8),
+                    lam=lam, hyb=SINGLE_EVAL)
+
+
+def config_c3_batch(n_cells: int = 64) -> list:
+    """Independent periodic cells of 4*n1*n2*n3 atoms, n_i in {5..10} (500-4,000 atoms)."""
+    g = rng_for(3, 1)
+    out = []
+    for c in range(n_cells):
+        nn = g.integers(5, 11, 3)
+        x = fcc_lattice(*nn)
+        x = x + 0.1 * g.standard_normal(x.shape)
+        n = x.shape[0]
+        cat = g.integers(0, 3, n)
+        lam = np.where(cat == 0, 0.0, np.where(cat == 1, 1.0, g.uniform(0.0, 1.0, n)))
+        out.append(Workload(f"c3_cell{c}", x, _periodic_box(*nn), np.full(n, MASS_CU),
+                            np.zeros(n, np.uint8), lam=lam, hyb=SINGLE_EVAL))
+    return out
+
+
+def config_c5(ncell: int = 100, hyb: HybridParams = HYB2, T: float = 300.0) -> Workload:
+    """Nanoindentation-shaped slab: ncell^3 FCC cells (4,000,000 atoms at ncell = 100)."""
+    nx = ny = nz = ncell
+    x = fcc_lattice(nx, ny, nz)
+    box = _slab_box(nx, ny, nz)
+    n = x.shape[0]
+    fixed = (x[:, 2] < 1.25 * A_CU).astype(np.uint8)      # bottom three (200) layers
+    mass = np.full(n, MASS_CU)
+    v = maxwell_boltzmann(mass, fixed == 0, T, rng_for(5, 1))
+    ztop = (nz - 0.5) * A_CU
+    R = 50.0
+    ind = Indenter(center0=np.array([nx * A_CU / 2, ny * A_CU / 2, ztop + R]),
+                   velocity=np.array([0.0, 0.0, -2.0e-4]), radius=R, k=10.0)
+    return Workload(f"c5_indent{ncell}", x, box, mass, fixed, v=v, indenter=ind, hyb=hyb)
+
+
+def sample_atoms(n: int, count: int, config: int, k: int = 7) -> np.ndarray:
+    """Seeded sorted sample of atom indices (for sampled parity checks)."""
+    g = rng_for(config, k)
+    return np.sort(g.choice(n, size=min(count, n), replace=False))
