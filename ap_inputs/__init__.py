@@ -240,9 +240,11 @@ def config_c3_batch(n_cells: int = 64) -> list:
     return out
 
 
-def config_c5(ncell: int = 100, hyb: HybridParams = HYB2, T: float = 300.0) -> Workload:
-    """Nanoindentation-shaped slab: ncell^3 FCC cells (4,000,000 atoms at ncell = 100)."""
-    nx = ny = nz = ncell
+def config_c5(ncell: int = 100, hyb: HybridParams = HYB2, T: float = 300.0, nxy: Optional[int] = None) -> Workload:
+    """Nanoindentation-shaped slab: ncell^3 FCC cells (4,000,000 atoms at ncell = 100).
+    nxy < ncell cuts a laterally periodic column of the same depth (nxy x nxy x ncell)."""
+    nx = ny = ncell if nxy is None else nxy
+    nz = ncell
     x = fcc_lattice(nx, ny, nz)
     box = _slab_box(nx, ny, nz)
     n = x.shape[0]

@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark of the adaptive-precision EAM/ACE molecular-dynamics step on GB300.
+
+Workload: the nanoindentation-shaped slab of 100x100x100 FCC cells (4,000,000
+copper-like atoms, x/y periodic, bottom 3 layers fixed, spherical indenter),
+parameter set Hyb2, lambda and the precise-atom queue updated every 10 MD steps,
+mixed precision (FP32 potentials, FP64 integration and energy sums).
+
+One bench step = one lambda period = 10 velocity-Verlet steps through ap_step
+(neighbour rebuild, classification, EAM for all atoms, ACE for the precise queue,
+indenter, integration).  Metric: atom-steps/s = N_atoms x MD steps / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs an independent replica (the path has no exchange
+step on one GPU per system); value = atoms x steps over all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ap_inputs as I  # noqa: E402
+
+MD_PER_STEP = 10
+METRIC = "atom-steps/s adaptive vs full-ACE on 1 GB300 at <=10 meV/A force error"
+# Algorithmic FLOPs of the fused ACE kernel: per neighbour pair within r_c and per
+# precise atom (contractions, basis functions and their gradients; FMA = 2).
+ACE_FLOP_PER_PAIR = 1855
+ACE_FLOP_PER_ATOM = 32000
+# FP32 SIMT peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--ncell", type=int, default=100)
+    p.add_argument("--mode", default="adaptive", choices=["adaptive", "full-ace", "full-eam"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--no-extras", action="store_true", help="skip full-ACE/full-EAM, error and CPU baseline legs")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def hyb_for(mode: str, hyb: I.HybridParams) -> I.HybridParams:
+    import dataclasses
+    if mode == "full-ace":       # every changeable atom detected: lambda = 0
+        return dataclasses.replace(hyb, csp_lo=-2.0, csp_hi=-1.0)
+    if mode == "full-eam":       # no atom detected: lambda = 1
+        return dataclasses.replace(hyb, csp_lo=1e30, csp_hi=2e30)
+    return hyb
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        loaded = [s for s in sm if s > 0.5 * max(mx)] if mx else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else (statistics.median(sm) if sm else None),
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle baseline
+def oracle_sample(hyb: I.HybridParams, reps: int = 1):
+    """Time the oracle on a bounded sample of the workload: a laterally periodic
+    6x6x100-cell column (14,400 atoms) of the same slab, one MD step's force work
+    (classification + hybrid EAM/ACE forces + indenter) per repetition."""
+    import oracle as O
+    w = I.config_c5(100, hyb=hyb, nxy=6)
+    ch = (w.fixed == 0).astype(np.uint8)
+    eam, ace = I.eam_params(0), O.ACE(I.ace_params(0))
+    times = []
+    for _ in range(reps):
+        st = O.LambdaState(w.n, hyb.n_csp_avg, hyb.n_lam_avg)
+        t0 = time.perf_counter()
+        lam, *_ = O.classify(st, w.x, w.box, hyb, changeable=ch)
+        e, f, _, _ = O.hybrid(w.x, w.box, lam, eam, ace)
+        O.indenter(w.x, w.indenter.center0, w.indenter.radius, w.indenter.k)
+        times.append(time.perf_counter() - t0)
+    return w.n, times, O.num_threads()
+
+
+def reference_arm(args, ws, rank):
+    if rank != 0:
+        return
+    hyb = hyb_for(args.mode, I.HYB2)
+    n, times, cores = oracle_sample(hyb, reps=args.warmup + args.steps)
+    timed = times[args.warmup:]
+    v = n * len(timed) / sum(timed)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "atom-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(timed) / len(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "6x6x100-cell column (14,400 atoms) of the 100^3-cell nanoindentation slab, "
+                                   "Hyb2, one MD step of force work per step (FP64 CPU oracle)"},
+            "cpu_baseline": {"value": v, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": "14,400-atom column, classification + hybrid forces + indenter"},
+            "e2e": {"value": v, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_2411_03002_gb300 as ap
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = ap.PREC_MIXED if args.precision == "mixed" else ap.PREC_FP64
+    w = I.config_c5(args.ncell, hyb=I.HYB2)
+    hyb = hyb_for(args.mode, w.hyb)
+    eam, acep = I.eam_params(0), I.ace_params(0)
+
+    def new_ctx(h, p=prec):
+        return ap.Context(ap.make_config(eam, acep, h, precision=p, indenter=w.indenter, lambda_every=MD_PER_STEP,
+                                         dt=w.dt))
+
+    def tensors():
+        return (torch.as_tensor(w.x, device=dev).clone(), torch.as_tensor(w.v, device=dev).clone(),
+                torch.zeros((w.n, 3), dtype=torch.float64, device=dev), torch.as_tensor(w.mass, device=dev),
+                torch.as_tensor(w.fixed, device=dev), torch.empty(w.n, dtype=torch.float64, device=dev))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    ctx = new_ctx(hyb)
+    x, v, f, mass, fixed, lam = tensors()
+    ctx.build_neighbors(x, w.box)
+    stats = ctx.step(x, v, f, mass, fixed, lam, 0)
+    for _ in range(args.warmup):
+        stats = ctx.step(x, v, f, mass, fixed, lam, MD_PER_STEP)
+    barrier()
+    ctx.profile_enable(True)
+    clocks = Clocks(local)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        stats = ctx.step(x, v, f, mass, fixed, lam, MD_PER_STEP)
+    e1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    atom_steps = w.n * MD_PER_STEP * args.steps * ws
+    value = atom_steps / (ms / 1e3)
+    ace_ms, ace_calls = prof["phases"]["ace"]
+    flops = ACE_FLOP_PER_PAIR * prof["ace_pairs"] + ACE_FLOP_PER_ATOM * prof["ace_atoms"]
+    achieved = flops / (ace_ms / 1e3) / 1e12 if ace_ms > 0 else 0.0
+    phase_share = {k: round(m / max(1e-9, sum(p[0] for p in prof["phases"].values())), 4)
+                   for k, (m, c) in prof["phases"].items()}
+
+    # end-to-end through the public call with host buffers (pinned), copies inside the timed region
+    xh, vh, fh = x.cpu().pin_memory(), v.cpu().pin_memory(), f.cpu().pin_memory()
+    lamh = lam.cpu().pin_memory()
+    barrier()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        x.copy_(xh, non_blocking=True)
+        v.copy_(vh, non_blocking=True)
+        f.copy_(fh, non_blocking=True)
+        ctx.step(x, v, f, mass, fixed, lam, MD_PER_STEP)
+        xh.copy_(x, non_blocking=True)
+        vh.copy_(v, non_blocking=True)
+        fh.copy_(f, non_blocking=True)
+        lamh.copy_(lam, non_blocking=True)
+    e3.record(stream)
+    barrier()
+    ms_e2e = e2.elapsed_time(e3)
+    if ws > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    h2d = 3 * w.n * 3 * 8
+    d2h = 3 * w.n * 3 * 8 + w.n * 8
+
+    extras = {}
+    cpu = None
+    if rank == 0 and not args.no_extras:
+        lam0 = ctx.get_lambda_state()["lam0"]
+        detected = torch.nonzero(lam0 < 1.0).flatten()
+        xs, lams = x.clone(), lam.clone()
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+        # force error on detected atoms: adaptive forces vs full ACE, same positions (FP32 path)
+        ev = new_ctx(hyb)
+        ev.build_neighbors(xs, w.box)
+        q = torch.nonzero(lams < 1.0).flatten().to(torch.int32)
+        nq = torch.tensor([q.numel()], dtype=torch.int64, device=dev)
+        _, fh_ = ev.eval_eam(xs, lams)
+        _, fh_ = ev.eval_ace(xs, lams, q, nq, f=fh_)
+        z = torch.zeros_like(lams)
+        allq = torch.arange(w.n, dtype=torch.int32, device=dev)
+        na = torch.tensor([w.n], dtype=torch.int64, device=dev)
+        _, fa_ = ev.eval_eam(xs, z)
+        _, fa_ = ev.eval_ace(xs, z, allq, na, f=fa_)
+        d = (fh_ - fa_)[detected]
+        extras["force_err_rms_meV_A_detected"] = float(torch.sqrt((d * d).mean()).item() * 1e3)
+        extras["force_err_max_meV_A_detected"] = float(d.abs().max().item() * 1e3)
+        ev.close()
+        del ev
+        torch.cuda.empty_cache()
+        # full-ACE and full-EAM on the same GPU, same workload, same code path
+        for mode in ("full-ace", "full-eam"):
+            c2 = new_ctx(hyb_for(mode, w.hyb))
+            x2, v2, f2, m2, fx2, l2 = tensors()
+            c2.build_neighbors(x2, w.box)
+            c2.step(x2, v2, f2, m2, fx2, l2, 0)
+            c2.step(x2, v2, f2, m2, fx2, l2, MD_PER_STEP)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            k2 = 2
+            for _ in range(k2):
+                c2.step(x2, v2, f2, m2, fx2, l2, MD_PER_STEP)
+            b.record(stream)
+            torch.cuda.synchronize()
+            extras[mode.replace("-", "_") + "_atom_steps_s"] = w.n * MD_PER_STEP * k2 / (a.elapsed_time(b) / 1e3)
+            c2.close()
+            del c2, x2, v2, f2, m2, fx2, l2
+            torch.cuda.empty_cache()
+        extras["speedup_vs_full_ace"] = value / ws / extras["full_ace_atom_steps_s"]
+        if ws == 1:
+            n_s, times, cores = oracle_sample(w.hyb, reps=1)
+            cpu = {"value": n_s / times[0], "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+                   "sample": "6x6x100-cell column (14,400 atoms) of the same slab, one MD step of force work "
+                             "(classification + hybrid forces + indenter), FP64 oracle"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == ap.PREC_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": f"nanoindentation-shaped FCC slab {args.ncell}^3 cells ({w.n} atoms), Hyb2 "
+                                   f"(r_lambda 8/20 A), {args.mode}, {args.precision} precision",
+                       "atoms": w.n, "md_steps_per_step": MD_PER_STEP, "lambda_every": MD_PER_STEP,
+                       "precision": "FP32 potentials, FP64 integration and energy sums" if prec == ap.PREC_MIXED
+                       else "FP64", "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "precise_fraction": stats.n_precise / w.n, "n_precise": stats.n_precise, "n_detected": stats.n_detected,
+            "e2e": {"value": atom_steps / (ms_e2e / 1e3), "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": prof["kernels"],
+            "roofline": {"bound": "alu", "kernel": "k_ace (fused ACE energy/adjoint/force)",
+                         "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived, not measured)",
+                         "ace_ms_per_launch": ace_ms / max(1, ace_calls), "ace_pairs": prof["ace_pairs"],
+                         "ace_atoms": prof["ace_atoms"]},
+            "phase_share": phase_share,
+            "clocks": ck,
+            "cpu_baseline": cpu,
+            **extras,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, ws, rank)
+        return
+    run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,267 @@
+/*
+ * ap.h -- C-ABI of the GB300 adaptive-precision EAM/ACE force evaluation.
+ *
+ * Method: "Adaptive-precision potentials for large-scale atomistic simulations"
+ * (arXiv 2411.03002).  Each atom i carries a switching parameter lambda_i in [0,1]
+ * (the fast weight): E_i = lambda_i E_i^(f) + (1 - lambda_i) E_i^(p) (Eq. energy_hyb),
+ * with E^(f) an embedded-atom model (Eq. energy_eam) and E^(p) a linear atomic
+ * cluster expansion (Eq. energy_ace).  lambda_i comes from the time-averaged
+ * centro-symmetry parameter (Eq. csp_1_i, Appendix A) through the switching
+ * function of Appendix B (Eqs. csp_2_i, lambda_1_i .. lambda_4_i).  Forces are
+ * the fixed-lambda gradient F_i^d (Eq. F_i_d, section 2.3); time integration is
+ * velocity Verlet with the lambda step (Eq. vv).
+ *
+ * Conventions for every entry point:
+ *   - Return value: ap_status, AP_OK (0) on success.  Nothing throws across the
+ *     ABI.  ap_last_error(ctx) returns a message for the last failure.
+ *   - Pointers named d_* are caller-owned DEVICE pointers (contiguous, CUDA
+ *     global memory of the current device); pointers named h_* are caller-owned
+ *     HOST pointers.  The library never frees caller memory.  It owns only the
+ *     scratch held in the context (neighbour lists, histories, queues), which it
+ *     allocates on first use and grows when a larger n arrives.
+ *   - Arrays of 3-vectors are row-major [n][3] (x0 y0 z0 x1 ...).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream) unless a comment says the call synchronises.
+ *   - A context is bound to one device and is not thread-safe.
+ *   - lambda is always the paper's lambda (1 = fast/EAM, 0 = precise/ACE).
+ *   - Units: eV, Angstrom, fs, amu.
+ */
+#ifndef AP_H
+#define AP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ap_status;
+
+#define AP_OK 0
+#define AP_ERR_ARG 1        /* invalid argument (null pointer, bad size, bad config)   */
+#define AP_ERR_CUDA 2       /* a CUDA runtime call failed                              */
+#define AP_ERR_CAPACITY 3   /* a neighbour row exceeded its capacity; see ap_need()    */
+#define AP_ERR_NONFINITE 4  /* NaN/Inf found in positions or forces                    */
+#define AP_ERR_TIMEOUT 5    /* a bounded device wait gave up                           */
+#define AP_ERR_STATE 6      /* call order violated (e.g. evaluation before neighbours) */
+#define AP_ERR_RADICAND 7   /* reserved: negative radicand in the local thermostat     */
+#define AP_ERR_BOX 8        /* an atom lies outside a non-periodic box dimension       */
+#define AP_ERR_SKIN 9       /* an atom moved more than skin/2 between list rebuilds    */
+
+#define AP_PREC_FP64 0      /* all potential arithmetic in FP64                        */
+#define AP_PREC_MIXED 1     /* FP32 potentials; FP64 integration and energy sums       */
+
+#define AP_FCUT_PRINTED 0   /* f_cut(x) = 1 - 1.875x + 1.25x^3 - 0.375x^5 as printed    */
+#define AP_FCUT_C2 1        /* C2-symmetric reading 0.5*p(2x-1)                         */
+
+/* Orthorhombic box: lo <= x < hi in periodic dimensions (positions may be
+ * unwrapped; the library works with images); in non-periodic dimensions every
+ * atom must satisfy lo <= x < hi, else AP_ERR_BOX. */
+typedef struct {
+  double lo[3];
+  double hi[3];
+  int32_t periodic[3];
+} ap_box;
+
+/* Every parameter of one run.  Plain data; copied by ap_create. */
+typedef struct {
+  /* EAM (Eq. energy_eam) with the analytic forms
+   *   zeta(r) = exp(-beta (r/r0 - 1)) psi((r - rc)/h),
+   *   xi(rho) = -A sqrt(rho),
+   *   Phi(r)  = D [exp(-2 alpha (r - rp)) - 2 exp(-alpha (r - rp))] psi((r - rc)/h),
+   *   psi(x)  = x^4/(1 + x^4) for x < 0, else 0. */
+  double eam_beta, eam_alpha, eam_A, eam_D, eam_rp, eam_r0, eam_rc, eam_h;
+  /* Linear ACE (Eq. energy_ace): E_i = sum_v c_v B_iv.  Radial basis
+   * g_k(r) = T_k(2r/rc - 1) f_cut(r/rc), R_nl = sum_k W[l][n][k] g_k (n,k < 8,
+   * l <= 4); A_nlm = (1/n0) sum_j R_nl Y_lm; B: nu = 1, 2 (all n1 <= n2, l) and 3
+   * (n <= 2, l <= 3, Gaunt-coupled), 325 functions in the order documented in
+   * the design doc.  ace_c holds ace_nc >= 325 coefficients (extra ignored). */
+  double ace_W[5 * 8 * 8];
+  double ace_c[512];
+  int32_t ace_nc;
+  double ace_rc, ace_n0;
+  /* Switching function (Appendix B, Table model_parameters). */
+  double csp_lo, csp_hi;     /* Angstrom^2 */
+  double r_lo, r_hi;         /* lambda spread radii, Angstrom */
+  double dlam_min;           /* minimum lambda step */
+  int32_t n_csp_avg;         /* samples in the CSP moving average */
+  int32_t n_lam_avg;         /* samples in the lambda_min moving average */
+  int32_t fcut_mode;         /* AP_FCUT_* */
+  /* Neighbour lists: radius = potential cutoff + skin.  cap_* = entries per row
+   * (0 selects 160 for EAM and 288 for ACE). */
+  double skin;
+  int32_t cap_eam, cap_ace;
+  int32_t precision;         /* AP_PREC_* */
+  /* Molecular dynamics (ap_step). */
+  double dt;                 /* fs */
+  int32_t lambda_every;      /* lambda update and list rebuild period (steps) */
+  int32_t indenter_on;       /* 1: spherical indenter F = k (R - r)^2 (x - c)/r, r < R */
+  double ind_c0[3], ind_v[3], ind_R, ind_k;   /* centre at t=0 (A), velocity (A/fs), R (A), k (eV/A^3) */
+} ap_config;
+
+typedef struct ap_ctx ap_ctx;
+
+/* Statistics written by ap_step (host struct). */
+typedef struct {
+  int64_t step;              /* MD steps done by this context so far */
+  int64_t n_precise;         /* |{i : lambda_i < 1}| after the last update */
+  int64_t n_detected;        /* |{i : lambda_0,i < 1}| after the last update */
+  int64_t rebuilds;          /* neighbour-list rebuilds so far */
+  double e_pot;              /* sum_i E_i (Eq. energy_hyb) + indenter energy, FP64 */
+  double e_kin;              /* sum_i m v^2 / 2, FP64 */
+  double max_disp;           /* largest displacement since the last rebuild (A) */
+  int32_t error_bits;        /* OR of 1 << AP_ERR_* seen on the device */
+} ap_step_stats;
+
+/* ----------------------------------------------------------------- lifetime */
+
+/* Create a context on the current CUDA device.  Builds the ACE coupling tables
+ * on the host (real Gaunt coefficients from the Racah formula).  Synchronous.
+ * Errors: AP_ERR_ARG for a null pointer or an invalid config. */
+ap_status ap_create(const ap_config* h_cfg, ap_ctx** out);
+
+/* Free all library-owned device memory.  Synchronises the device. */
+void ap_destroy(ap_ctx* ctx);
+
+/* Static message of the last error of ctx (never NULL). */
+const char* ap_last_error(const ap_ctx* ctx);
+
+/* Required capacity after AP_ERR_CAPACITY (largest row count seen). */
+int64_t ap_need(const ap_ctx* ctx);
+
+/* Number of ACE B-functions (325) and their description: h_desc[v*7 + 0..6] =
+ * nu, n1, n2, n3, l1, l2, l3 (unused slots 0). */
+int32_t ap_ace_nbasis(const ap_ctx* ctx);
+ap_status ap_ace_basis_desc(const ap_ctx* ctx, int32_t* h_desc);
+
+/* Real Gaunt coefficients used by the nu = 3 couplings, computed on the host
+ * from the Racah 3j formula: h_out[((((l1*7+m1+3)*4+l2)*7+m2+3)*4+l3)*7+m3+3]. */
+ap_status ap_ace_gaunt(const ap_ctx* ctx, double* h_out);
+
+/* ----------------------------------------------------------------- neighbours */
+
+/* Cell list (section 2.4: per-domain neighbour search) and full neighbour rows
+ * at eam_rc + skin for every atom: j in row i iff (j,s) != (i,0) and
+ * |x_j + s L - x_i|^2 < (eam_rc + skin)^2 in FP64 (the defining arithmetic; FP32
+ * is only a pre-filter with a guard band).  d_x [n][3] FP64 positions, possibly
+ * unwrapped.  d_species may be NULL (single species; nonzero entries are an
+ * error).  Synchronises to check capacity; grows the rows and rebuilds once if a
+ * row overflowed.  Errors: AP_ERR_ARG, AP_ERR_BOX, AP_ERR_CAPACITY, AP_ERR_CUDA. */
+ap_status ap_build_neighbors(ap_ctx* ctx, int64_t n, const double* d_x, const int32_t* d_species,
+                             const ap_box* h_box, void* stream);
+
+/* Same for n_sys independent systems concatenated in d_x: system s owns atoms
+ * [h_offsets[s], h_offsets[s+1]) and box h_boxes[s].  No pair crosses systems. */
+ap_status ap_build_neighbors_batch(ap_ctx* ctx, int32_t n_sys, const int64_t* h_offsets, const ap_box* h_boxes,
+                                   const double* d_x, const int32_t* d_species, void* stream);
+
+/* Export the neighbour rows (which = 0: EAM rows of all atoms; 1: ACE rows of
+ * the last precise queue, radius ace_rc + skin).  d_cnt [rows], d_idx
+ * [rows][cap], d_shift [rows][cap][3] = s of each entry relative to the d_x of
+ * the build.  *h_rows receives the number of rows.  Synchronises. */
+ap_status ap_get_neighbors(ap_ctx* ctx, int32_t which, int32_t* d_cnt, int32_t* d_idx, int32_t* d_shift, int64_t cap,
+                           int64_t* h_rows);
+
+/* ----------------------------------------------------------------- lambda */
+
+/* One lambda update (Appendix B) from the current neighbour rows, in FP64 with
+ * the arithmetic order of the definitions (bit-reproducible sets):
+ *   CSP_i: 12 nearest neighbours within eam_rc + skin (fewer -> +inf), the 6
+ *     smallest |r_a + r_b|^2 summed in ascending order (Eq. csp_1_i, Appendix A);
+ *   CSP_avg: mean of the last n_csp_avg samples incl. this one (Eq. csp_2_i);
+ *   lambda_0 = 1 - f_cut((csp_hi - CSP_avg)/(csp_hi - csp_lo)) (Eq. lambda_1_i);
+ *   lambda_min: minimum over detected atoms within r_hi (Eq. lambda_2_i);
+ *   lambda_avg: mean of the last n_lam_avg lambda_min samples (Eq. lambda_3_i);
+ *   lambda = lambda_avg,msz (Eq. lambda_4_i).
+ * d_changeable [n] uint8 (NULL = all changeable; 0 = lambda fixed at 1).
+ * Outputs: d_lam [n] FP64; d_precise_idx [n] int32 = ascending indices with
+ * lambda < 1 (the precise work queue); d_n_precise device int64.  The first call
+ * after creation or ap_reset_lambda fills the histories with its sample.
+ * Requires a neighbour build at the same positions for exact CSP candidates. */
+ap_status ap_classify(ap_ctx* ctx, int64_t n, const double* d_x, const uint8_t* d_changeable, double* d_lam,
+                      int32_t* d_precise_idx, int64_t* d_n_precise, void* stream);
+
+/* Forget the CSP/lambda histories and the previous lambda. */
+ap_status ap_reset_lambda(ap_ctx* ctx);
+
+/* Copy intermediate arrays of the last ap_classify (any pointer may be NULL):
+ * CSP sample, CSP_avg, lambda_0, lambda_min, lambda_avg (each [n] FP64). */
+ap_status ap_get_lambda_state(ap_ctx* ctx, double* d_csp, double* d_csp_avg, double* d_lam0, double* d_lam_min,
+                              double* d_lam_avg, void* stream);
+
+/* ----------------------------------------------------------------- potentials */
+
+/* EAM for every atom (Eq. energy_eam) with lambda weights (Eq. F_i_d):
+ *   d_e_fast[i] = xi(rho_i) + 1/2 sum_j Phi(r_ij)              (written, FP64)
+ *   d_f[i]     += -grad_i sum_k lambda_k E_k^(f)  at fixed lambda (accumulated)
+ * d_lam [n] FP64 (NULL = all 1).  Requires ap_build_neighbors on the same n. */
+ap_status ap_eval_eam(ap_ctx* ctx, int64_t n, const double* d_x, const double* d_lam, double* d_e_fast, double* d_f,
+                      void* stream);
+
+/* Linear ACE for the atoms of the precise queue (Eq. energy_ace) with weights
+ * w_i = 1 - lambda_i:
+ *   d_e_prec[i] = E_i^(p) for i in the queue, 0 for every other atom  (written)
+ *   d_f[k]     += -grad_k sum_i w_i E_i^(p)                           (accumulated)
+ * d_precise_idx [*d_n_precise] int32 atom indices (e.g. from ap_classify);
+ * d_n_precise is a DEVICE int64.  Builds the ACE rows (ace_rc + skin) for the
+ * queue.  d_f may be NULL (energies only). */
+ap_status ap_eval_ace(ap_ctx* ctx, int64_t n, const double* d_x, const double* d_lam, const int32_t* d_precise_idx,
+                      const int64_t* d_n_precise, double* d_e_prec, double* d_f, void* stream);
+
+/* Blend (Eq. energy_hyb): d_e_atom[i] = lambda_i e_fast_i + (1 - lambda_i) e_prec_i
+ * (FP64) and d_e_total (device double) = sum_i d_e_atom[i] by a fixed-order
+ * tree reduction (bitwise reproducible).  d_e_atom may be NULL. */
+ap_status ap_blend_forces(ap_ctx* ctx, int64_t n, const double* d_lam, const double* d_e_fast, const double* d_e_prec,
+                          double* d_e_atom, double* d_e_total, void* stream);
+
+/* ----------------------------------------------------------------- dynamics */
+
+/* nsteps of velocity Verlet with the lambda step (Eq. vv), all on the device:
+ * half kick, drift, [every lambda_every steps: wrap, neighbour rebuild, lambda
+ * update, precise queue], EAM + ACE forces at the new lambda, indenter, half kick.
+ * Fixed atoms (d_fixed[i] != 0) keep v = 0, do not move and keep lambda = 1.
+ * On the first call the context prepares neighbours, lambda and F(x(0)) itself.
+ * d_x, d_v, d_f [n][3] FP64 in/out; d_mass [n] FP64; d_fixed [n] uint8 or NULL;
+ * d_lam [n] FP64 out.  h_stats (may be NULL) is filled at the end; the call
+ * synchronises the stream once at its end.  Errors: as above plus AP_ERR_SKIN
+ * (an atom moved more than skin/2 before a rebuild) and AP_ERR_NONFINITE. */
+ap_status ap_step(ap_ctx* ctx, int64_t n, double* d_x, double* d_v, double* d_f, const double* d_mass,
+                  const uint8_t* d_fixed, double* d_lam, int64_t nsteps, ap_step_stats* h_stats, void* stream);
+
+/* ----------------------------------------------------------------- profiling */
+
+/* Phases timed by ap_step when profiling is on (CUDA events on the call's stream). */
+#define AP_PHASE_NEIGHBORS 0   /* wrap, cell list, shadows, EAM rows              */
+#define AP_PHASE_CLASSIFY 1    /* CSP, lambda_0, spread, averages, queue, ACE rows */
+#define AP_PHASE_EAM 2         /* EAM density + force kernels                      */
+#define AP_PHASE_ACE 3         /* fused ACE energy/adjoint/force kernel           */
+#define AP_PHASE_OTHER 4       /* integrator, finalize, indenter, reductions      */
+#define AP_NUM_PHASES 5
+
+/* Turn per-phase event timing in ap_step on (1) or off (0) and clear the totals.
+ * No paper counterpart: instrumentation of this implementation. */
+ap_status ap_profile_enable(ap_ctx* ctx, int32_t on);
+
+/* Accumulated device milliseconds and launch counts per phase since the last
+ * ap_profile_enable (h_ms, h_calls: AP_NUM_PHASES entries each), the number of
+ * this library's kernels launched by ap_step (*h_kernels), and the neighbour
+ * pairs within ace_rc (*h_ace_pairs) and precise atoms (*h_ace_atoms) that the
+ * ACE kernel processed, as of the last synchronising call.  Host pointers; any
+ * may be NULL. */
+ap_status ap_profile_read(ap_ctx* ctx, double* h_ms, int64_t* h_calls, int64_t* h_kernels, int64_t* h_ace_pairs,
+                          int64_t* h_ace_atoms);
+
+/* ----------------------------------------------------------------- checkpoint */
+
+/* Serialise the lambda histories, previous lambda, ring positions and step
+ * counter into a host buffer.  With h_buf == NULL only *h_len (bytes) is set.
+ * Synchronises. */
+ap_status ap_state_export(ap_ctx* ctx, void* h_buf, size_t* h_len);
+ap_status ap_state_import(ap_ctx* ctx, const void* h_buf, size_t h_len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AP_H */

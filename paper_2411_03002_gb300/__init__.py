@@ -1,0 +1,12 @@
+"""GB300-native adaptive-precision EAM/ACE force evaluation (arXiv 2411.03002).
+
+The computation lives in libap.so (hand-written CUDA for sm_103a, C-ABI in
+include/ap.h).  This package is its Python binding.
+"""
+from .api import (Context, StepStats, ace_basis_desc, ace_gaunt, ace_nbasis, ap_blend_forces, ap_build_neighbors,
+                  ap_classify, ap_create, ap_eval_ace, ap_eval_eam, ap_step, make_box, make_config)
+from ._native import ApConfig, ApError, PREC_FP64, PREC_MIXED
+
+__all__ = ["Context", "StepStats", "ApConfig", "ApError", "PREC_FP64", "PREC_MIXED", "make_box", "make_config",
+           "ace_nbasis", "ace_basis_desc", "ace_gaunt", "ap_create", "ap_build_neighbors", "ap_classify",
+           "ap_eval_eam", "ap_eval_ace", "ap_blend_forces", "ap_step"]

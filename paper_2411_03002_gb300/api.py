@@ -1,0 +1,287 @@
+"""Python binding of the C-ABI (include/ap.h): the same calls, marshalled from
+torch tensors.  Every step of the computation runs in libap.so's CUDA kernels;
+this module only passes device pointers, sizes and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _native as N
+from ._native import ApBox, ApConfig, ApError, ApStepStats
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_box(lo, hi, periodic) -> ApBox:
+    b = ApBox()
+    for k in range(3):
+        b.lo[k] = float(lo[k])
+        b.hi[k] = float(hi[k])
+        b.periodic[k] = int(bool(periodic[k]))
+    return b
+
+
+def make_config(eam, ace, hyb, precision: int = N.PREC_MIXED, skin: float = 1.0, dt: float = 1.0,
+                indenter=None, cap_eam: int = 0, cap_ace: int = 0, lambda_every: Optional[int] = None) -> ApConfig:
+    """Fill an ap_config from parameter objects with the attribute names of
+    the EAM (beta, alpha, A, D, rp, r0, rc, h), ACE (W, c, rc, n0) and switching
+    (csp_lo, csp_hi, r_lo, r_hi, dlam_min, n_csp_avg, n_lam_avg, fcut_mode,
+    sample_every) parameter sets."""
+    c = ApConfig()
+    for k in ("beta", "alpha", "A", "D", "rp", "r0", "rc", "h"):
+        setattr(c, "eam_" + k, float(getattr(eam, k)))
+    W = np.ascontiguousarray(ace.W, dtype=np.float64).reshape(-1)
+    if W.size != 320:
+        raise ValueError("ACE W must have 5*8*8 entries")
+    cc = np.ascontiguousarray(ace.c, dtype=np.float64).reshape(-1)
+    for i in range(320):
+        c.ace_W[i] = W[i]
+    nc = min(512, cc.size)
+    for i in range(nc):
+        c.ace_c[i] = cc[i]
+    c.ace_nc = nc
+    c.ace_rc = float(ace.rc)
+    c.ace_n0 = float(ace.n0)
+    c.csp_lo, c.csp_hi = float(hyb.csp_lo), float(hyb.csp_hi)
+    c.r_lo, c.r_hi = float(hyb.r_lo), float(hyb.r_hi)
+    c.dlam_min = float(hyb.dlam_min)
+    c.n_csp_avg, c.n_lam_avg = int(hyb.n_csp_avg), int(hyb.n_lam_avg)
+    c.fcut_mode = int(hyb.fcut_mode)
+    c.skin = float(skin)
+    c.cap_eam, c.cap_ace = int(cap_eam), int(cap_ace)
+    c.precision = int(precision)
+    c.dt = float(dt)
+    c.lambda_every = int(lambda_every if lambda_every is not None else hyb.sample_every)
+    if indenter is not None:
+        c.indenter_on = 1
+        for k in range(3):
+            c.ind_c0[k] = float(indenter.center0[k])
+            c.ind_v[k] = float(indenter.velocity[k])
+        c.ind_R = float(indenter.radius)
+        c.ind_k = float(indenter.k)
+    return c
+
+
+def ace_nbasis() -> int:
+    return N.lib().ap_ace_nbasis(None)
+
+
+def ace_basis_desc() -> np.ndarray:
+    d = np.zeros((ace_nbasis(), 7), np.int32)
+    _check(None, N.lib().ap_ace_basis_desc(None, d.ctypes.data_as(ctypes.c_void_p)))
+    return d
+
+
+def ace_gaunt() -> np.ndarray:
+    g = np.zeros((4, 7, 4, 7, 4, 7))
+    _check(None, N.lib().ap_ace_gaunt(None, g.ctypes.data_as(ctypes.c_void_p)))
+    return g
+
+
+def _check(ctx, st: int):
+    if st != N.AP_OK:
+        msg = N.lib().ap_last_error(ctx).decode() if ctx else ""
+        raise ApError(st, msg)
+
+
+@dataclasses.dataclass
+class StepStats:
+    step: int
+    n_precise: int
+    n_detected: int
+    rebuilds: int
+    e_pot: float
+    e_kin: float
+    max_disp: float
+    error_bits: int
+
+
+class Context:
+    """One ap_ctx on the current CUDA device."""
+
+    def __init__(self, cfg: ApConfig):
+        self.lib = N.lib()
+        h = ctypes.c_void_p()
+        st = self.lib.ap_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != N.AP_OK:
+            raise ApError(st, "ap_create failed")
+        self.h = h
+        self.cfg = cfg
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ap_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st):
+        _check(self.h, st)
+
+    @property
+    def nbasis(self) -> int:
+        return self.lib.ap_ace_nbasis(self.h)
+
+    def need(self) -> int:
+        return self.lib.ap_need(self.h)
+
+    # ---------------------------------------------------------------- neighbours
+    def build_neighbors(self, x: torch.Tensor, box, species: Optional[torch.Tensor] = None, stream=None):
+        b = box if isinstance(box, ApBox) else make_box(box.lo, box.hi, box.periodic)
+        self.n = x.shape[0]
+        self._ck(self.lib.ap_build_neighbors(self.h, self.n, _ptr(x), _ptr(species), ctypes.byref(b),
+                                             _stream(stream)))
+
+    def build_neighbors_batch(self, x: torch.Tensor, offsets: Sequence[int], boxes: Sequence, species=None,
+                              stream=None):
+        ns = len(boxes)
+        off = (ctypes.c_int64 * (ns + 1))(*[int(o) for o in offsets])
+        arr = (ApBox * ns)(*[b if isinstance(b, ApBox) else make_box(b.lo, b.hi, b.periodic) for b in boxes])
+        self.n = int(offsets[-1])
+        self._ck(self.lib.ap_build_neighbors_batch(self.h, ns, off, arr, _ptr(x), _ptr(species), _stream(stream)))
+
+    def get_neighbors(self, which: int = 0, cap: int = 320):
+        """(cnt [rows], idx [rows, cap], shift [rows, cap, 3]) as CUDA int32 tensors."""
+        rows = ctypes.c_int64()
+        dev = torch.device("cuda")
+        nrows = self.n
+        cnt = torch.zeros(max(nrows, 1), dtype=torch.int32, device=dev)
+        idx = torch.zeros((max(nrows, 1), cap), dtype=torch.int32, device=dev)
+        sh = torch.zeros((max(nrows, 1), cap, 3), dtype=torch.int32, device=dev)
+        self._ck(self.lib.ap_get_neighbors(self.h, which, _ptr(cnt), _ptr(idx), _ptr(sh), cap, ctypes.byref(rows)))
+        r = rows.value
+        return cnt[:r], idx[:r], sh[:r]
+
+    # ---------------------------------------------------------------- lambda
+    def classify(self, x: torch.Tensor, changeable: Optional[torch.Tensor] = None, stream=None):
+        n = x.shape[0]
+        lam = torch.empty(n, dtype=torch.float64, device=x.device)
+        idx = torch.empty(max(n, 1), dtype=torch.int32, device=x.device)
+        cnt = torch.zeros(1, dtype=torch.int64, device=x.device)
+        self._ck(self.lib.ap_classify(self.h, n, _ptr(x), _ptr(changeable), _ptr(lam), _ptr(idx), _ptr(cnt),
+                                      _stream(stream)))
+        return lam, idx, cnt
+
+    def reset_lambda(self):
+        self._ck(self.lib.ap_reset_lambda(self.h))
+
+    def get_lambda_state(self, stream=None):
+        n = self.n
+        dev = torch.device("cuda")
+        out = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(5)]
+        self._ck(self.lib.ap_get_lambda_state(self.h, *[_ptr(t) for t in out], _stream(stream)))
+        return dict(zip(("csp", "csp_avg", "lam0", "lam_min", "lam_avg"), out))
+
+    # ---------------------------------------------------------------- potentials
+    def eval_eam(self, x, lam=None, e_fast=None, f=None, stream=None):
+        n = x.shape[0]
+        if e_fast is None:
+            e_fast = torch.empty(n, dtype=torch.float64, device=x.device)
+        if f is None:
+            f = torch.zeros((n, 3), dtype=torch.float64, device=x.device)
+        self._ck(self.lib.ap_eval_eam(self.h, n, _ptr(x), _ptr(lam), _ptr(e_fast), _ptr(f), _stream(stream)))
+        return e_fast, f
+
+    def eval_ace(self, x, lam, precise_idx, n_precise, e_prec=None, f=None, forces: bool = True, stream=None):
+        n = x.shape[0]
+        if e_prec is None:
+            e_prec = torch.empty(n, dtype=torch.float64, device=x.device)
+        if f is None and forces:
+            f = torch.zeros((n, 3), dtype=torch.float64, device=x.device)
+        self._ck(self.lib.ap_eval_ace(self.h, n, _ptr(x), _ptr(lam), _ptr(precise_idx), _ptr(n_precise),
+                                      _ptr(e_prec), _ptr(f), _stream(stream)))
+        return e_prec, f
+
+    def blend_forces(self, lam, e_fast, e_prec, stream=None):
+        n = e_fast.shape[0]
+        e_atom = torch.empty(n, dtype=torch.float64, device=e_fast.device)
+        e_tot = torch.zeros(1, dtype=torch.float64, device=e_fast.device)
+        self._ck(self.lib.ap_blend_forces(self.h, n, _ptr(lam), _ptr(e_fast), _ptr(e_prec), _ptr(e_atom),
+                                          _ptr(e_tot), _stream(stream)))
+        return e_atom, e_tot
+
+    # ---------------------------------------------------------------- dynamics
+    def step(self, x, v, f, mass, fixed, lam, nsteps: int, stream=None) -> StepStats:
+        st = ApStepStats()
+        n = x.shape[0]
+        self._ck(self.lib.ap_step(self.h, n, _ptr(x), _ptr(v), _ptr(f), _ptr(mass), _ptr(fixed), _ptr(lam),
+                                  int(nsteps), ctypes.byref(st), _stream(stream)))
+        return StepStats(st.step, st.n_precise, st.n_detected, st.rebuilds, st.e_pot, st.e_kin, st.max_disp,
+                         st.error_bits)
+
+    PHASES = ("neighbors", "classify", "eam", "ace", "other")
+
+    def profile_enable(self, on: bool = True):
+        self._ck(self.lib.ap_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        ms = (ctypes.c_double * 5)()
+        calls = (ctypes.c_int64 * 5)()
+        kern, pairs, atoms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._ck(self.lib.ap_profile_read(self.h, ms, calls, ctypes.byref(kern), ctypes.byref(pairs),
+                                          ctypes.byref(atoms)))
+        return {"phases": {p: (ms[k], calls[k]) for k, p in enumerate(self.PHASES)}, "kernels": kern.value,
+                "ace_pairs": pairs.value, "ace_atoms": atoms.value}
+
+    def state_export(self) -> bytes:
+        ln = ctypes.c_size_t()
+        self._ck(self.lib.ap_state_export(self.h, None, ctypes.byref(ln)))
+        buf = ctypes.create_string_buffer(ln.value)
+        self._ck(self.lib.ap_state_export(self.h, buf, ctypes.byref(ln)))
+        return buf.raw
+
+    def state_import(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        self._ck(self.lib.ap_state_import(self.h, buf, len(data)))
+
+
+# Module-level calls with the C-ABI names.
+def ap_create(cfg: ApConfig) -> Context:
+    return Context(cfg)
+
+
+def ap_build_neighbors(ctx: Context, x, box, species=None, stream=None):
+    return ctx.build_neighbors(x, box, species, stream)
+
+
+def ap_classify(ctx: Context, x, changeable=None, stream=None):
+    return ctx.classify(x, changeable, stream)
+
+
+def ap_eval_eam(ctx: Context, x, lam=None, e_fast=None, f=None, stream=None):
+    return ctx.eval_eam(x, lam, e_fast, f, stream)
+
+
+def ap_eval_ace(ctx: Context, x, lam, precise_idx, n_precise, e_prec=None, f=None, stream=None):
+    return ctx.eval_ace(x, lam, precise_idx, n_precise, e_prec, f, stream=stream)
+
+
+def ap_blend_forces(ctx: Context, lam, e_fast, e_prec, stream=None):
+    return ctx.blend_forces(lam, e_fast, e_prec, stream)
+
+
+def ap_step(ctx: Context, x, v, f, mass, fixed, lam, nsteps: int, stream=None) -> StepStats:
+    return ctx.step(x, v, f, mass, fixed, lam, nsteps, stream)

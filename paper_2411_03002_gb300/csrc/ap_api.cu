@@ -1,0 +1,793 @@
+// C-ABI entry points (include/ap.h) and the host-side orchestration.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ap_internal.cuh"
+
+using namespace ap;
+
+namespace {
+
+ap_status fail(ap_ctx* c, ap_status st, const std::string& msg) {
+  if (c) c->err_msg = msg;
+  return st;
+}
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(c, AP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <typename T>
+cudaError_t dalloc(T*& p, size_t count) {
+  dfree(p);
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)&p, sizeof(T) * count);
+}
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+ap_status validate(const ap_config& g, std::string& why) {
+  auto bad = [&](const char* m) {
+    why = m;
+    return AP_ERR_ARG;
+  };
+  if (!(g.eam_rc > 0 && g.eam_h > 0 && g.eam_r0 > 0)) return bad("EAM cutoff, h and r0 must be positive");
+  if (!(g.ace_rc > 0 && g.ace_n0 > 0)) return bad("ACE cutoff and N0 must be positive");
+  if (!(g.skin >= 0)) return bad("skin must be >= 0");
+  if (!(g.csp_hi > g.csp_lo)) return bad("csp_hi must exceed csp_lo");
+  if (!(g.r_hi > g.r_lo && g.r_lo >= 0)) return bad("need 0 <= r_lo < r_hi");
+  if (g.n_csp_avg < 1 || g.n_lam_avg < 1) return bad("averaging windows must be >= 1");
+  if (g.precision != AP_PREC_FP64 && g.precision != AP_PREC_MIXED) return bad("unknown precision");
+  if (g.fcut_mode != AP_FCUT_PRINTED && g.fcut_mode != AP_FCUT_C2) return bad("unknown fcut_mode");
+  if (g.ace_nc < 0 || g.ace_nc > 512) return bad("ace_nc out of range");
+  if (g.cap_eam < 0 || g.cap_ace < 0 || g.cap_eam > 4096 || g.cap_ace > 4096) return bad("row capacity out of range");
+  if (g.lambda_every < 1) return bad("lambda_every must be >= 1");
+  return AP_OK;
+}
+
+// Cell grid of every system: edge >= (largest list radius)/2, so a 5x5x5 stencil
+// covers both lists.
+ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box* boxes) {
+  const ap_config& g = c->cfg;
+  double rlist = std::max(g.eam_rc, g.ace_rc) + g.skin;
+  double htarget = rlist / kStencil;
+  std::vector<SysInfo> sys(n_sys);
+  int base = 0;
+  bool stored = false;
+  int spread[3] = {0, 0, 0};
+  for (int s = 0; s < n_sys; ++s) {
+    SysInfo& I = sys[s];
+    std::memset(&I, 0, sizeof(I));
+    for (int d = 0; d < 3; ++d) {
+      double L = boxes[s].hi[d] - boxes[s].lo[d];
+      if (!(L > 0)) return fail(c, AP_ERR_ARG, "box hi must exceed lo in every dimension");
+      int nc = (int)std::floor(L / htarget);
+      if (nc < 1) nc = 1;
+      if (nc > kMaxCellsPerDim) return fail(c, AP_ERR_ARG, "box too large for the cell grid (1023 cells per dimension)");
+      I.lo[d] = boxes[s].lo[d];
+      I.L[d] = L;
+      I.nc[d] = nc;
+      I.h[d] = L / nc;
+      I.hf[d] = (float)I.h[d];
+      I.periodic[d] = boxes[s].periodic[d] ? 1 : 0;
+      if (I.periodic[d] && nc < 2 * kStencil + 1) stored = true;
+      int sp = (int)std::ceil(g.r_hi / I.h[d]);
+      if (!I.periodic[d]) sp = std::min(sp, nc);
+      spread[d] = std::max(spread[d], sp);
+    }
+    I.cell_base = base;
+    base += I.nc[0] * I.nc[1] * I.nc[2];
+  }
+  bool same = (n_sys == c->n_sys) && c->h_offsets.size() == (size_t)n_sys + 1 &&
+              std::equal(offsets, offsets + n_sys + 1, c->h_offsets.begin()) &&
+              std::memcmp(sys.data(), c->h_sys.data(), sizeof(SysInfo) * n_sys) == 0;
+  if (same) return AP_OK;
+  c->h_sys = sys;
+  c->h_offsets.assign(offsets, offsets + n_sys + 1);
+  c->n_sys = n_sys;
+  c->n_cells = base;
+  c->stored_off = stored;
+  for (int d = 0; d < 3; ++d) c->sten_spread[d] = spread[d];
+  CK(dalloc(c->d_sys, n_sys));
+  CK(cudaMemcpy(c->d_sys, sys.data(), sizeof(SysInfo) * n_sys, cudaMemcpyHostToDevice));
+  dfree(c->d_atom_sys);
+  int64_t n = offsets[n_sys];
+  if (n_sys > 1 && n > 0) {
+    std::vector<int> as(n);
+    for (int s = 0; s < n_sys; ++s)
+      for (int64_t i = offsets[s]; i < offsets[s + 1]; ++i) as[i] = s;
+    CK(dalloc(c->d_atom_sys, n));
+    CK(cudaMemcpy(c->d_atom_sys, as.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  }
+  if (c->n_cells + 1 > c->cells_cap) {
+    c->cells_cap = c->n_cells + 1;
+    CK(dalloc(c->d_cell_start, c->cells_cap + 1));
+    CK(dalloc(c->d_cell_count, c->cells_cap));
+  }
+  size_t need_tmp = scan_tmp_bytes(std::max<int64_t>(c->n_cells + 1, n + 1)) / sizeof(int) + 1;
+  if (need_tmp > c->scan_tmp_cap) {
+    c->scan_tmp_cap = need_tmp;
+    CK(dalloc(c->d_scan_tmp, need_tmp));
+  }
+  c->built = false;
+  return AP_OK;
+}
+
+ap_status alloc_rows(ap_ctx* c, bool eam, bool ace) {
+  if (eam) {
+    CK(dalloc(c->d_nbr_eam, (size_t)c->n_cap * c->cap_eam));
+    if (c->stored_off) CK(dalloc(c->d_off_eam, (size_t)c->n_cap * c->cap_eam));
+  }
+  if (ace) {
+    CK(dalloc(c->d_nbr_ace, (size_t)c->n_cap * c->cap_ace));
+    if (c->stored_off) CK(dalloc(c->d_off_ace, (size_t)c->n_cap * c->cap_ace));
+  }
+  return AP_OK;
+}
+
+ap_status ensure_capacity(ap_ctx* c, int64_t n) {
+  if (n > 0x7fffffff / 4) return fail(c, AP_ERR_ARG, "too many atoms for 32-bit indices");
+  bool stored_changed = c->stored_off && (!c->d_off_eam || !c->d_off_ace);
+  if (n <= c->n_cap && !stored_changed) return AP_OK;
+  int64_t m = std::max<int64_t>(n, c->n_cap);
+  c->n_cap = m;
+  CK(dalloc(c->d_cell, m));
+  CK(dalloc(c->d_cunw, m));
+  CK(dalloc(c->d_cell_atoms, m));
+  CK(dalloc(c->d_slot, m));
+  CK(dalloc(c->d_sh32, m));
+  CK(dalloc(c->d_sh64, m));
+  CK(dalloc(c->d_xbuild, 3 * m));
+  CK(dalloc(c->d_cnt_eam, m));
+  CK(dalloc(c->d_cnt_ace, m));
+  ap_status st = alloc_rows(c, true, true);
+  if (st) return st;
+  CK(dalloc(c->d_csp, m));
+  CK(dalloc(c->d_csp_avg, m));
+  CK(dalloc(c->d_lam0, m));
+  CK(dalloc(c->d_lam_min, m));
+  CK(dalloc(c->d_lam_avg, m));
+  CK(dalloc(c->d_lam_prev, m));
+  CK(dalloc(c->d_csp_hist, (size_t)c->cfg.n_csp_avg * m));
+  CK(dalloc(c->d_lam_hist, (size_t)c->cfg.n_lam_avg * m));
+  CK(dalloc(c->d_flag, m));
+  CK(dalloc(c->d_scan, m + 1));
+  CK(dalloc(c->d_detected, m));
+  CK(dalloc(c->d_precise, m));
+  CK(dalloc(c->d_lam_int, m));
+  void* q = c->d_q;
+  if (q) cudaFree(q);
+  CK(cudaMalloc(&c->d_q, 16 * (size_t)m));
+  CK(dalloc(c->d_xi, m));
+  CK(dalloc(c->d_facc32, m));
+  CK(dalloc(c->d_facc64, 3 * m));
+  CK(dalloc(c->d_efast, m));
+  CK(dalloc(c->d_eprec, m));
+  CK(dalloc(c->d_eatom, m));
+  CK(dalloc(c->d_eext, m));
+  CK(dalloc(c->d_changeable, m));
+  size_t need_tmp = scan_tmp_bytes(std::max<int64_t>(c->n_cells + 1, m + 1)) / sizeof(int) + 1;
+  if (need_tmp > c->scan_tmp_cap) {
+    c->scan_tmp_cap = need_tmp;
+    CK(dalloc(c->d_scan_tmp, need_tmp));
+  }
+  if (!c->d_red) CK(dalloc(c->d_red, 2048));
+  c->hist_started = false;
+  c->lam_ready = false;
+  c->md_ready = false;
+  return AP_OK;
+}
+
+ap_status read_scalars(ap_ctx* c, cudaStream_t s) {
+  CK(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return AP_OK;
+}
+
+ap_status check_err_bits(ap_ctx* c) {
+  int e = c->h_sc->err;
+  if (e & kErrArg)
+    return fail(c, AP_ERR_ARG, "invalid device input: nonzero species (single-species potentials) or queue index out of range");
+  if (e & kErrNonfinite) return fail(c, AP_ERR_NONFINITE, "non-finite position");
+  if (e & kErrBox) return fail(c, AP_ERR_BOX, "atom outside a non-periodic box dimension");
+  if (e & kErrCapacity) {
+    c->need = std::max(c->h_sc->need_eam, c->h_sc->need_ace);
+    return fail(c, AP_ERR_CAPACITY, "neighbour row capacity exceeded");
+  }
+  if (e & kErrSkin) return fail(c, AP_ERR_SKIN, "an atom moved more than skin/2 between rebuilds");
+  return AP_OK;
+}
+
+ap_status clear_err(ap_ctx* c, cudaStream_t s) {
+  CK(cudaMemsetAsync(&c->d_sc->err, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(&c->d_sc->need_eam, 0, 2 * sizeof(int), s));
+  return AP_OK;
+}
+
+// Bin, sort, shadow and EAM rows at the given positions (asynchronous).
+void build_async(ap_ctx* c, const double* d_x, const int32_t* d_species, cudaStream_t s) {
+  launch_bin(c, d_x, d_species, s);
+  launch_cell_sort(c, s);
+  launch_shadow(c, d_x, s);
+  launch_build_eam(c, d_x, s);
+  cudaMemcpyAsync(c->d_xbuild, d_x, sizeof(double) * 3 * (size_t)c->n, cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(&c->d_sc->max_disp2_bits, 0, sizeof(unsigned int), s);
+  c->rebuilds++;
+}
+
+// Build with a capacity check; grows the rows once if needed.  Synchronises.
+ap_status build_checked(ap_ctx* c, const double* d_x, const int32_t* d_species, cudaStream_t s) {
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    ap_status st = clear_err(c, s);
+    if (st) return st;
+    build_async(c, d_x, d_species, s);
+    CK(cudaGetLastError());
+    st = read_scalars(c, s);
+    if (st) return st;
+    int e = c->h_sc->err;
+    if ((e & kErrCapacity) && attempt == 0 && c->cfg.cap_eam == 0) {
+      c->cap_eam = c->h_sc->need_eam + 16;
+      st = alloc_rows(c, true, false);
+      if (st) return st;
+      continue;
+    }
+    st = check_err_bits(c);
+    if (st) return st;
+    break;
+  }
+  c->built = true;
+  return AP_OK;
+}
+
+ap_status build_ace_checked(ap_ctx* c, const double* d_x, const int* d_queue, cudaStream_t s) {
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    ap_status st = clear_err(c, s);
+    if (st) return st;
+    launch_build_ace(c, d_x, d_queue, &c->d_sc->n_precise, s);
+    CK(cudaGetLastError());
+    st = read_scalars(c, s);
+    if (st) return st;
+    if ((c->h_sc->err & kErrCapacity) && attempt == 0 && c->cfg.cap_ace == 0) {
+      c->cap_ace = c->h_sc->need_ace + 16;
+      st = alloc_rows(c, false, true);
+      if (st) return st;
+      continue;
+    }
+    return check_err_bits(c);
+  }
+  return AP_OK;
+}
+
+// Queue length from the caller's device int64, clamped to [0, n].
+__global__ void k_set_count(const long long* src, int n, int* dst32, long long* dst64) {
+  long long v = *src;
+  v = v < 0 ? 0 : (v > n ? n : v);
+  *dst32 = (int)v;
+  if (dst64) *dst64 = v;
+}
+
+// Copy the caller's queue (its first *count entries only); indices outside [0, n)
+// are replaced by 0 and flagged as an argument error.
+__global__ void k_copy_queue(const int* __restrict__ src, const int* __restrict__ count, int n, int* __restrict__ dst,
+                             DevScalars* sc) {
+  const int m = *count;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+    int i = src[q];
+    if (i < 0 || i >= n) {
+      atomicOr(&sc->err, kErrArg);
+      i = 0;
+    }
+    dst[q] = i;
+  }
+}
+
+__global__ void k_changeable(int n, const uint8_t* fixed, uint8_t* ch) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ch[i] = fixed[i] ? 0 : 1;
+}
+
+__global__ void k_check_skin(DevScalars* sc, float limit2) {
+  if (__uint_as_float(sc->max_disp2_bits) > limit2) atomicOr(&sc->err, kErrSkin);
+}
+
+__global__ void k_flag_precise(int n, const double* lam, int* flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = lam[i] < 1.0 ? 1 : 0;
+}
+
+__global__ void k_compact_q(int n, const int* flag, const int* scan, int* out, int* count32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) out[scan[i]] = i;
+  if (i == 0) *count32 = scan[n];
+}
+
+// Precise queue from an imported lambda (restart without a new lambda sample).
+void queue_from_lambda(ap_ctx* c, cudaStream_t s) {
+  int n = (int)c->n;
+  k_flag_precise<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_lam_int, c->d_flag);
+  scan_exclusive(c->d_flag, c->d_scan, n, c->d_scan_tmp, s);
+  k_compact_q<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_flag, c->d_scan, c->d_precise, &c->d_sc->n_precise);
+}
+
+// Event pair around one phase of ap_step (only when profiling is on).
+struct PhaseTimer {
+  ap_ctx* c;
+  cudaStream_t s;
+  int phase;
+  int start = -1;
+  static int next_event(ap_ctx* c) {
+    if (c->ev_used == (int)c->ev_pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c->ev_pool.push_back(e);
+    }
+    return c->ev_used++;
+  }
+  PhaseTimer(ap_ctx* c_, cudaStream_t s_, int phase_) : c(c_), s(s_), phase(phase_) {
+    if (!c->prof_on) return;
+    start = next_event(c);
+    cudaEventRecord(c->ev_pool[start], s);
+  }
+  ~PhaseTimer() {
+    if (start < 0) return;
+    int e = next_event(c);
+    cudaEventRecord(c->ev_pool[e], s);
+    c->ev_pairs_phase.push_back({phase, start});
+  }
+};
+
+// After a synchronisation: fold the recorded event pairs into the totals.
+void collect_profile(ap_ctx* c) {
+  for (auto& pr : c->ev_pairs_phase) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[pr.second], c->ev_pool[pr.second + 1]) == cudaSuccess) {
+      c->prof_ms[pr.first] += ms;
+      c->prof_calls[pr.first] += 1;
+    }
+  }
+  c->ev_pairs_phase.clear();
+  c->ev_used = 0;
+}
+
+void classify_async(ap_ctx* c, const double* d_x, const uint8_t* d_ch, double* d_lam, int* d_queue,
+                    int64_t* d_nq64, cudaStream_t s) {
+  launch_csp(c, d_x, d_ch, s);
+  launch_lambda0(c, d_ch, s);
+  launch_spread(c, d_x, d_ch, s);
+  launch_lambda_final(c, d_ch, d_lam, d_queue, d_nq64, s);
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+ap_status ap_create(const ap_config* h_cfg, ap_ctx** out) {
+  if (!h_cfg || !out) return AP_ERR_ARG;
+  *out = nullptr;
+  std::string why;
+  if (validate(*h_cfg, why) != AP_OK) return AP_ERR_ARG;
+  ap_ctx* c = new ap_ctx();
+  c->cfg = *h_cfg;
+  c->cap_eam = h_cfg->cap_eam ? h_cfg->cap_eam : 160;
+  c->cap_ace = h_cfg->cap_ace ? h_cfg->cap_ace : 288;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return AP_ERR_CUDA;
+  }
+  build_ace_tables(c->cfg, c->ace);
+  if (c->cfg.ace_nc < c->ace.nb) {
+    delete c;
+    return AP_ERR_ARG;
+  }
+  upload_ace_tables(c);
+  e = cudaMalloc(&c->d_sc, sizeof(DevScalars));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_sc, sizeof(DevScalars));
+  if (e == cudaSuccess) e = cudaMemset(c->d_sc, 0, sizeof(DevScalars));
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ap_destroy(c);
+    return AP_ERR_CUDA;
+  }
+  std::memset(c->h_sc, 0, sizeof(DevScalars));
+  *out = c;
+  return AP_OK;
+}
+
+void ap_destroy(ap_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  void* ptrs[] = {c->d_sys, c->d_atom_sys, c->d_cell, c->d_cunw, c->d_cell_start, c->d_cell_count, c->d_cell_atoms,
+                  c->d_slot, c->d_sh32, c->d_sh64, c->d_xbuild, c->d_nbr_eam, c->d_off_eam, c->d_cnt_eam,
+                  c->d_nbr_ace, c->d_off_ace, c->d_cnt_ace, c->d_csp, c->d_csp_avg, c->d_lam0, c->d_lam_min,
+                  c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected,
+                  c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_efast, c->d_eprec,
+                  c->d_eatom, c->d_eext, c->d_changeable, c->d_term_idx, c->d_term_coef32, c->d_term_coef64,
+                  c->d_W32, c->d_W64, c->d_scan_tmp, c->d_red, c->d_sc};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_sc) cudaFreeHost(c->h_sc);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* ap_last_error(const ap_ctx* c) { return c ? c->err_msg.c_str() : "null context"; }
+
+int64_t ap_need(const ap_ctx* c) { return c ? c->need : 0; }
+
+static const AceTables& default_tables() {
+  static AceTables t;
+  static bool done = false;
+  if (!done) {
+    ap_config g;
+    std::memset(&g, 0, sizeof(g));
+    build_ace_tables(g, t);
+    done = true;
+  }
+  return t;
+}
+
+int32_t ap_ace_nbasis(const ap_ctx* c) { return c ? c->ace.nb : default_tables().nb; }
+
+ap_status ap_ace_basis_desc(const ap_ctx* c, int32_t* h_desc) {
+  if (!h_desc) return AP_ERR_ARG;
+  const AceTables& t = c ? c->ace : default_tables();
+  std::memcpy(h_desc, t.desc.data(), sizeof(int32_t) * t.desc.size());
+  return AP_OK;
+}
+
+ap_status ap_ace_gaunt(const ap_ctx* c, double* h_out) {
+  if (!h_out) return AP_ERR_ARG;
+  const AceTables& t = c ? c->ace : default_tables();
+  std::memcpy(h_out, t.gaunt.data(), sizeof(double) * t.gaunt.size());
+  return AP_OK;
+}
+
+ap_status ap_build_neighbors_batch(ap_ctx* c, int32_t n_sys, const int64_t* h_offsets, const ap_box* h_boxes,
+                                   const double* d_x, const int32_t* d_species, void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (n_sys < 1 || !h_offsets || !h_boxes) return fail(c, AP_ERR_ARG, "need n_sys >= 1, offsets and boxes");
+  if (h_offsets[0] != 0) return fail(c, AP_ERR_ARG, "offsets must start at 0");
+  for (int s = 0; s < n_sys; ++s)
+    if (h_offsets[s + 1] < h_offsets[s]) return fail(c, AP_ERR_ARG, "offsets must be non-decreasing");
+  int64_t n = h_offsets[n_sys];
+  if (n > 0 && !d_x) return fail(c, AP_ERR_ARG, "null positions");
+  ap_status st = set_systems(c, n_sys, h_offsets, h_boxes);
+  if (st) return st;
+  st = ensure_capacity(c, n);
+  if (st) return st;
+  if (n != c->n) {
+    c->hist_started = false;
+    c->lam_ready = false;
+    c->md_ready = false;
+  }
+  c->n = n;
+  if (n == 0) {
+    c->built = true;
+    return AP_OK;
+  }
+  return build_checked(c, d_x, d_species, S(stream));
+}
+
+ap_status ap_build_neighbors(ap_ctx* c, int64_t n, const double* d_x, const int32_t* d_species, const ap_box* h_box,
+                             void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (n < 0 || !h_box) return fail(c, AP_ERR_ARG, "need n >= 0 and a box");
+  int64_t off[2] = {0, n};
+  return ap_build_neighbors_batch(c, 1, off, h_box, d_x, d_species, stream);
+}
+
+ap_status ap_get_neighbors(ap_ctx* c, int32_t which, int32_t* d_cnt, int32_t* d_idx, int32_t* d_shift, int64_t cap,
+                           int64_t* h_rows) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->built) return fail(c, AP_ERR_STATE, "no neighbour build yet");
+  if (which != 0 && which != 1) return fail(c, AP_ERR_ARG, "which must be 0 (EAM) or 1 (ACE)");
+  ap_status st = read_scalars(c, 0);
+  if (st) return st;
+  int64_t rows = which == 0 ? c->n : c->h_sc->n_precise;
+  if (h_rows) *h_rows = rows;
+  if (rows > 0 && (!d_cnt || !d_idx || !d_shift || cap <= 0)) return fail(c, AP_ERR_ARG, "null output or cap <= 0");
+  launch_export_rows(c, which, (int)rows, (int)cap, d_cnt, d_idx, d_shift, 0);
+  CK(cudaGetLastError());
+  CK(cudaDeviceSynchronize());
+  return AP_OK;
+}
+
+ap_status ap_classify(ap_ctx* c, int64_t n, const double* d_x, const uint8_t* d_changeable, double* d_lam,
+                      int32_t* d_precise_idx, int64_t* d_n_precise, void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->built || n != c->n) return fail(c, AP_ERR_STATE, "ap_classify needs ap_build_neighbors on the same atoms");
+  if (n > 0 && (!d_x || !d_lam || !d_precise_idx)) return fail(c, AP_ERR_ARG, "null argument");
+  cudaStream_t s = S(stream);
+  if (n == 0) {
+    if (d_n_precise) CK(cudaMemsetAsync(d_n_precise, 0, sizeof(int64_t), s));
+    CK(cudaMemsetAsync(&c->d_sc->n_precise, 0, sizeof(int), s));
+    return AP_OK;
+  }
+  launch_shadow(c, d_x, s);
+  classify_async(c, d_x, d_changeable, d_lam, d_precise_idx, d_n_precise, s);
+  CK(cudaGetLastError());
+  c->lam_ready = true;
+  return AP_OK;
+}
+
+ap_status ap_reset_lambda(ap_ctx* c) {
+  if (!c) return AP_ERR_ARG;
+  c->hist_started = false;
+  c->csp_pos = c->lam_pos = -1;
+  c->lam_ready = false;
+  c->md_ready = false;
+  return AP_OK;
+}
+
+ap_status ap_get_lambda_state(ap_ctx* c, double* d_csp, double* d_csp_avg, double* d_lam0, double* d_lam_min,
+                              double* d_lam_avg, void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->lam_ready) return fail(c, AP_ERR_STATE, "no classification yet");
+  cudaStream_t s = S(stream);
+  size_t b = sizeof(double) * (size_t)c->n;
+  if (b == 0) return AP_OK;
+  if (d_csp) CK(cudaMemcpyAsync(d_csp, c->d_csp, b, cudaMemcpyDeviceToDevice, s));
+  if (d_csp_avg) CK(cudaMemcpyAsync(d_csp_avg, c->d_csp_avg, b, cudaMemcpyDeviceToDevice, s));
+  if (d_lam0) CK(cudaMemcpyAsync(d_lam0, c->d_lam0, b, cudaMemcpyDeviceToDevice, s));
+  if (d_lam_min) CK(cudaMemcpyAsync(d_lam_min, c->d_lam_min, b, cudaMemcpyDeviceToDevice, s));
+  if (d_lam_avg) CK(cudaMemcpyAsync(d_lam_avg, c->d_lam_avg, b, cudaMemcpyDeviceToDevice, s));
+  return AP_OK;
+}
+
+ap_status ap_eval_eam(ap_ctx* c, int64_t n, const double* d_x, const double* d_lam, double* d_e_fast, double* d_f,
+                      void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->built || n != c->n) return fail(c, AP_ERR_STATE, "ap_eval_eam needs ap_build_neighbors on the same atoms");
+  if (n == 0) return AP_OK;
+  if (!d_x || !d_e_fast || !d_f) return fail(c, AP_ERR_ARG, "null argument");
+  cudaStream_t s = S(stream);
+  launch_shadow(c, d_x, s);
+  launch_eam(c, d_lam, d_e_fast, d_f, true, s);
+  CK(cudaGetLastError());
+  return AP_OK;
+}
+
+ap_status ap_eval_ace(ap_ctx* c, int64_t n, const double* d_x, const double* d_lam, const int32_t* d_precise_idx,
+                      const int64_t* d_n_precise, double* d_e_prec, double* d_f, void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->built || n != c->n) return fail(c, AP_ERR_STATE, "ap_eval_ace needs ap_build_neighbors on the same atoms");
+  if (n == 0) return AP_OK;
+  if (!d_x || !d_precise_idx || !d_n_precise || !d_e_prec) return fail(c, AP_ERR_ARG, "null argument");
+  cudaStream_t s = S(stream);
+  launch_shadow(c, d_x, s);
+  k_set_count<<<1, 1, 0, s>>>((const long long*)d_n_precise, (int)n, &c->d_sc->n_precise, &c->d_sc->n_precise64);
+  k_copy_queue<<<c->num_sms * 4, 256, 0, s>>>(d_precise_idx, &c->d_sc->n_precise, (int)n, c->d_precise, c->d_sc);
+  ap_status st = build_ace_checked(c, d_x, c->d_precise, s);
+  if (st) return st;
+  CK(cudaMemsetAsync(d_e_prec, 0, sizeof(double) * (size_t)n, s));
+  launch_ace(c, d_lam, c->d_precise, d_e_prec, d_f != nullptr, s);
+  if (d_f) launch_ace_finalize(c, d_f, s);
+  CK(cudaGetLastError());
+  return AP_OK;
+}
+
+ap_status ap_blend_forces(ap_ctx* c, int64_t n, const double* d_lam, const double* d_e_fast, const double* d_e_prec,
+                          double* d_e_atom, double* d_e_total, void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (n != c->n) return fail(c, AP_ERR_STATE, "n differs from the last neighbour build");
+  if (!d_e_fast || !d_e_total) return fail(c, AP_ERR_ARG, "null argument");
+  cudaStream_t s = S(stream);
+  launch_blend(c, d_lam, d_e_fast, d_e_prec, nullptr, d_e_atom, d_e_total, s);
+  CK(cudaGetLastError());
+  return AP_OK;
+}
+
+ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, const double* d_mass,
+                  const uint8_t* d_fixed, double* d_lam, int64_t nsteps, ap_step_stats* h_stats, void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (nsteps < 0) return fail(c, AP_ERR_ARG, "nsteps < 0");
+  if (!c->n_sys || n != c->n) return fail(c, AP_ERR_STATE, "ap_step needs ap_build_neighbors on the same atoms");
+  if (n == 0) return AP_OK;
+  if (!d_x || !d_v || !d_f || !d_mass || !d_lam) return fail(c, AP_ERR_ARG, "null argument");
+  if (!(c->cfg.dt > 0)) return fail(c, AP_ERR_ARG, "dt must be positive");
+  cudaStream_t s = S(stream);
+  const uint8_t* ch = nullptr;
+  if (d_fixed) {
+    k_changeable<<<(int)((n + 255) / 256), 256, 0, s>>>((int)n, d_fixed, c->d_changeable);
+    c->kernels += 1;
+    ch = c->d_changeable;
+  }
+  const ap_config& g = c->cfg;
+  ap_status st;
+  if (!c->md_ready) {
+    launch_wrap_positions(c, d_x, s);
+    st = build_checked(c, d_x, nullptr, s);
+    if (st) return st;
+    if (c->restart_pending) {
+      queue_from_lambda(c, s);
+      c->restart_pending = false;
+    } else {
+      classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s);
+    }
+    st = build_ace_checked(c, d_x, c->d_precise, s);
+    if (st) return st;
+    CK(cudaMemsetAsync(c->d_eprec, 0, sizeof(double) * (size_t)n, s));
+    launch_eam(c, c->d_lam_int, c->d_efast, d_f, false, s);
+    launch_ace(c, c->d_lam_int, c->d_precise, c->d_eprec, true, s);
+    launch_ace_finalize(c, d_f, s);
+    if (g.indenter_on) launch_indenter(c, d_x, d_f, c->step * g.dt, s);
+    c->lam_ready = true;
+    c->md_ready = true;
+  }
+  st = clear_err(c, s);
+  if (st) return st;
+  const float skin_lim2 = (float)(0.25 * g.skin * g.skin);
+  for (int64_t k = 0; k < nsteps; ++k) {
+    c->step++;
+    {
+      PhaseTimer t(c, s, AP_PHASE_OTHER);
+      launch_vv_first(c, d_x, d_v, d_f, d_mass, d_fixed, s);
+    }
+    if (c->step % g.lambda_every == 0) {
+      {
+        PhaseTimer t(c, s, AP_PHASE_NEIGHBORS);
+        k_check_skin<<<1, 1, 0, s>>>(c->d_sc, skin_lim2);
+        c->kernels += 1;
+        launch_wrap_positions(c, d_x, s);
+        build_async(c, d_x, nullptr, s);
+      }
+      {
+        PhaseTimer t(c, s, AP_PHASE_CLASSIFY);
+        classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s);
+        launch_build_ace(c, d_x, c->d_precise, &c->d_sc->n_precise, s);
+      }
+    } else {
+      PhaseTimer t(c, s, AP_PHASE_NEIGHBORS);
+      launch_shadow(c, d_x, s);
+    }
+    {
+      PhaseTimer t(c, s, AP_PHASE_EAM);
+      launch_eam(c, c->d_lam_int, c->d_efast, d_f, false, s);
+    }
+    {
+      PhaseTimer t(c, s, AP_PHASE_ACE);
+      CK(cudaMemsetAsync(c->d_eprec, 0, sizeof(double) * (size_t)n, s));
+      launch_ace(c, c->d_lam_int, c->d_precise, c->d_eprec, true, s);
+    }
+    {
+      PhaseTimer t(c, s, AP_PHASE_OTHER);
+      launch_ace_finalize(c, d_f, s);
+      if (g.indenter_on) launch_indenter(c, d_x, d_f, c->step * g.dt, s);
+      launch_vv_second(c, d_v, d_f, d_mass, d_fixed, s);
+    }
+  }
+  {
+    PhaseTimer t(c, s, AP_PHASE_OTHER);
+    k_check_skin<<<1, 1, 0, s>>>(c->d_sc, skin_lim2);
+    c->kernels += 1;
+    launch_blend(c, c->d_lam_int, c->d_efast, c->d_eprec, g.indenter_on ? c->d_eext : nullptr, c->d_eatom,
+                 &c->d_sc->e_total, s);
+    launch_kinetic(c, d_v, d_mass, &c->d_sc->e_kin, s);
+  }
+  CK(cudaMemcpyAsync(d_lam, c->d_lam_int, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaGetLastError());
+  st = read_scalars(c, s);
+  if (st) return st;
+  collect_profile(c);
+  if (h_stats) {
+    h_stats->step = c->step;
+    h_stats->n_precise = c->h_sc->n_precise;
+    h_stats->n_detected = c->h_sc->n_detected;
+    h_stats->rebuilds = c->rebuilds;
+    h_stats->e_pot = c->h_sc->e_total;
+    h_stats->e_kin = c->h_sc->e_kin;
+    float d2;
+    std::memcpy(&d2, &c->h_sc->max_disp2_bits, sizeof(float));
+    h_stats->max_disp = std::sqrt((double)d2);
+    h_stats->error_bits = c->h_sc->err;
+  }
+  return check_err_bits(c);
+}
+
+ap_status ap_profile_enable(ap_ctx* c, int32_t on) {
+  if (!c) return AP_ERR_ARG;
+  c->prof_on = on != 0;
+  for (int p = 0; p < AP_NUM_PHASES; ++p) {
+    c->prof_ms[p] = 0.0;
+    c->prof_calls[p] = 0;
+  }
+  c->ev_pairs_phase.clear();
+  c->ev_used = 0;
+  c->kernels = 0;
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemset(&c->d_sc->ace_pairs, 0, 2 * sizeof(unsigned long long)));
+  c->h_sc->ace_pairs = c->h_sc->ace_atoms = 0;
+  return AP_OK;
+}
+
+ap_status ap_profile_read(ap_ctx* c, double* h_ms, int64_t* h_calls, int64_t* h_kernels, int64_t* h_ace_pairs,
+                          int64_t* h_ace_atoms) {
+  if (!c) return AP_ERR_ARG;
+  for (int p = 0; p < AP_NUM_PHASES; ++p) {
+    if (h_ms) h_ms[p] = c->prof_ms[p];
+    if (h_calls) h_calls[p] = c->prof_calls[p];
+  }
+  if (h_kernels) *h_kernels = c->kernels;
+  if (h_ace_pairs) *h_ace_pairs = (int64_t)c->h_sc->ace_pairs;
+  if (h_ace_atoms) *h_ace_atoms = (int64_t)c->h_sc->ace_atoms;
+  return AP_OK;
+}
+
+ap_status ap_state_export(ap_ctx* c, void* h_buf, size_t* h_len) {
+  if (!c || !h_len) return AP_ERR_ARG;
+  const size_t n = (size_t)c->n;
+  const size_t hdr = 8 * sizeof(int64_t);
+  const size_t body = sizeof(double) * n * ((size_t)c->cfg.n_csp_avg + c->cfg.n_lam_avg + 2);
+  if (!h_buf) {
+    *h_len = hdr + body;
+    return AP_OK;
+  }
+  if (*h_len < hdr + body) return fail(c, AP_ERR_ARG, "buffer too small");
+  CK(cudaDeviceSynchronize());
+  int64_t* h = (int64_t*)h_buf;
+  h[0] = 0x41505354;  // "APST"
+  h[1] = (int64_t)n;
+  h[2] = c->cfg.n_csp_avg;
+  h[3] = c->cfg.n_lam_avg;
+  h[4] = c->csp_pos;
+  h[5] = c->lam_pos;
+  h[6] = c->hist_started ? 1 : 0;
+  h[7] = c->step;
+  char* p = (char*)h_buf + hdr;
+  if (n) {
+    CK(cudaMemcpy(p, c->d_csp_hist, sizeof(double) * n * c->cfg.n_csp_avg, cudaMemcpyDeviceToHost));
+    p += sizeof(double) * n * c->cfg.n_csp_avg;
+    CK(cudaMemcpy(p, c->d_lam_hist, sizeof(double) * n * c->cfg.n_lam_avg, cudaMemcpyDeviceToHost));
+    p += sizeof(double) * n * c->cfg.n_lam_avg;
+    CK(cudaMemcpy(p, c->d_lam_prev, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    p += sizeof(double) * n;
+    CK(cudaMemcpy(p, c->d_lam_int, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  }
+  *h_len = hdr + body;
+  return AP_OK;
+}
+
+ap_status ap_state_import(ap_ctx* c, const void* h_buf, size_t h_len) {
+  if (!c || !h_buf) return AP_ERR_ARG;
+  const int64_t* h = (const int64_t*)h_buf;
+  const size_t hdr = 8 * sizeof(int64_t);
+  if (h_len < hdr || h[0] != 0x41505354) return fail(c, AP_ERR_ARG, "not an ap state buffer");
+  const size_t n = (size_t)h[1];
+  if ((int64_t)n != c->n) return fail(c, AP_ERR_STATE, "state was saved for a different atom count");
+  if (h[2] != c->cfg.n_csp_avg || h[3] != c->cfg.n_lam_avg) return fail(c, AP_ERR_ARG, "window sizes differ");
+  const size_t body = sizeof(double) * n * ((size_t)c->cfg.n_csp_avg + c->cfg.n_lam_avg + 2);
+  if (h_len < hdr + body) return fail(c, AP_ERR_ARG, "buffer too small");
+  c->csp_pos = (int)h[4];
+  c->lam_pos = (int)h[5];
+  c->hist_started = h[6] != 0;
+  c->step = h[7];
+  const char* p = (const char*)h_buf + hdr;
+  if (n) {
+    CK(cudaMemcpy(c->d_csp_hist, p, sizeof(double) * n * c->cfg.n_csp_avg, cudaMemcpyHostToDevice));
+    p += sizeof(double) * n * c->cfg.n_csp_avg;
+    CK(cudaMemcpy(c->d_lam_hist, p, sizeof(double) * n * c->cfg.n_lam_avg, cudaMemcpyHostToDevice));
+    p += sizeof(double) * n * c->cfg.n_lam_avg;
+    CK(cudaMemcpy(c->d_lam_prev, p, sizeof(double) * n, cudaMemcpyHostToDevice));
+    p += sizeof(double) * n;
+    CK(cudaMemcpy(c->d_lam_int, p, sizeof(double) * n, cudaMemcpyHostToDevice));
+  }
+  c->md_ready = false;
+  c->restart_pending = true;
+  return AP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,247 @@
+// Internal declarations of the GB300 adaptive-precision library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ap.h"
+
+namespace ap {
+
+// ------------------------------------------------------------------ geometry
+// One simulation cell.  Cells of the search grid have edge h[d] = L[d]/nc[d] >=
+// (largest list radius)/2, so every list needs a stencil half-width of 2 cells.
+struct SysInfo {
+  double lo[3];
+  double L[3];       // hi - lo, computed once on the host
+  double h[3];       // cell edge
+  float hf[3];       // FP32 copy of h
+  int nc[3];         // cells per dimension (<= 1023)
+  int periodic[3];
+  int cell_base;     // first global cell id of this system
+  int pad;
+};
+
+constexpr int kMaxCellsPerDim = 1023;
+constexpr int kStencil = 2;          // cell half-width of the EAM and ACE list stencils
+
+// Packed wrapped cell coordinates (10 bits each) carried in the shadow .w.
+__host__ __device__ inline int pack_cell(int cx, int cy, int cz) { return cx | (cy << 10) | (cz << 20); }
+__host__ __device__ inline int cell_x(int c) { return c & 1023; }
+__host__ __device__ inline int cell_y(int c) { return (c >> 10) & 1023; }
+__host__ __device__ inline int cell_z(int c) { return (c >> 20) & 1023; }
+
+// Stored per-entry cell offsets k (small boxes): 8 bits per component, biased by 128.
+__host__ __device__ inline int pack_off(int kx, int ky, int kz) { return (kx + 128) | ((ky + 128) << 8) | ((kz + 128) << 16); }
+__host__ __device__ inline int off_x(int p) { return (p & 255) - 128; }
+__host__ __device__ inline int off_y(int p) { return ((p >> 8) & 255) - 128; }
+__host__ __device__ inline int off_z(int p) { return ((p >> 16) & 255) - 128; }
+
+// Cell offset of a pair from the wrapped cells (valid when nc >= 2*kStencil+1 in
+// every periodic dimension, i.e. when offsets are not stored).
+__device__ inline int wrap_off(int dc, int nc, int periodic) {
+  if (periodic) {
+    if (dc > nc / 2) dc -= nc;
+    else if (dc < -(nc / 2)) dc += nc;
+  }
+  return dc;
+}
+
+// ------------------------------------------------------------------ error bits
+enum : int {
+  kErrCapacity = 1 << AP_ERR_CAPACITY,
+  kErrNonfinite = 1 << AP_ERR_NONFINITE,
+  kErrBox = 1 << AP_ERR_BOX,
+  kErrSkin = 1 << AP_ERR_SKIN,
+  kErrArg = 1 << AP_ERR_ARG,
+};
+
+// ------------------------------------------------------------------ device buffers
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+// Device-side scalars of one context.
+struct DevScalars {
+  int err;            // OR of error bits
+  int need_eam;       // largest EAM row count seen
+  int need_ace;       // largest ACE row count seen
+  int n_detected;     // |D|
+  int n_precise;      // |P| (int32 copy used by kernels)
+  int work_counter;   // persistent-kernel work counter
+  unsigned int max_disp2_bits;  // float bits of the largest squared displacement
+  int pad;
+  long long n_precise64;
+  double e_total;
+  double e_kin;
+  double e_ind;
+  unsigned long long ace_pairs;   // neighbour pairs within the ACE cutoff processed (cumulative)
+  unsigned long long ace_atoms;   // precise atoms processed by the ACE kernel (cumulative)
+};
+
+// ------------------------------------------------------------------ ACE tables
+struct AceTables {
+  int nb = 0;
+  std::vector<int> desc;         // nb * 7
+  std::vector<double> gaunt;     // 4*7*4*7*4*7
+  // Flattened product terms of E = sum_v c_v B_v, each t: coef * A[a1] * A[a2] * A[a3]
+  // (a2 = a3 = 255 for nu = 1 and a3 = 255 for nu = 2).
+  std::vector<int> term_idx;     // packed a1 | a2 << 8 | a3 << 16
+  std::vector<double> term_coef;
+  int n_terms = 0;
+};
+void build_ace_tables(const ap_config& cfg, AceTables& t);
+
+// ------------------------------------------------------------------ context
+}  // namespace ap
+
+struct ap_ctx {
+  ap_config cfg;
+  int device = 0;
+  std::string err_msg = "no error";
+  int64_t need = 0;
+  ap::AceTables ace;
+
+  // systems
+  int n_sys = 0;
+  std::vector<ap::SysInfo> h_sys;
+  std::vector<int64_t> h_offsets;
+  ap::SysInfo* d_sys = nullptr;
+  int* d_atom_sys = nullptr;     // null when n_sys == 1
+  int n_cells = 0;
+  bool stored_off = false;
+  int sten_spread[3] = {0, 0, 0};
+
+  // capacity
+  int64_t n_cap = 0;             // per-atom arrays sized for this many atoms
+  int64_t n = 0;                 // atoms of the last build
+  int cells_cap = 0;
+  int cap_eam = 0, cap_ace = 0;
+  bool built = false;
+  bool lam_ready = false;        // a classification exists for the current n
+  int64_t rebuilds = 0;
+
+  // per-atom state (device)
+  int* d_cell = nullptr;         // global cell id (wrapped)
+  int4* d_cunw = nullptr;        // unwrapped cell coords (x,y,z) + packed wrapped code (w)
+  int* d_cell_start = nullptr;   // [n_cells + 1]
+  int* d_cell_count = nullptr;   // [n_cells]
+  int* d_cell_atoms = nullptr;   // [n]
+  int* d_slot = nullptr;         // [n] slot inside cell
+  float4* d_sh32 = nullptr;      // FP32 cell-relative shadow
+  double4_32a* d_sh64 = nullptr;     // FP64 cell-relative shadow
+  double* d_xbuild = nullptr;    // [n][3] positions at the last build
+  int* d_nbr_eam = nullptr;      // [n][cap_eam]
+  int* d_off_eam = nullptr;      // [n][cap_eam] (stored offsets only)
+  int* d_cnt_eam = nullptr;      // [n]
+  int* d_nbr_ace = nullptr;      // [n][cap_ace] rows in queue order
+  int* d_off_ace = nullptr;
+  int* d_cnt_ace = nullptr;
+  int64_t ace_rows_cap = 0;
+
+  // lambda state (FP64)
+  double* d_csp = nullptr;       // sample
+  double* d_csp_avg = nullptr;
+  double* d_lam0 = nullptr;
+  double* d_lam_min = nullptr;
+  double* d_lam_avg = nullptr;
+  double* d_lam_prev = nullptr;
+  double* d_csp_hist = nullptr;  // [n_csp_avg][n]
+  double* d_lam_hist = nullptr;  // [n_lam_avg][n]
+  int csp_pos = -1, lam_pos = -1;
+  bool hist_started = false;
+  int* d_flag = nullptr;         // [n] compaction flags
+  int* d_scan = nullptr;         // [n + 1] scan output
+  int* d_detected = nullptr;     // [n] detected queue
+  int* d_precise = nullptr;      // [n] internal precise queue
+  double* d_lam_int = nullptr;   // [n] internal lambda (ap_step)
+
+  // potentials scratch
+  void* d_q = nullptr;           // [n] (lambda xi', lambda) as float2 or double2
+  double* d_xi = nullptr;        // [n] xi(rho)
+  float4* d_facc32 = nullptr;    // [n] ACE force accumulator (mixed)
+  double* d_facc64 = nullptr;    // [n][3] ACE force accumulator (FP64)
+  double* d_efast = nullptr;     // [n] internal (ap_step)
+  double* d_eprec = nullptr;     // [n] internal (ap_step)
+  double* d_eatom = nullptr;     // [n] internal (ap_step)
+  double* d_eext = nullptr;      // [n] indenter energy per atom (ap_step)
+  uint8_t* d_changeable = nullptr;  // [n] complement of the fixed mask (ap_step)
+  bool restart_pending = false;  // lambda state imported; next ap_step reuses it
+  int* d_term_idx = nullptr;
+  float* d_term_coef32 = nullptr;
+  double* d_term_coef64 = nullptr;
+  float* d_W32 = nullptr;        // [5][8][8]
+  double* d_W64 = nullptr;
+
+  // scan scratch
+  int* d_scan_tmp = nullptr;
+  size_t scan_tmp_cap = 0;
+  double* d_red = nullptr;       // reduction partials
+  int red_cap = 0;
+
+  ap::DevScalars* d_sc = nullptr;
+  ap::DevScalars* h_sc = nullptr;  // pinned mirror
+
+  // MD
+  int64_t step = 0;
+  bool md_ready = false;
+  int num_sms = 0;
+
+  // profiling (ap_profile_enable / ap_profile_read)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;   // reusable events
+  std::vector<std::pair<int, int>> ev_pairs_phase;  // (phase, index of start event)
+  int ev_used = 0;
+  double prof_ms[AP_NUM_PHASES] = {0, 0, 0, 0, 0};
+  int64_t prof_calls[AP_NUM_PHASES] = {0, 0, 0, 0, 0};
+  int64_t kernels = 0;                // kernels launched by ap_step since the last enable
+};
+
+namespace ap {
+
+// ------------------------------------------------------------------ launchers
+// scan.cu / k_neighbors.cu
+size_t scan_tmp_bytes(int n);
+// d_out has n+1 entries; returns the number of kernels launched
+int scan_exclusive(const int* d_in, int* d_out, int n, int* d_tmp, cudaStream_t s);
+void launch_bin(ap_ctx* c, const double* d_x, const int32_t* d_species, cudaStream_t s);
+void launch_cell_sort(ap_ctx* c, cudaStream_t s);
+void launch_shadow(ap_ctx* c, const double* d_x, cudaStream_t s);
+void launch_build_eam(ap_ctx* c, const double* d_x, cudaStream_t s);
+void launch_build_ace(ap_ctx* c, const double* d_x, const int* d_queue, const int* d_nq, cudaStream_t s);
+void launch_export_rows(ap_ctx* c, int which, int rows, int cap_out, int* d_cnt, int* d_idx, int* d_shift,
+                        cudaStream_t s);
+void launch_wrap_positions(ap_ctx* c, double* d_x, cudaStream_t s);
+
+// k_classify.cu
+void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s);
+void launch_lambda0(ap_ctx* c, const uint8_t* d_ch, cudaStream_t s);
+void launch_spread(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s);
+void launch_lambda_final(ap_ctx* c, const uint8_t* d_ch, double* d_lam, int* d_queue, int64_t* d_nq64,
+                         cudaStream_t s);
+
+// k_eam.cu
+void launch_eam(ap_ctx* c, const double* d_lam, double* d_e_fast, double* d_f, bool accumulate, cudaStream_t s);
+
+// k_ace.cu
+void upload_ace_tables(ap_ctx* c);
+void launch_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_prec, bool forces, cudaStream_t s);
+void launch_ace_finalize(ap_ctx* c, double* d_f, cudaStream_t s);
+
+// k_md.cu
+void launch_vv_first(ap_ctx* c, double* d_x, double* d_v, const double* d_f, const double* d_mass,
+                     const uint8_t* d_fixed, cudaStream_t s);
+void launch_vv_second(ap_ctx* c, double* d_v, const double* d_f, const double* d_mass, const uint8_t* d_fixed,
+                      cudaStream_t s);
+void launch_indenter(ap_ctx* c, const double* d_x, double* d_f, double t, cudaStream_t s);
+void launch_blend(ap_ctx* c, const double* d_lam, const double* d_ef, const double* d_ep, const double* d_e_ext,
+                  double* d_e_atom, double* d_e_total, cudaStream_t s);
+void launch_kinetic(ap_ctx* c, const double* d_v, const double* d_mass, double* d_out, cudaStream_t s);
+void launch_fill_lambda(ap_ctx* c, double* d_lam, double value, cudaStream_t s);
+
+}  // namespace ap

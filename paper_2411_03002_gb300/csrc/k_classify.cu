@@ -1,0 +1,464 @@
+// Precision classification (Appendix A and B): centro-symmetry parameter,
+// moving averages, lambda_0, lambda_min spread, minimum-step hysteresis and the
+// compacted precise-atom work queue.  Every value that decides a set is computed
+// in FP64 with explicit round-to-nearest operations in the order of the
+// definitions, so the detected and precise sets are reproducible bit for bit.
+// FP32 is used only to pick candidates, with a guard band and an exact fallback.
+#include "ap_internal.cuh"
+
+namespace ap {
+
+namespace {
+
+constexpr float kBand = 1e-3f;     // FP32 guard band (A^2) on squared lengths
+constexpr int kNN = 12;            // N nearest neighbours of FCC (N_buffer = 0)
+constexpr int kHalf = kNN / 2;
+
+__device__ inline const SysInfo& sys_of(const SysInfo* sys, const int* atom_sys, int i) {
+  return sys[atom_sys ? atom_sys[i] : 0];
+}
+__device__ inline int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// f_cut of Appendix B in FP64 with the oracle's operation order.
+__device__ inline double fcut_exact(double x, int mode) {
+  if (x < 0.0) return 1.0;
+  if (x > 1.0) return 0.0;
+  double t = x;
+  if (mode == 1) t = __dsub_rn(__dmul_rn(2.0, x), 1.0);
+  double t2 = __dmul_rn(t, t);
+  double t3 = __dmul_rn(t2, t);
+  double t5 = __dmul_rn(t3, t2);
+  double p = __dsub_rn(__dadd_rn(__dsub_rn(1.0, __dmul_rn(1.875, t)), __dmul_rn(1.25, t3)), __dmul_rn(0.375, t5));
+  if (mode == 1) p = __dmul_rn(0.5, p);
+  return p;
+}
+
+// Cell offset k of a row entry.
+__device__ inline void entry_offset(const int* off, size_t e, const SysInfo& S, int wi, int wj, int k[3]) {
+  if (off) {
+    int p = off[e];
+    k[0] = off_x(p);
+    k[1] = off_y(p);
+    k[2] = off_z(p);
+  } else {
+    k[0] = wrap_off(cell_x(wj) - cell_x(wi), S.nc[0], S.periodic[0]);
+    k[1] = wrap_off(cell_y(wj) - cell_y(wi), S.nc[1], S.periodic[1]);
+    k[2] = wrap_off(cell_z(wj) - cell_z(wi), S.nc[2], S.periodic[2]);
+  }
+}
+
+// Exact displacement (x_j + S L) - x_i for a row entry with cell offset k.
+__device__ inline void exact_disp(const double* __restrict__ x, const SysInfo& S, int i, int j, const int4& ci,
+                                  const int4& cj, const int k[3], double d[3]) {
+  int cu_i[3] = {ci.x, ci.y, ci.z}, cu_j[3] = {cj.x, cj.y, cj.z};
+  for (int a = 0; a < 3; ++a) {
+    int sd = S.periodic[a] ? (k[a] - (cu_j[a] - cu_i[a])) / S.nc[a] : 0;
+    double shifted = __dadd_rn(x[3 * j + a], __dmul_rn((double)sd, S.L[a]));
+    d[a] = __dsub_rn(shifted, x[3 * i + a]);
+  }
+}
+
+__device__ inline double norm2_exact(const double d[3]) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+// Candidate order (r^2, j, s) of the definition.
+__device__ inline bool cand_less(double ra, int ja, const int* sa, double rb, int jb, const int* sb) {
+  if (ra != rb) return ra < rb;
+  if (ja != jb) return ja < jb;
+  for (int a = 0; a < 3; ++a)
+    if (sa[a] != sb[a]) return sa[a] < sb[a];
+  return false;
+}
+
+__device__ inline void image_of(const SysInfo& S, const int4& ci, const int4& cj, const int k[3], int s[3]) {
+  int cu_i[3] = {ci.x, ci.y, ci.z}, cu_j[3] = {cj.x, cj.y, cj.z};
+  for (int a = 0; a < 3; ++a) s[a] = S.periodic[a] ? (k[a] - (cu_j[a] - cu_i[a])) / S.nc[a] : 0;
+}
+
+// ------------------------------------------------------------------ CSP
+__global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x, const uint8_t* __restrict__ ch,
+                                             const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
+                                             const float4* __restrict__ s32, const int4* __restrict__ cunw,
+                                             const int* __restrict__ nbr, const int* __restrict__ off,
+                                             const int* __restrict__ cnt, int cap, float rsf2, double rs2,
+                                             double* __restrict__ csp) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (ch && !ch[i]) {
+    csp[i] = 0.0;
+    return;
+  }
+  const SysInfo& S = sys_of(sys, atom_sys, i);
+  const float4 si = s32[i];
+  const int4 ci = cunw[i];
+  const int c = cnt[i];
+  const size_t row = (size_t)i * cap;
+
+  // 1. the 13 smallest FP32 r^2 among candidates inside r_search
+  float tr[kNN + 1];
+  int tq[kNN + 1];
+#pragma unroll
+  for (int a = 0; a <= kNN; ++a) {
+    tr[a] = INFINITY;
+    tq[a] = -1;
+  }
+  int n_in = 0;
+  for (int q = 0; q < c; ++q) {
+    int j = nbr[row + q];
+    float4 sj = s32[j];
+    int k[3];
+    entry_offset(off, row + q, S, ci.w, __float_as_int(sj.w), k);
+    float dx = (float)k[0] * S.hf[0] + sj.x - si.x;
+    float dy = (float)k[1] * S.hf[1] + sj.y - si.y;
+    float dz = (float)k[2] * S.hf[2] + sj.z - si.z;
+    float r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 > rsf2 + kBand) continue;
+    if (r2 >= rsf2 - kBand) {
+      double d[3];
+      exact_disp(x, S, i, j, ci, cunw[j], k, d);
+      if (!(norm2_exact(d) < rs2)) continue;
+    }
+    ++n_in;
+    if (r2 < tr[kNN]) {
+      int p = kNN;
+      while (p > 0 && tr[p - 1] > r2) {
+        tr[p] = tr[p - 1];
+        tq[p] = tq[p - 1];
+        --p;
+      }
+      tr[p] = r2;
+      tq[p] = q;
+    }
+  }
+  if (n_in < kNN) {
+    csp[i] = INFINITY;
+    return;
+  }
+  // 2. exact selection when the 12/13 boundary lies within the guard band
+  bool exact_sel = (n_in > kNN) && (tr[kNN] - tr[kNN - 1] <= 2.f * kBand);
+  if (exact_sel) {
+    double br[kNN];
+    int bj[kNN], bs[kNN][3], bq[kNN];
+    for (int a = 0; a < kNN; ++a) {
+      br[a] = INFINITY;
+      bj[a] = 0x7fffffff;
+      bq[a] = -1;
+      bs[a][0] = bs[a][1] = bs[a][2] = 0x7fffffff;
+    }
+    for (int q = 0; q < c; ++q) {
+      int j = nbr[row + q];
+      int4 cj = cunw[j];
+      int k[3];
+      entry_offset(off, row + q, S, ci.w, cj.w, k);
+      double d[3];
+      exact_disp(x, S, i, j, ci, cj, k, d);
+      double r2 = norm2_exact(d);
+      if (!(r2 < rs2)) continue;
+      int s[3];
+      image_of(S, ci, cj, k, s);
+      if (!cand_less(r2, j, s, br[kNN - 1], bj[kNN - 1], bs[kNN - 1])) continue;
+      int p = kNN - 1;
+      while (p > 0 && cand_less(r2, j, s, br[p - 1], bj[p - 1], bs[p - 1])) {
+        br[p] = br[p - 1];
+        bj[p] = bj[p - 1];
+        bq[p] = bq[p - 1];
+        bs[p][0] = bs[p - 1][0];
+        bs[p][1] = bs[p - 1][1];
+        bs[p][2] = bs[p - 1][2];
+        --p;
+      }
+      br[p] = r2;
+      bj[p] = j;
+      bq[p] = q;
+      bs[p][0] = s[0];
+      bs[p][1] = s[1];
+      bs[p][2] = s[2];
+    }
+    for (int a = 0; a < kNN; ++a) tq[a] = bq[a];
+  }
+  // 3. vectors of the 12 (FP32 for the pair selection)
+  float vx[kNN], vy[kNN], vz[kNN];
+  for (int a = 0; a < kNN; ++a) {
+    int j = nbr[row + tq[a]];
+    float4 sj = s32[j];
+    int k[3];
+    entry_offset(off, row + tq[a], S, ci.w, __float_as_int(sj.w), k);
+    vx[a] = (float)k[0] * S.hf[0] + sj.x - si.x;
+    vy[a] = (float)k[1] * S.hf[1] + sj.y - si.y;
+    vz[a] = (float)k[2] * S.hf[2] + sj.z - si.z;
+  }
+  // 4. the 7 smallest FP32 pair values |r_a + r_b|^2
+  float pv[kHalf + 1];
+  int pc[kHalf + 1];
+  for (int a = 0; a <= kHalf; ++a) {
+    pv[a] = INFINITY;
+    pc[a] = -1;
+  }
+  for (int a = 0; a < kNN; ++a)
+    for (int b = a + 1; b < kNN; ++b) {
+      float sx = vx[a] + vx[b], sy = vy[a] + vy[b], sz = vz[a] + vz[b];
+      float v = sx * sx + sy * sy + sz * sz;
+      if (v < pv[kHalf]) {
+        int p = kHalf;
+        while (p > 0 && pv[p - 1] > v) {
+          pv[p] = pv[p - 1];
+          pc[p] = pc[p - 1];
+          --p;
+        }
+        pv[p] = v;
+        pc[p] = a * 16 + b;
+      }
+    }
+  // exact vectors of the 12 (FP64) computed on demand
+  auto exact_vec = [&](int a, double d[3]) {
+    int q = tq[a];
+    int j = nbr[row + q];
+    int4 cj = cunw[j];
+    int k[3];
+    entry_offset(off, row + q, S, ci.w, cj.w, k);
+    exact_disp(x, S, i, j, ci, cj, k, d);
+  };
+  double chosen[kHalf];
+  if (pv[kHalf] - pv[kHalf - 1] > 2.f * kBand) {
+    for (int t = 0; t < kHalf; ++t) {
+      double da[3], db[3];
+      exact_vec(pc[t] >> 4, da);
+      exact_vec(pc[t] & 15, db);
+      double s3[3] = {__dadd_rn(da[0], db[0]), __dadd_rn(da[1], db[1]), __dadd_rn(da[2], db[2])};
+      chosen[t] = norm2_exact(s3);
+    }
+  } else {
+    // all 66 in FP64, keep the 6 smallest
+    for (int t = 0; t < kHalf; ++t) chosen[t] = INFINITY;
+    double ex[kNN][3];
+    for (int a = 0; a < kNN; ++a) exact_vec(a, ex[a]);
+    for (int a = 0; a < kNN; ++a)
+      for (int b = a + 1; b < kNN; ++b) {
+        double s3[3] = {__dadd_rn(ex[a][0], ex[b][0]), __dadd_rn(ex[a][1], ex[b][1]), __dadd_rn(ex[a][2], ex[b][2])};
+        double v = norm2_exact(s3);
+        if (v < chosen[kHalf - 1]) {
+          int p = kHalf - 1;
+          while (p > 0 && chosen[p - 1] > v) {
+            chosen[p] = chosen[p - 1];
+            --p;
+          }
+          chosen[p] = v;
+        }
+      }
+  }
+  // 5. ascending sum of the six values
+  for (int a = 1; a < kHalf; ++a) {
+    double t = chosen[a];
+    int p = a - 1;
+    while (p >= 0 && chosen[p] > t) {
+      chosen[p + 1] = chosen[p];
+      --p;
+    }
+    chosen[p + 1] = t;
+  }
+  double sum = chosen[0];
+  for (int a = 1; a < kHalf; ++a) sum = __dadd_rn(sum, chosen[a]);
+  csp[i] = sum;
+}
+
+// Canonical moving average over a ring buffer [ns][n]: oldest -> newest, then / ns.
+__device__ inline double ring_mean(const double* __restrict__ hist, int ns, int newest, size_t n, int i) {
+  int q0 = (newest + 1) % ns;
+  double s = hist[(size_t)q0 * n + i];
+  for (int q = 1; q < ns; ++q) s = __dadd_rn(s, hist[(size_t)((newest + 1 + q) % ns) * n + i]);
+  return __ddiv_rn(s, (double)ns);
+}
+
+// Push CSP, average, lambda_0 (Eq. lambda_1_i), detected flag, lambda_min init.
+__global__ void k_lambda0(int n, const uint8_t* __restrict__ ch, const double* __restrict__ csp,
+                          double* __restrict__ hist, int ns, int pos, int fill, double csp_lo, double csp_hi,
+                          int mode, double* __restrict__ csp_avg, double* __restrict__ lam0,
+                          double* __restrict__ lam_min, int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double c = csp[i];
+  if (fill) {
+    for (int q = 0; q < ns; ++q) hist[(size_t)q * n + i] = c;
+  } else {
+    hist[(size_t)pos * n + i] = c;
+  }
+  double avg = ring_mean(hist, ns, pos, (size_t)n, i);
+  csp_avg[i] = avg;
+  bool changeable = !ch || ch[i];
+  double l0 = 1.0;
+  if (changeable) {
+    double y = __ddiv_rn(__dsub_rn(csp_hi, avg), __dsub_rn(csp_hi, csp_lo));
+    l0 = __dsub_rn(1.0, fcut_exact(y, mode));
+  }
+  lam0[i] = l0;
+  lam_min[i] = changeable ? l0 : 1.0;
+  flag[i] = (changeable && l0 < 1.0) ? 1 : 0;
+}
+
+__global__ void k_compact(int n, const int* __restrict__ flag, const int* __restrict__ scan, int* __restrict__ out,
+                          int* __restrict__ count32, long long* __restrict__ count64) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) out[scan[i]] = i;
+  if (i == 0) {
+    int tot = scan[n];
+    if (count32) *count32 = tot;
+    if (count64) *count64 = tot;
+  }
+}
+
+// lambda_min spread (Eq. lambda_2_i): one warp per detected atom i scans the cells
+// within r_hi; for every image j with r_ij < r_hi it lowers lambda_min,j to
+// 1 - (1 - lambda_0,i) f_cut((r_ij - r_lo)/(r_hi - r_lo)) by a 64-bit atomicMin on
+// the bit pattern (order-free and exact for non-negative doubles).
+__global__ void __launch_bounds__(256) k_spread(const int* __restrict__ det, const int* __restrict__ n_det,
+                                                const double* __restrict__ x, const uint8_t* __restrict__ ch,
+                                                const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
+                                                const float4* __restrict__ s32, const int4* __restrict__ cunw,
+                                                const int* __restrict__ cstart, const int* __restrict__ catoms,
+                                                const double* __restrict__ lam0, double r_lo, double r_hi, int mode,
+                                                int sx, int sy, int sz, double* __restrict__ lam_min) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int m = *n_det;
+  const double rh2 = __dmul_rn(r_hi, r_hi);
+  const float rhf2 = (float)rh2;
+  const double width = __dsub_rn(r_hi, r_lo);
+  const int wx = 2 * sx + 1, wy = 2 * sy + 1, wz = 2 * sz + 1;
+  const int ncell = wx * wy * wz;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < m; w += warps) {
+    const int i = det[w];
+    const SysInfo& S = sys_of(sys, atom_sys, i);
+    const float4 si = s32[i];
+    const int4 ci = cunw[i];
+    const double one_minus = __dsub_rn(1.0, lam0[i]);
+    const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
+    for (int t = lane; t < ncell; t += 32) {
+      int dx = t % wx - sx;
+      int dy = (t / wx) % wy - sy;
+      int dz = t / (wx * wy) - sz;
+      int tc[3] = {cw[0] + dx, cw[1] + dy, cw[2] + dz};
+      int img[3] = {0, 0, 0};
+      bool skip = false;
+      for (int a = 0; a < 3; ++a) {
+        if (S.periodic[a]) {
+          img[a] = floor_div(tc[a], S.nc[a]);
+          tc[a] -= img[a] * S.nc[a];
+        } else if (tc[a] < 0 || tc[a] >= S.nc[a]) {
+          skip = true;
+        }
+      }
+      if (skip) continue;
+      float gx = fmaxf(0.f, fmaxf((float)dx * S.hf[0] - si.x, si.x - (float)(dx + 1) * S.hf[0]));
+      float gy = fmaxf(0.f, fmaxf((float)dy * S.hf[1] - si.y, si.y - (float)(dy + 1) * S.hf[1]));
+      float gz = fmaxf(0.f, fmaxf((float)dz * S.hf[2] - si.z, si.z - (float)(dz + 1) * S.hf[2]));
+      if (gx * gx + gy * gy + gz * gz > rhf2 + kBand) continue;
+      int cid = S.cell_base + (tc[2] * S.nc[1] + tc[1]) * S.nc[0] + tc[0];
+      int b = cstart[cid], e = cstart[cid + 1];
+      const float ox = (float)dx * S.hf[0] - si.x;
+      const float oy = (float)dy * S.hf[1] - si.y;
+      const float oz = (float)dz * S.hf[2] - si.z;
+      for (int a = b; a < e; ++a) {
+        int j = catoms[a];
+        if (j == i && dx == 0 && dy == 0 && dz == 0) continue;
+        if (ch && !ch[j]) continue;
+        float4 sj = s32[j];
+        float ddx = ox + sj.x, ddy = oy + sj.y, ddz = oz + sj.z;
+        float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
+        if (r2f > rhf2 + kBand) continue;
+        int4 cj = cunw[j];
+        double d[3];
+        // image relative to the input positions: S = img + nwrap_i - nwrap_j
+        int cu_i[3] = {ci.x, ci.y, ci.z}, cu_j[3] = {cj.x, cj.y, cj.z};
+        int cwi[3] = {cw[0], cw[1], cw[2]}, cwj[3] = {cell_x(cj.w), cell_y(cj.w), cell_z(cj.w)};
+        for (int q = 0; q < 3; ++q) {
+          int sd = 0;
+          if (S.periodic[q]) sd = img[q] + (cu_i[q] - cwi[q]) / S.nc[q] - (cu_j[q] - cwj[q]) / S.nc[q];
+          double shifted = __dadd_rn(x[3 * j + q], __dmul_rn((double)sd, S.L[q]));
+          d[q] = __dsub_rn(shifted, x[3 * i + q]);
+        }
+        double r2 = norm2_exact(d);
+        if (!(r2 < rh2)) continue;
+        double r = __dsqrt_rn(r2);
+        double f = fcut_exact(__ddiv_rn(__dsub_rn(r, r_lo), width), mode);
+        double v = __dsub_rn(1.0, __dmul_rn(one_minus, f));
+        atomicMin((unsigned long long*)&lam_min[j], (unsigned long long)__double_as_longlong(v));
+      }
+    }
+  }
+}
+
+// Push lambda_min, average (Eq. lambda_3_i), hysteresis (Eq. lambda_4_i), flag precise.
+__global__ void k_lambda_final(int n, const uint8_t* __restrict__ ch, const double* __restrict__ lam_min,
+                               double* __restrict__ hist, int ns, int pos, int fill, double dlam_min,
+                               double* __restrict__ lam_avg, double* __restrict__ lam_prev, double* __restrict__ lam,
+                               int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double lm = lam_min[i];
+  if (fill) {
+    for (int q = 0; q < ns; ++q) hist[(size_t)q * n + i] = lm;
+  } else {
+    hist[(size_t)pos * n + i] = lm;
+  }
+  double avg = ring_mean(hist, ns, pos, (size_t)n, i);
+  lam_avg[i] = avg;
+  double prev = fill ? avg : lam_prev[i];
+  bool take = fabs(__dsub_rn(avg, prev)) >= dlam_min || avg == 0.0 || avg == 1.0;
+  double l = take ? avg : prev;
+  if (ch && !ch[i]) l = 1.0;
+  lam_prev[i] = l;
+  lam[i] = l;
+  flag[i] = l < 1.0 ? 1 : 0;
+}
+
+inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s) {
+  double r = c->cfg.eam_rc + c->cfg.skin;
+  double rs2 = r * r;
+  k_csp<<<nblk(c->n, 128), 128, 0, s>>>((int)c->n, d_x, d_ch, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
+                                        c->d_nbr_eam, c->stored_off ? c->d_off_eam : nullptr, c->d_cnt_eam,
+                                        c->cap_eam, (float)rs2, rs2, c->d_csp);
+  c->kernels += 1;
+}
+
+void launch_lambda0(ap_ctx* c, const uint8_t* d_ch, cudaStream_t s) {
+  int ns = c->cfg.n_csp_avg;
+  int fill = c->hist_started ? 0 : 1;
+  int pos = fill ? 0 : (c->csp_pos + 1) % ns;
+  c->csp_pos = pos;
+  k_lambda0<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_ch, c->d_csp, c->d_csp_hist, ns, pos, fill, c->cfg.csp_lo,
+                                            c->cfg.csp_hi, c->cfg.fcut_mode, c->d_csp_avg, c->d_lam0, c->d_lam_min,
+                                            c->d_flag);
+  c->kernels += 2 + scan_exclusive(c->d_flag, c->d_scan, (int)c->n, c->d_scan_tmp, s);
+  k_compact<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, c->d_flag, c->d_scan, c->d_detected, &c->d_sc->n_detected,
+                                            nullptr);
+}
+
+void launch_spread(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s) {
+  int grid = c->num_sms * 8;
+  k_spread<<<grid, 256, 0, s>>>(c->d_detected, &c->d_sc->n_detected, d_x, d_ch, c->d_sys, c->d_atom_sys, c->d_sh32,
+                                c->d_cunw, c->d_cell_start, c->d_cell_atoms, c->d_lam0, c->cfg.r_lo, c->cfg.r_hi,
+                                c->cfg.fcut_mode, c->sten_spread[0], c->sten_spread[1], c->sten_spread[2],
+                                c->d_lam_min);
+  c->kernels += 1;
+}
+
+void launch_lambda_final(ap_ctx* c, const uint8_t* d_ch, double* d_lam, int* d_queue, int64_t* d_nq64,
+                         cudaStream_t s) {
+  int ns = c->cfg.n_lam_avg;
+  int fill = c->hist_started ? 0 : 1;
+  int pos = fill ? 0 : (c->lam_pos + 1) % ns;
+  c->lam_pos = pos;
+  c->hist_started = true;
+  k_lambda_final<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_ch, c->d_lam_min, c->d_lam_hist, ns, pos, fill,
+                                                 c->cfg.dlam_min, c->d_lam_avg, c->d_lam_prev, d_lam, c->d_flag);
+  c->kernels += 2 + scan_exclusive(c->d_flag, c->d_scan, (int)c->n, c->d_scan_tmp, s);
+  k_compact<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, c->d_flag, c->d_scan, d_queue, &c->d_sc->n_precise,
+                                            (long long*)(d_nq64 ? d_nq64 : (int64_t*)&c->d_sc->n_precise64));
+}
+
+}  // namespace ap

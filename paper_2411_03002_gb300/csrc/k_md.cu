@@ -1,0 +1,172 @@
+// Velocity Verlet with the lambda step (Eq. vv), the external indenter, the
+// blended energy E_i = lambda_i E_i^(f) + (1 - lambda_i) E_i^(p) (Eq. energy_hyb)
+// and fixed-order FP64 reductions (bitwise reproducible for a given n).
+#include "ap_internal.cuh"
+
+namespace ap {
+
+namespace {
+
+// 1 eV/(A amu) in A/fs^2, from 1 eV = 1.602176634e-19 J and 1 amu = 1.66053906660e-27 kg
+constexpr double kAcc = 1.602176634e-19 / 1.66053906660e-27 * 1e-20 / 1e-10;
+constexpr int kRedBlocks = 512;
+constexpr int kRedThreads = 256;
+
+__global__ void k_vv_first(int n, double* __restrict__ x, double* __restrict__ v, const double* __restrict__ f,
+                           const double* __restrict__ mass, const uint8_t* __restrict__ fixed, double dt,
+                           const double* __restrict__ xb, DevScalars* sc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float d2 = 0.f;
+  if (i < n) {
+    if (fixed && fixed[i]) {
+      v[3 * i + 0] = v[3 * i + 1] = v[3 * i + 2] = 0.0;
+    } else {
+      double s = 0.5 * dt * kAcc / mass[i];
+      bool bad = false;
+      double dd = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        double vv = v[3 * i + a] + s * f[3 * i + a];
+        double xx = x[3 * i + a] + dt * vv;
+        v[3 * i + a] = vv;
+        x[3 * i + a] = xx;
+        bad |= !isfinite(xx);
+        double e = xx - xb[3 * i + a];
+        dd += e * e;
+      }
+      if (bad) atomicOr(&sc->err, kErrNonfinite);
+      d2 = (float)dd;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+  if ((threadIdx.x & 31) == 0 && d2 > 0.f) atomicMax(&sc->max_disp2_bits, __float_as_uint(d2));
+}
+
+__global__ void k_vv_second(int n, double* __restrict__ v, const double* __restrict__ f,
+                            const double* __restrict__ mass, const uint8_t* __restrict__ fixed, double dt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (fixed && fixed[i]) {
+    v[3 * i + 0] = v[3 * i + 1] = v[3 * i + 2] = 0.0;
+    return;
+  }
+  double s = 0.5 * dt * kAcc / mass[i];
+  for (int a = 0; a < 3; ++a) v[3 * i + a] += s * f[3 * i + a];
+}
+
+// Spherical indenter: F = k (R - r)^2 (x - c)/r, E = k (R - r)^3 / 3 for r < R.
+__global__ void k_indenter(int n, const double* __restrict__ x, double* __restrict__ f, double* __restrict__ e_ext,
+                           double cx, double cy, double cz, double R, double k) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double dx = x[3 * i] - cx, dy = x[3 * i + 1] - cy, dz = x[3 * i + 2] - cz;
+  double r2 = dx * dx + dy * dy + dz * dz;
+  double e = 0.0;
+  if (r2 < R * R && r2 > 0.0) {
+    double r = sqrt(r2);
+    double g = k * (R - r) * (R - r) / r;
+    f[3 * i + 0] += g * dx;
+    f[3 * i + 1] += g * dy;
+    f[3 * i + 2] += g * dz;
+    e = k * (R - r) * (R - r) * (R - r) / 3.0;
+  }
+  if (e_ext) e_ext[i] = e;
+}
+
+template <typename F>
+__device__ inline void block_reduce_store(double v, double* out) {
+  __shared__ double sh[kRedThreads];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// Fixed partition: block b owns [b*chunk, (b+1)*chunk); thread t sums a strided
+// sequence in order; the tree order is fixed.  Same n -> same bits.
+__global__ void k_blend_partial(int n, const double* __restrict__ lam, const double* __restrict__ ef,
+                                const double* __restrict__ ep, const double* __restrict__ e_ext,
+                                double* __restrict__ e_atom, double* __restrict__ part) {
+  int chunk = (n + gridDim.x - 1) / gridDim.x;
+  int b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+  double s = 0.0;
+  for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    double l = lam ? lam[i] : 1.0;
+    double e = l * ef[i] + (1.0 - l) * (ep ? ep[i] : 0.0);
+    if (e_atom) e_atom[i] = e;
+    if (e_ext) e += e_ext[i];
+    s += e;
+  }
+  block_reduce_store<double>(s, &part[blockIdx.x]);
+}
+
+__global__ void k_kin_partial(int n, const double* __restrict__ v, const double* __restrict__ mass,
+                              double* __restrict__ part) {
+  int chunk = (n + gridDim.x - 1) / gridDim.x;
+  int b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+  double s = 0.0;
+  for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    double vv = v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2];
+    s += 0.5 * mass[i] * vv / kAcc;
+  }
+  block_reduce_store<double>(s, &part[blockIdx.x]);
+}
+
+__global__ void k_final_sum(int m, const double* __restrict__ part, double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s += part[i];
+  block_reduce_store<double>(s, out);
+}
+
+__global__ void k_fill(int n, double* __restrict__ a, double v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_vv_first(ap_ctx* c, double* d_x, double* d_v, const double* d_f, const double* d_mass,
+                     const uint8_t* d_fixed, cudaStream_t s) {
+  k_vv_first<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, d_v, d_f, d_mass, d_fixed, c->cfg.dt, c->d_xbuild,
+                                             c->d_sc);
+  c->kernels += 1;
+}
+
+void launch_vv_second(ap_ctx* c, double* d_v, const double* d_f, const double* d_mass, const uint8_t* d_fixed,
+                      cudaStream_t s) {
+  k_vv_second<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_v, d_f, d_mass, d_fixed, c->cfg.dt);
+  c->kernels += 1;
+}
+
+void launch_indenter(ap_ctx* c, const double* d_x, double* d_f, double t, cudaStream_t s) {
+  const ap_config& g = c->cfg;
+  k_indenter<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, d_f, c->d_eext, g.ind_c0[0] + g.ind_v[0] * t,
+                                             g.ind_c0[1] + g.ind_v[1] * t, g.ind_c0[2] + g.ind_v[2] * t, g.ind_R,
+                                             g.ind_k);
+  c->kernels += 1;
+}
+
+void launch_blend(ap_ctx* c, const double* d_lam, const double* d_ef, const double* d_ep, const double* d_e_ext,
+                  double* d_e_atom, double* d_e_total, cudaStream_t s) {
+  k_blend_partial<<<kRedBlocks, kRedThreads, 0, s>>>((int)c->n, d_lam, d_ef, d_ep, d_e_ext, d_e_atom, c->d_red);
+  k_final_sum<<<1, kRedThreads, 0, s>>>(kRedBlocks, c->d_red, d_e_total);
+  c->kernels += 2;
+}
+
+void launch_kinetic(ap_ctx* c, const double* d_v, const double* d_mass, double* d_out, cudaStream_t s) {
+  k_kin_partial<<<kRedBlocks, kRedThreads, 0, s>>>((int)c->n, d_v, d_mass, c->d_red + kRedBlocks);
+  k_final_sum<<<1, kRedThreads, 0, s>>>(kRedBlocks, c->d_red + kRedBlocks, d_out);
+  c->kernels += 2;
+}
+
+void launch_fill_lambda(ap_ctx* c, double* d_lam, double value, cudaStream_t s) {
+  k_fill<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_lam, value);
+  c->kernels += 1;
+}
+
+}  // namespace ap

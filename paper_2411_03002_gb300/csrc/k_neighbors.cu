@@ -1,0 +1,410 @@
+// Cell list and neighbour rows (section 2.4: the per-domain neighbour search that
+// the paper delegates to LAMMPS).  Row i of a list holds every image (j, s) with
+// |x_j + s L - x_i|^2 < r_list^2, decided by that FP64 expression; an FP32
+// cell-relative pre-filter only skips candidates that are clearly in or out.
+#include "ap_internal.cuh"
+
+namespace ap {
+
+namespace {
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void k_scan_block(const int* __restrict__ in, int* __restrict__ out, int m, int n_in,
+                             int* __restrict__ bsum) {
+  __shared__ int ws[kScanThreads / 32];
+  const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  int v[kScanItems];
+  int tsum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int idx = base + k;
+    v[k] = (idx < n_in) ? in[idx] : 0;
+    tsum += v[k];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = (lane < kScanThreads / 32) ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kScanThreads / 32) ws[lane] = w;
+  }
+  __syncthreads();
+  int run = x - tsum + (wid > 0 ? ws[wid - 1] : 0);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int idx = base + k;
+    if (idx < m) out[idx] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = run;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int m, const int* __restrict__ offs) {
+  int b = blockIdx.x;
+  int add = offs[b];
+  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+    int idx = b * kScanTile + k;
+    if (idx < m) out[idx] += add;
+  }
+}
+
+int scan_rec(const int* in, int n_in, int* out, int m, int* tmp, cudaStream_t s) {
+  int nb = (m + kScanTile - 1) / kScanTile;
+  int k = 1;
+  k_scan_block<<<nb, kScanThreads, 0, s>>>(in, out, m, n_in, tmp);
+  if (nb > 1) {
+    int* offs = tmp + nb;
+    k += scan_rec(tmp, nb, offs, nb, tmp + 2 * nb, s);
+    k_scan_add<<<nb, 256, 0, s>>>(out, m, offs);
+    ++k;
+  }
+  return k;
+}
+
+__device__ inline int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+__device__ inline const SysInfo& sys_of(const SysInfo* sys, const int* atom_sys, int i) {
+  return sys[atom_sys ? atom_sys[i] : 0];
+}
+
+// ------------------------------------------------------------------ binning
+__global__ void k_bin(int n, const double* __restrict__ x, const int32_t* __restrict__ species,
+                      const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys, int* __restrict__ cell,
+                      int* __restrict__ slot, int4* __restrict__ cunw, int* __restrict__ cell_count,
+                      DevScalars* sc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const SysInfo& S = sys_of(sys, atom_sys, i);
+  int cw[3], cu[3];
+  int bad = 0;
+  if (species && species[i] != 0) bad |= kErrArg;
+  for (int d = 0; d < 3; ++d) {
+    double xv = x[3 * i + d];
+    if (!isfinite(xv)) {
+      bad |= kErrNonfinite;
+      cw[d] = 0;
+      cu[d] = 0;
+      continue;
+    }
+    double rel = xv - S.lo[d];
+    int nw = 0;
+    if (S.periodic[d]) {
+      nw = (int)floor(rel / S.L[d]);
+      rel = rel - (double)nw * S.L[d];
+    } else if (rel < 0.0 || rel >= S.L[d]) {
+      bad |= kErrBox;
+    }
+    int c = (int)floor(rel / S.h[d]);
+    c = c < 0 ? 0 : (c >= S.nc[d] ? S.nc[d] - 1 : c);
+    cw[d] = c;
+    cu[d] = c + nw * S.nc[d];
+  }
+  if (bad) atomicOr(&sc->err, bad);
+  int id = S.cell_base + (cw[2] * S.nc[1] + cw[1]) * S.nc[0] + cw[0];
+  cell[i] = id;
+  cunw[i] = make_int4(cu[0], cu[1], cu[2], pack_cell(cw[0], cw[1], cw[2]));
+  slot[i] = atomicAdd(&cell_count[id], 1);
+}
+
+__global__ void k_cell_scatter(int n, const int* __restrict__ cell, const int* __restrict__ slot,
+                               const int* __restrict__ start, int* __restrict__ atoms) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  atoms[start[cell[i]] + slot[i]] = i;
+}
+
+// Sort each cell's atoms by index so that rows come out in a deterministic order.
+__global__ void k_cell_sort(int n_cells, const int* __restrict__ start, int* __restrict__ atoms) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  int b = start[c], e = start[c + 1];
+  for (int a = b + 1; a < e; ++a) {
+    int t = atoms[a];
+    int p = a - 1;
+    while (p >= b && atoms[p] > t) {
+      atoms[p + 1] = atoms[p];
+      --p;
+    }
+    atoms[p + 1] = t;
+  }
+}
+
+// Cell-relative coordinates s = (x - lo) - c_unw h; w = packed wrapped cell.
+__global__ void k_shadow(int n, const double* __restrict__ x, const SysInfo* __restrict__ sys,
+                         const int* __restrict__ atom_sys, const int4* __restrict__ cunw, float4* __restrict__ s32,
+                         double4_32a* __restrict__ s64) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const SysInfo& S = sys_of(sys, atom_sys, i);
+  int4 c = cunw[i];
+  double s0 = (x[3 * i + 0] - S.lo[0]) - (double)c.x * S.h[0];
+  double s1 = (x[3 * i + 1] - S.lo[1]) - (double)c.y * S.h[1];
+  double s2 = (x[3 * i + 2] - S.lo[2]) - (double)c.z * S.h[2];
+  s32[i] = make_float4((float)s0, (float)s1, (float)s2, __int_as_float(c.w));
+  if (s64) s64[i] = make_double4_32a(s0, s1, s2, (double)c.w);
+}
+
+__global__ void k_wrap(int n, double* __restrict__ x, const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const SysInfo& S = sys_of(sys, atom_sys, i);
+  for (int d = 0; d < 3; ++d) {
+    if (!S.periodic[d]) continue;
+    double xv = x[3 * i + d];
+    double rel = xv - S.lo[d];
+    if (rel >= 0.0 && rel < S.L[d]) continue;
+    int nw = (int)floor(rel / S.L[d]);
+    x[3 * i + d] = __dsub_rn(xv, __dmul_rn((double)nw, S.L[d]));
+  }
+}
+
+// ------------------------------------------------------------------ row builds
+// The exact decision: |(x_j + S L) - x_i|^2 < rc2 with explicit round-to-nearest
+// operations (no contraction), S the image of j relative to the input positions.
+__device__ inline bool exact_within(const double* __restrict__ x, const SysInfo& S, int i, int j, const int4& ci,
+                                    const int4& cj, const int img[3], double rc2) {
+  int cwi[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
+  int cwj[3] = {cell_x(cj.w), cell_y(cj.w), cell_z(cj.w)};
+  int cui[3] = {ci.x, ci.y, ci.z};
+  int cuj[3] = {cj.x, cj.y, cj.z};
+  double r2 = 0.0;
+  double dd[3];
+  for (int d = 0; d < 3; ++d) {
+    int Sd = 0;
+    if (S.periodic[d]) Sd = img[d] + (cui[d] - cwi[d]) / S.nc[d] - (cuj[d] - cwj[d]) / S.nc[d];
+    double shifted = __dadd_rn(x[3 * j + d], __dmul_rn((double)Sd, S.L[d]));
+    dd[d] = __dsub_rn(shifted, x[3 * i + d]);
+  }
+  r2 = __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])), __dmul_rn(dd[2], dd[2]));
+  return r2 < rc2;
+}
+
+// Scan the 5x5x5 stencil around atom i and append accepted (j, offset) to a row.
+__device__ inline int build_row(int i, const double* __restrict__ x, const SysInfo& S, const float4* __restrict__ s32,
+                                const int4* __restrict__ cunw, const int* __restrict__ cstart,
+                                const int* __restrict__ catoms, float rcf2, double rc2, float band, int cap,
+                                int* __restrict__ row, int* __restrict__ offrow) {
+  const float4 si = s32[i];
+  const int4 ci = cunw[i];
+  const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
+  const float sv[3] = {si.x, si.y, si.z};
+  const float rmax2 = rcf2 + band;
+  int cnt = 0;
+  for (int dz = -kStencil; dz <= kStencil; ++dz) {
+    int tz = cw[2] + dz, iz = 0;
+    if (S.periodic[2]) {
+      iz = floor_div(tz, S.nc[2]);
+      tz -= iz * S.nc[2];
+    } else if (tz < 0 || tz >= S.nc[2]) {
+      continue;
+    }
+    float gz = fmaxf(0.f, fmaxf((float)dz * S.hf[2] - sv[2], sv[2] - (float)(dz + 1) * S.hf[2]));
+    for (int dy = -kStencil; dy <= kStencil; ++dy) {
+      int ty = cw[1] + dy, iy = 0;
+      if (S.periodic[1]) {
+        iy = floor_div(ty, S.nc[1]);
+        ty -= iy * S.nc[1];
+      } else if (ty < 0 || ty >= S.nc[1]) {
+        continue;
+      }
+      float gy = fmaxf(0.f, fmaxf((float)dy * S.hf[1] - sv[1], sv[1] - (float)(dy + 1) * S.hf[1]));
+      if (gz * gz + gy * gy > rmax2) continue;
+      for (int dx = -kStencil; dx <= kStencil; ++dx) {
+        int tx = cw[0] + dx, ix = 0;
+        if (S.periodic[0]) {
+          ix = floor_div(tx, S.nc[0]);
+          tx -= ix * S.nc[0];
+        } else if (tx < 0 || tx >= S.nc[0]) {
+          continue;
+        }
+        float gx = fmaxf(0.f, fmaxf((float)dx * S.hf[0] - sv[0], sv[0] - (float)(dx + 1) * S.hf[0]));
+        if (gz * gz + gy * gy + gx * gx > rmax2) continue;
+        int cid = S.cell_base + (tz * S.nc[1] + ty) * S.nc[0] + tx;
+        int b = cstart[cid], e = cstart[cid + 1];
+        const float ox = (float)dx * S.hf[0] - si.x;
+        const float oy = (float)dy * S.hf[1] - si.y;
+        const float oz = (float)dz * S.hf[2] - si.z;
+        for (int a = b; a < e; ++a) {
+          int j = catoms[a];
+          if (j == i && dx == 0 && dy == 0 && dz == 0) continue;
+          float4 sj = s32[j];
+          float ddx = ox + sj.x, ddy = oy + sj.y, ddz = oz + sj.z;
+          float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
+          if (r2f > rcf2 + band) continue;
+          bool take = r2f < rcf2 - band;
+          if (!take) {
+            int img[3] = {ix, iy, iz};
+            take = exact_within(x, S, i, j, ci, cunw[j], img, rc2);
+          }
+          if (take) {
+            if (cnt < cap) {
+              row[cnt] = j;
+              if (offrow) offrow[cnt] = pack_off(dx, dy, dz);
+            }
+            ++cnt;
+          }
+        }
+      }
+    }
+  }
+  return cnt;
+}
+
+__global__ void k_build_eam(int n, const double* __restrict__ x, const SysInfo* __restrict__ sys,
+                            const int* __restrict__ atom_sys, const float4* __restrict__ s32,
+                            const int4* __restrict__ cunw, const int* __restrict__ cstart,
+                            const int* __restrict__ catoms, float rcf2, double rc2, float band, int cap,
+                            int* __restrict__ nbr, int* __restrict__ off, int* __restrict__ cnt, DevScalars* sc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const SysInfo& S = sys_of(sys, atom_sys, i);
+  int c = build_row(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, band, cap, nbr + (size_t)i * cap,
+                    off ? off + (size_t)i * cap : nullptr);
+  cnt[i] = c < cap ? c : cap;
+  if (c > cap) {
+    atomicMax(&sc->need_eam, c);
+    atomicOr(&sc->err, kErrCapacity);
+  }
+}
+
+__global__ void k_build_ace(const int* __restrict__ queue, const int* __restrict__ nq, const double* __restrict__ x,
+                            const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
+                            const float4* __restrict__ s32, const int4* __restrict__ cunw,
+                            const int* __restrict__ cstart, const int* __restrict__ catoms, float rcf2, double rc2,
+                            float band, int cap, int* __restrict__ nbr, int* __restrict__ off, int* __restrict__ cnt,
+                            DevScalars* sc) {
+  const int m = *nq;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+    int i = queue[q];
+    const SysInfo& S = sys_of(sys, atom_sys, i);
+    int c = build_row(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, band, cap, nbr + (size_t)q * cap,
+                      off ? off + (size_t)q * cap : nullptr);
+    cnt[q] = c < cap ? c : cap;
+    if (c > cap) {
+      atomicMax(&sc->need_ace, c);
+      atomicOr(&sc->err, kErrCapacity);
+    }
+  }
+}
+
+// Export: entry (j, k) -> image s relative to the build positions.
+__global__ void k_export(int rows, int cap_in, int cap_out, const int* __restrict__ row_atom,
+                         const int* __restrict__ nbr, const int* __restrict__ off, const int* __restrict__ cnt_in,
+                         const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
+                         const int4* __restrict__ cunw, int* __restrict__ cnt_out, int* __restrict__ idx_out,
+                         int* __restrict__ shift_out) {
+  int r = blockIdx.x;
+  if (r >= rows) return;
+  int i = row_atom ? row_atom[r] : r;
+  const SysInfo& S = sys_of(sys, atom_sys, i);
+  int c = cnt_in[r];
+  if (threadIdx.x == 0) cnt_out[r] = c < cap_out ? c : cap_out;
+  int4 ci = cunw[i];
+  for (int q = threadIdx.x; q < c && q < cap_out; q += blockDim.x) {
+    int j = nbr[(size_t)r * cap_in + q];
+    int4 cj = cunw[j];
+    int k[3];
+    if (off) {
+      int p = off[(size_t)r * cap_in + q];
+      k[0] = off_x(p);
+      k[1] = off_y(p);
+      k[2] = off_z(p);
+    } else {
+      k[0] = wrap_off(cell_x(cj.w) - cell_x(ci.w), S.nc[0], S.periodic[0]);
+      k[1] = wrap_off(cell_y(cj.w) - cell_y(ci.w), S.nc[1], S.periodic[1]);
+      k[2] = wrap_off(cell_z(cj.w) - cell_z(ci.w), S.nc[2], S.periodic[2]);
+    }
+    int cu_i[3] = {ci.x, ci.y, ci.z}, cu_j[3] = {cj.x, cj.y, cj.z};
+    idx_out[(size_t)r * cap_out + q] = j;
+    for (int d = 0; d < 3; ++d) {
+      int sd = 0;
+      if (S.periodic[d]) sd = (k[d] - (cu_j[d] - cu_i[d])) / S.nc[d];
+      shift_out[((size_t)r * cap_out + q) * 3 + d] = sd;
+    }
+  }
+}
+
+inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+size_t scan_tmp_bytes(int n) { return sizeof(int) * ((size_t)n / 512 + 256); }
+
+int scan_exclusive(const int* d_in, int* d_out, int n, int* d_tmp, cudaStream_t s) {
+  return scan_rec(d_in, n, d_out, n + 1, d_tmp, s);
+}
+
+void launch_wrap_positions(ap_ctx* c, double* d_x, cudaStream_t s) {
+  k_wrap<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, c->d_sys, c->d_atom_sys);
+  c->kernels += 1;
+}
+
+void launch_bin(ap_ctx* c, const double* d_x, const int32_t* d_species, cudaStream_t s) {
+  cudaMemsetAsync(c->d_cell_count, 0, sizeof(int) * (size_t)c->n_cells, s);
+  k_bin<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, d_species, c->d_sys, c->d_atom_sys, c->d_cell, c->d_slot,
+                                        c->d_cunw, c->d_cell_count, c->d_sc);
+  c->kernels += 1;
+}
+
+void launch_cell_sort(ap_ctx* c, cudaStream_t s) {
+  c->kernels += 2 + scan_exclusive(c->d_cell_count, c->d_cell_start, c->n_cells, c->d_scan_tmp, s);
+  k_cell_scatter<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, c->d_cell, c->d_slot, c->d_cell_start, c->d_cell_atoms);
+  k_cell_sort<<<nblk(c->n_cells, 128), 128, 0, s>>>(c->n_cells, c->d_cell_start, c->d_cell_atoms);
+}
+
+void launch_shadow(ap_ctx* c, const double* d_x, cudaStream_t s) {
+  k_shadow<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, c->d_sys, c->d_atom_sys, c->d_cunw, c->d_sh32,
+                                           c->cfg.precision == AP_PREC_FP64 ? c->d_sh64 : nullptr);
+  c->kernels += 1;
+}
+
+static constexpr float kBand = 1e-3f;   // guard band on r^2 (A^2) around the cutoff
+
+void launch_build_eam(ap_ctx* c, const double* d_x, cudaStream_t s) {
+  double r = c->cfg.eam_rc + c->cfg.skin;
+  double rc2 = r * r;
+  k_build_eam<<<nblk(c->n, 128), 128, 0, s>>>((int)c->n, d_x, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
+                                              c->d_cell_start, c->d_cell_atoms, (float)rc2, rc2, kBand, c->cap_eam,
+                                              c->d_nbr_eam, c->stored_off ? c->d_off_eam : nullptr, c->d_cnt_eam,
+                                              c->d_sc);
+  c->kernels += 1;
+}
+
+void launch_build_ace(ap_ctx* c, const double* d_x, const int* d_queue, const int* d_nq, cudaStream_t s) {
+  double r = c->cfg.ace_rc + c->cfg.skin;
+  double rc2 = r * r;
+  int grid = c->num_sms * 8;
+  k_build_ace<<<grid, 128, 0, s>>>(d_queue, d_nq, d_x, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
+                                   c->d_cell_start, c->d_cell_atoms, (float)rc2, rc2, kBand, c->cap_ace,
+                                   c->d_nbr_ace, c->stored_off ? c->d_off_ace : nullptr, c->d_cnt_ace, c->d_sc);
+  c->kernels += 1;
+}
+
+void launch_export_rows(ap_ctx* c, int which, int rows, int cap_out, int* d_cnt, int* d_idx, int* d_shift,
+                        cudaStream_t s) {
+  if (rows <= 0) return;
+  if (which == 0)
+    k_export<<<rows, 128, 0, s>>>(rows, c->cap_eam, cap_out, nullptr, c->d_nbr_eam,
+                                  c->stored_off ? c->d_off_eam : nullptr, c->d_cnt_eam, c->d_sys, c->d_atom_sys,
+                                  c->d_cunw, d_cnt, d_idx, d_shift);
+  else
+    k_export<<<rows, 128, 0, s>>>(rows, c->cap_ace, cap_out, c->d_precise, c->d_nbr_ace,
+                                  c->stored_off ? c->d_off_ace : nullptr, c->d_cnt_ace, c->d_sys, c->d_atom_sys,
+                                  c->d_cunw, d_cnt, d_idx, d_shift);
+}
+
+}  // namespace ap
