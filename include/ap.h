@@ -98,6 +98,8 @@ typedef struct {
   int32_t lambda_every;      /* lambda update and list rebuild period (steps) */
   int32_t indenter_on;       /* 1: spherical indenter F = k (R - r)^2 (x - c)/r, r < R */
   double ind_c0[3], ind_v[3], ind_R, ind_k;   /* centre at t=0 (A), velocity (A/fs), R (A), k (eV/A^3) */
+  int32_t rebuild_every;     /* neighbour rebuild period (steps); 0 = lambda_every.  Every
+                                lambda update also rebuilds, so the CSP sees fresh rows. */
 } ap_config;
 
 typedef struct ap_ctx ap_ctx;

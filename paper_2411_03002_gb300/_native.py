@@ -28,7 +28,8 @@ class ApConfig(ctypes.Structure):
                    ("csp_lo", F64), ("csp_hi", F64), ("r_lo", F64), ("r_hi", F64), ("dlam_min", F64),
                    ("n_csp_avg", I32), ("n_lam_avg", I32), ("fcut_mode", I32), ("skin", F64), ("cap_eam", I32),
                    ("cap_ace", I32), ("precision", I32), ("dt", F64), ("lambda_every", I32), ("indenter_on", I32),
-                   ("ind_c0", F64 * 3), ("ind_v", F64 * 3), ("ind_R", F64), ("ind_k", F64)])
+                   ("ind_c0", F64 * 3), ("ind_v", F64 * 3), ("ind_R", F64), ("ind_k", F64),
+                   ("rebuild_every", I32)])
 
 
 class ApStepStats(ctypes.Structure):

@@ -40,7 +40,8 @@ def make_box(lo, hi, periodic) -> ApBox:
 
 
 def make_config(eam, ace, hyb, precision: int = N.PREC_MIXED, skin: float = 1.0, dt: float = 1.0,
-                indenter=None, cap_eam: int = 0, cap_ace: int = 0, lambda_every: Optional[int] = None) -> ApConfig:
+                indenter=None, cap_eam: int = 0, cap_ace: int = 0, lambda_every: Optional[int] = None,
+                rebuild_every: int = 0) -> ApConfig:
     """Fill an ap_config from parameter objects with the attribute names of
     the EAM (beta, alpha, A, D, rp, r0, rc, h), ACE (W, c, rc, n0) and switching
     (csp_lo, csp_hi, r_lo, r_hi, dlam_min, n_csp_avg, n_lam_avg, fcut_mode,
@@ -70,6 +71,7 @@ def make_config(eam, ace, hyb, precision: int = N.PREC_MIXED, skin: float = 1.0,
     c.precision = int(precision)
     c.dt = float(dt)
     c.lambda_every = int(lambda_every if lambda_every is not None else hyb.sample_every)
+    c.rebuild_every = int(rebuild_every)
     if indenter is not None:
         c.indenter_on = 1
         for k in range(3):

@@ -53,6 +53,7 @@ ap_status validate(const ap_config& g, std::string& why) {
   if (g.ace_nc < 0 || g.ace_nc > 512) return bad("ace_nc out of range");
   if (g.cap_eam < 0 || g.cap_ace < 0 || g.cap_eam > 4096 || g.cap_ace > 4096) return bad("row capacity out of range");
   if (g.lambda_every < 1) return bad("lambda_every must be >= 1");
+  if (g.rebuild_every < 0) return bad("rebuild_every must be >= 0");
   return AP_OK;
 }
 
@@ -637,7 +638,9 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
       PhaseTimer t(c, s, AP_PHASE_OTHER);
       launch_vv_first(c, d_x, d_v, d_f, d_mass, d_fixed, s);
     }
-    if (c->step % g.lambda_every == 0) {
+    const bool lam_step = c->step % g.lambda_every == 0;
+    const int rb = g.rebuild_every > 0 ? g.rebuild_every : g.lambda_every;
+    if (lam_step || c->step % rb == 0) {
       {
         PhaseTimer t(c, s, AP_PHASE_NEIGHBORS);
         k_check_skin<<<1, 1, 0, s>>>(c->d_sc, skin_lim2);
@@ -647,7 +650,7 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
       }
       {
         PhaseTimer t(c, s, AP_PHASE_CLASSIFY);
-        classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s);
+        if (lam_step) classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s);
         launch_build_ace(c, d_x, c->d_precise, &c->d_sc->n_precise, s);
       }
     } else {

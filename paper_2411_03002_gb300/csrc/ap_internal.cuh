@@ -94,6 +94,8 @@ struct AceTables {
   std::vector<int> term_idx;     // packed a1 | a2 << 8 | a3 << 16
   std::vector<double> term_coef;
   int n_terms = 0;
+  std::vector<double> c1;        // [8] nu = 1 coefficients
+  std::vector<double> m2;        // [5][8][8] nu = 2 symmetric coupling matrices
 };
 void build_ace_tables(const ap_config& cfg, AceTables& t);
 

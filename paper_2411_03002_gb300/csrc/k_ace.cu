@@ -126,32 +126,53 @@ void build_ace_tables(const ap_config& cfg, AceTables& t) {
         t.desc.insert(t.desc.end(), {3, p1 >> 2, p2 >> 2, p3 >> 2, l1, l2, l3});
       }
   t.nb = (int)(t.desc.size() / 7);
-  // flattened product terms with the coefficients folded in
-  t.term_idx.clear();
-  t.term_coef.clear();
+  // nu = 1: E1 = sum_n c1[n] A_n00.
+  // nu = 2: E2 = 1/2 sum_lm A_lm^T M_l A_lm with the symmetric 8x8 matrices
+  //         M_l[n1][n2] = c(n1,n2,l) (n1 != n2), M_l[n][n] = 2 c(n,n,l), so that
+  //         dE2/dA_{n,lm} = sum_n2 M_l[n][n2] A_{n2,lm}.
+  // nu = 3: flattened Gaunt product terms coef * A[a1] A[a2] A[a3] (coef = c_v G),
+  //         interleaved across functions so that neighbouring terms touch
+  //         different A entries.
+  t.c1.assign(8, 0.0);
+  t.m2.assign(5 * 64, 0.0);
+  std::vector<std::vector<std::pair<int, double>>> per_fn;
   for (int v = 0; v < t.nb; ++v) {
     const int* d = &t.desc[7 * v];
     double cv = (v < cfg.ace_nc) ? cfg.ace_c[v] : 0.0;
     if (d[0] == 1) {
-      t.term_idx.push_back(aidx(d[1], 0, 0) | (255 << 8) | (255 << 16));
-      t.term_coef.push_back(cv);
+      t.c1[d[1]] = cv;
     } else if (d[0] == 2) {
-      int l = d[4];
-      for (int m = -l; m <= l; ++m) {
-        t.term_idx.push_back(aidx(d[1], l, m) | (aidx(d[2], l, m) << 8) | (255 << 16));
-        t.term_coef.push_back(cv);
+      int l = d[4], n1 = d[1], n2 = d[2];
+      if (n1 == n2) {
+        t.m2[l * 64 + n1 * 8 + n1] = 2.0 * cv;
+      } else {
+        t.m2[l * 64 + n1 * 8 + n2] = cv;
+        t.m2[l * 64 + n2 * 8 + n1] = cv;
       }
     } else {
       int l1 = d[4], l2 = d[5], l3 = d[6];
+      std::vector<std::pair<int, double>> terms;
       for (int m1 = -l1; m1 <= l1; ++m1)
         for (int m2 = -l2; m2 <= l2; ++m2)
           for (int m3 = -l3; m3 <= l3; ++m3) {
             double g = G(l1, m1, l2, m2, l3, m3);
             if (std::fabs(g) < 1e-14) continue;
-            t.term_idx.push_back(aidx(d[1], l1, m1) | (aidx(d[2], l2, m2) << 8) | (aidx(d[3], l3, m3) << 16));
-            t.term_coef.push_back(cv * g);
+            terms.push_back({aidx(d[1], l1, m1) | (aidx(d[2], l2, m2) << 8) | (aidx(d[3], l3, m3) << 16), cv * g});
           }
+      per_fn.push_back(terms);
     }
+  }
+  t.term_idx.clear();
+  t.term_coef.clear();
+  for (size_t k = 0;; ++k) {
+    bool any = false;
+    for (auto& fn : per_fn)
+      if (k < fn.size()) {
+        t.term_idx.push_back(fn[k].first);
+        t.term_coef.push_back(fn[k].second);
+        any = true;
+      }
+    if (!any) break;
   }
   t.n_terms = (int)t.term_idx.size();
 }
@@ -161,7 +182,8 @@ namespace {
 
 constexpr int kCols = 36;            // 32 neighbour slots + 4 pad (16-byte rows, conflict-free)
 constexpr int kRows = 33;            // 8 radial + 25 angular rows
-constexpr int kWarps = 4;            // warps per CTA
+template <typename R>
+constexpr int kWarps = sizeof(R) == 4 ? 10 : 4;   // warps per CTA: two CTAs fit per SM in FP32
 
 template <typename R>
 struct V;
@@ -335,9 +357,10 @@ __device__ inline void pair_disp(const SysInfo& S, const typename V<R>::S4& si, 
   }
 }
 
-__device__ inline void add_force(float4* facc32, double* facc64, int j, double sx, double sy, double sz) {
-  if (facc32) {
-    atomicAdd(&facc32[j], make_float4((float)sx, (float)sy, (float)sz, 0.f));
+template <typename R>
+__device__ inline void add_force(float4* facc32, double* facc64, int j, R sx, R sy, R sz) {
+  if constexpr (sizeof(R) == 4) {
+    atomicAdd(&facc32[j], make_float4(sx, sy, sz, 0.f));
   } else {
     atomicAdd(&facc64[3 * j + 0], sx);
     atomicAdd(&facc64[3 * j + 1], sy);
@@ -355,9 +378,9 @@ __device__ inline void force_block(const R* __restrict__ U, R ux, R uy, R uz, co
     const int lm = L * L + m;
     auto ua = ld4<R>(&U[lm * 8]);
     auto ub = ld4<R>(&U[lm * 8 + 4]);
-    R S = ua.x * g[0] + ua.y * g[1] + ua.z * g[2] + ua.w * g[3] + ub.x * g[4] + ub.y * g[5] + ub.z * g[6] + ub.w * g[7];
-    R Sp = ua.x * dg[0] + ua.y * dg[1] + ua.z * dg[2] + ua.w * dg[3] + ub.x * dg[4] + ub.y * dg[5] + ub.z * dg[6] +
-           ub.w * dg[7];
+    R S = (ua.x * g[0] + ua.y * g[1]) + (ua.z * g[2] + ua.w * g[3]) + ((ub.x * g[4] + ub.y * g[5]) + (ub.z * g[6] + ub.w * g[7]));
+    R Sp = (ua.x * dg[0] + ua.y * dg[1]) + (ua.z * dg[2] + ua.w * dg[3]) +
+           ((ub.x * dg[4] + ub.y * dg[5]) + (ub.z * dg[6] + ub.w * dg[7]));
     pr += Sp * Y[m];
     R lz = R(L) * Y[m];
     ptx += S * (gx[m] - lz * ux);
@@ -372,6 +395,13 @@ __device__ inline T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+__device__ inline float pack_j(int j, float) { return __int_as_float(j); }
+__device__ inline double pack_j(int j, double) { return __longlong_as_double((long long)j); }
+__device__ inline int unpack_j(float v) { return __float_as_int(v); }
+__device__ inline int unpack_j(double v) { return (int)__double_as_longlong(v); }
+
+constexpr int kListCap = 192;   // neighbours inside ace_rc kept per precise atom (FCC bulk: 134)
 
 template <typename R>
 struct AceArgs {
@@ -391,6 +421,8 @@ struct AceArgs {
   const R* term_coef;
   int n_terms;
   const R* W;
+  const R* M2;
+  const R* C1;
   R rc2, inv_rc, inv_n0;
   int mode;
   double* e_prec;
@@ -399,21 +431,31 @@ struct AceArgs {
 };
 
 template <typename R, bool FORCES>
-__global__ void __launch_bounds__(kWarps * 32) k_ace(AceArgs<R> a) {
-  // Layout (every region a multiple of 32 bytes, so 4-wide FP64 loads stay aligned):
-  // W [320] | term coefficients [t8] | term indices [t8] | per warp: g/Y tile, A, dA, U
+__global__ void __launch_bounds__(kWarps<R> * 32) k_ace(AceArgs<R> a) {
+  // Shared memory (every region a multiple of 32 bytes, so 4-wide FP64 loads stay aligned):
+  //   W [320] | M2 [320] | C1 [8] | nu=3 coefficients [t8] | nu=3 indices [t8] |
+  //   per warp: compacted neighbours [kListCap][4] | tile [kRows][kCols]
+  // A, dA, U and the G scratch alias the tile once stage A's contraction is done.
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int t8 = (a.n_terms + 7) & ~7;
-  R* Ws = reinterpret_cast<R*>(smem_raw);                       // 320
-  R* coef = Ws + 320;                                            // t8
-  int* tidx = reinterpret_cast<int*>(coef + t8);                 // t8
+  R* Ws = reinterpret_cast<R*>(smem_raw);
+  R* M2 = Ws + 320;
+  R* C1 = M2 + 320;
+  R* coef = C1 + 8;
+  int* tidx = reinterpret_cast<int*>(coef + t8);
   R* wbase = reinterpret_cast<R*>(tidx + t8);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  R* buf = wbase + warp * (kRows * kCols + 600);
-  R* A = buf + kRows * kCols;
-  R* dA = A + 200;
-  R* U = dA + 200;
-  for (int t = threadIdx.x; t < 320; t += blockDim.x) Ws[t] = a.W[t];
+  R* list = wbase + warp * (4 * kListCap + kRows * kCols);
+  R* tile = list + 4 * kListCap;
+  R* A = tile;
+  R* dA = tile + 200;
+  R* U = tile + 400;
+  R* Gs = tile + 600;
+  for (int t = threadIdx.x; t < 320; t += blockDim.x) {
+    Ws[t] = a.W[t];
+    M2[t] = a.M2[t];
+  }
+  if (threadIdx.x < 8) C1[threadIdx.x] = a.C1[threadIdx.x];
   for (int t = threadIdx.x; t < a.n_terms; t += blockDim.x) {
     coef[t] = a.term_coef[t];
     tidx[t] = a.term_idx[t];
@@ -421,6 +463,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_ace(AceArgs<R> a) {
   __syncthreads();
   const int m = a.sc->n_precise;
   const int kq = lane & 7, grp = lane >> 3;
+  const unsigned lt_mask = (1u << lane) - 1u;
   while (true) {
     int q = 0;
     if (lane == 0) q = atomicAdd(a.counter, 1);
@@ -432,107 +475,122 @@ __global__ void __launch_bounds__(kWarps * 32) k_ace(AceArgs<R> a) {
     const int c = a.cnt[q];
     const size_t row = (size_t)q * a.cap;
 
-    // ---------------- stage A: G_klm = sum_j g_k Y_lm
+    // ---------------- pass 0: compact the row entries inside ace_rc (j and r_ij)
+    int nin = 0;
+    for (int base = 0; base < c; base += 32) {
+      const int slot = base + lane;
+      bool in = false;
+      R d[3] = {R(0), R(0), R(0)};
+      int j = 0;
+      if (slot < c) {
+        j = a.nbr[row + slot];
+        auto sj = a.sh[j];
+        pair_disp<R>(S, si, sj, a.off, row + slot, d);
+        in = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < a.rc2;
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, in);
+      const int pos = nin + __popc(mask & lt_mask);
+      if (in && pos < kListCap) {
+        R* e = &list[4 * pos];
+        e[0] = d[0];
+        e[1] = d[1];
+        e[2] = d[2];
+        e[3] = pack_j(j, R(0));
+      }
+      nin += __popc(mask);
+    }
+    if (nin > kListCap) {
+      if (lane == 0) atomicOr(&a.stats->err, kErrCapacity);
+      nin = kListCap;
+    }
+    __syncwarp();
+
+    // ---------------- stage A: G_klm = sum_j g_k Y_lm over the compacted neighbours
     R acc[7];
 #pragma unroll
     for (int t = 0; t < 7; ++t) acc[t] = R(0);
-    int pairs = 0;
-    for (int base = 0; base < c; base += 32) {
+    for (int base = 0; base < nin; base += 32) {
       const int slot = base + lane;
       R g[8], Y[25];
-      bool in = false;
-      if (slot < c) {
-        int j = a.nbr[row + slot];
-        auto sj = a.sh[j];
-        R d[3];
-        pair_disp<R>(S, si, sj, a.off, row + slot, d);
-        R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        if (r2 < a.rc2) {
-          in = true;
-          R ir = rsqrt_(r2);
-          R r = r2 * ir;
-          radial<R, false>(r, a.inv_rc, a.mode, g, nullptr);
-          sh_values<R>(d[0] * ir, d[1] * ir, d[2] * ir, Y);
-        }
-      }
-      pairs += __popc(__ballot_sync(0xffffffffu, in));
-      if (!in) {
+      if (slot < nin) {
+        auto e = ld4<R>(&list[4 * slot]);
+        R r2 = e.x * e.x + e.y * e.y + e.z * e.z;
+        R ir = rsqrt_(r2);
+        radial<R, false>(r2 * ir, a.inv_rc, a.mode, g, nullptr);
+        sh_values<R>(e.x * ir, e.y * ir, e.z * ir, Y);
+      } else {
 #pragma unroll
         for (int k = 0; k < 8; ++k) g[k] = R(0);
 #pragma unroll
         for (int k = 0; k < 25; ++k) Y[k] = R(0);
       }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) buf[k * kCols + lane] = g[k];
+      for (int k = 0; k < 8; ++k) tile[k * kCols + lane] = g[k];
 #pragma unroll
-      for (int k = 0; k < 25; ++k) buf[(8 + k) * kCols + lane] = Y[k];
+      for (int k = 0; k < 25; ++k) tile[(8 + k) * kCols + lane] = Y[k];
       __syncwarp();
-      const int nv = min(32, c - base);
+      const int nv = min(32, nin - base);
       for (int s4 = 0; s4 < (nv + 3) / 4; ++s4) {
-        auto g4 = ld4<R>(&buf[kq * kCols + 4 * s4]);
+        auto g4 = ld4<R>(&tile[kq * kCols + 4 * s4]);
 #pragma unroll
         for (int t = 0; t < 7; ++t) {
           const int lm = grp + 4 * t;
           if (lm < 25) {
-            auto y4 = ld4<R>(&buf[(8 + lm) * kCols + 4 * s4]);
+            auto y4 = ld4<R>(&tile[(8 + lm) * kCols + 4 * s4]);
             acc[t] += g4.x * y4.x + g4.y * y4.y + g4.z * y4.z + g4.w * y4.w;
           }
         }
       }
       __syncwarp();
     }
-    // G into U (scratch), then A = (1/N0) W . G
+    // G into the scratch, then A = (1/N0) W . G
 #pragma unroll
     for (int t = 0; t < 7; ++t) {
       const int lm = grp + 4 * t;
-      if (lm < 25) U[kq * 25 + lm] = acc[t];
+      if (lm < 25) Gs[kq * 25 + lm] = acc[t];
     }
     __syncwarp();
     for (int o = lane; o < 200; o += 32) {
-      const int n = o / 25, lm = o - 25 * (o / 25), l = l_of(lm);
+      const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
       const R* w = &Ws[(l * 8 + n) * 8];
       R s = R(0);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) s += w[k] * U[k * 25 + lm];
+      for (int k = 0; k < 8; ++k) s += w[k] * Gs[k * 25 + lm];
       A[o] = s * a.inv_n0;
       dA[o] = R(0);
     }
     __syncwarp();
 
     // ---------------- stage B: E and dE/dA
+    // nu = 3 terms (atomics into dA), then nu = 2 and nu = 1 per owned output
     R e = R(0);
     for (int t = lane; t < a.n_terms; t += 32) {
       const int pk = tidx[t];
       const R cf = coef[t];
-      const int a1 = pk & 255, a2 = (pk >> 8) & 255, a3 = (pk >> 16) & 255;
-      const R A1 = A[a1];
-      if (a2 == 255) {
-        e += cf * A1;
-        if (FORCES) atomicAdd(&dA[a1], cf);
-      } else {
-        const R A2 = A[a2];
-        if (a3 == 255) {
-          e += cf * A1 * A2;
-          if (FORCES) {
-            atomicAdd(&dA[a1], cf * A2);
-            atomicAdd(&dA[a2], cf * A1);
-          }
-        } else {
-          const R A3 = A[a3];
-          const R p12 = cf * A1 * A2;
-          e += p12 * A3;
-          if (FORCES) {
-            atomicAdd(&dA[a1], cf * A2 * A3);
-            atomicAdd(&dA[a2], cf * A1 * A3);
-            atomicAdd(&dA[a3], p12);
-          }
-        }
+      const R A1 = A[pk & 255], A2 = A[(pk >> 8) & 255], A3 = A[(pk >> 16) & 255];
+      const R p12 = cf * A1 * A2;
+      e += p12 * A3;
+      if (FORCES) {
+        atomicAdd(&dA[pk & 255], cf * A2 * A3);
+        atomicAdd(&dA[(pk >> 8) & 255], cf * A1 * A3);
+        atomicAdd(&dA[(pk >> 16) & 255], p12);
       }
+    }
+    __syncwarp();
+    for (int o = lane; o < 200; o += 32) {
+      const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
+      const R* mrow = &M2[l * 64 + n * 8];
+      R s = R(0);
+#pragma unroll
+      for (int n2 = 0; n2 < 8; ++n2) s += mrow[n2] * A[n2 * 25 + lm];
+      const R lin = lm == 0 ? C1[n] : R(0);
+      e += A[o] * (R(0.5) * s + lin);
+      if (FORCES) dA[o] += s + lin;
     }
     double E = warp_sum<double>((double)e);
     if (lane == 0) {
       a.e_prec[i] = E;
-      atomicAdd(&a.stats->ace_pairs, (unsigned long long)pairs);
+      atomicAdd(&a.stats->ace_pairs, (unsigned long long)nin);
       atomicAdd(&a.stats->ace_atoms, 1ull);
     }
     if (!FORCES) {
@@ -540,7 +598,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_ace(AceArgs<R> a) {
       continue;
     }
     __syncwarp();
-    // ---------------- stage C: u_klm and forces
+    // ---------------- stage C: u_klm and forces over the compacted neighbours
     for (int o = lane; o < 200; o += 32) {
       const int lm = o >> 3, k = o & 7, l = l_of(lm);
       R s = R(0);
@@ -551,20 +609,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_ace(AceArgs<R> a) {
     __syncwarp();
     const R wgt = (R)(1.0 - (a.lam ? a.lam[i] : 0.0));
     R pix = R(0), piy = R(0), piz = R(0);
-    for (int base = 0; base < c; base += 32) {
+    for (int base = 0; base < nin; base += 32) {
       const int slot = base + lane;
-      if (slot >= c) continue;
-      int j = a.nbr[row + slot];
-      auto sj = a.sh[j];
-      R d[3];
-      pair_disp<R>(S, si, sj, a.off, row + slot, d);
-      R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-      if (!(r2 < a.rc2)) continue;
+      if (slot >= nin) continue;
+      auto ev = ld4<R>(&list[4 * slot]);
+      const int j = unpack_j(ev.w);
+      R r2 = ev.x * ev.x + ev.y * ev.y + ev.z * ev.z;
       R ir = rsqrt_(r2);
-      R r = r2 * ir;
-      R ux = d[0] * ir, uy = d[1] * ir, uz = d[2] * ir;
+      R ux = ev.x * ir, uy = ev.y * ir, uz = ev.z * ir;
       R g[8], dg[8];
-      radial<R, true>(r, a.inv_rc, a.mode, g, dg);
+      radial<R, true>(r2 * ir, a.inv_rc, a.mode, g, dg);
       R pr = R(0), ptx = R(0), pty = R(0), ptz = R(0);
       force_block<R, 0>(U, ux, uy, uz, g, dg, pr, ptx, pty, ptz);
       force_block<R, 1>(U, ux, uy, uz, g, dg, pr, ptx, pty, ptz);
@@ -575,12 +629,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_ace(AceArgs<R> a) {
       pix += px;
       piy += py;
       piz += pz;
-      add_force(a.facc32, a.facc64, j, -(double)(wgt * px), -(double)(wgt * py), -(double)(wgt * pz));
+      add_force<R>(a.facc32, a.facc64, j, -wgt * px, -wgt * py, -wgt * pz);
     }
     pix = warp_sum<R>(pix);
     piy = warp_sum<R>(piy);
     piz = warp_sum<R>(piz);
-    if (lane == 0) add_force(a.facc32, a.facc64, i, (double)(wgt * pix), (double)(wgt * piy), (double)(wgt * piz));
+    if (lane == 0) add_force<R>(a.facc32, a.facc64, i, wgt * pix, wgt * piy, wgt * piz);
     __syncwarp();
   }
 }
@@ -603,7 +657,8 @@ __global__ void k_ace_finalize64(int n, const double* __restrict__ acc, double* 
 template <typename R>
 size_t ace_smem(int n_terms) {
   size_t t8 = (size_t)((n_terms + 7) & ~7);
-  return sizeof(R) * 320 + sizeof(R) * t8 + sizeof(int) * t8 + sizeof(R) * kWarps * (kRows * kCols + 600);
+  return sizeof(R) * (320 + 320 + 8) + sizeof(R) * t8 + sizeof(int) * t8 +
+         sizeof(R) * kWarps<R> * (4 * kListCap + kRows * kCols);
 }
 
 template <typename R>
@@ -636,6 +691,8 @@ void run_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_pre
     a.facc32 = nullptr;
     a.facc64 = c->d_facc64;
   }
+  a.M2 = a.W + 320;   // the parameter block is [W (320) | M2 (320) | C1 (8)]
+  a.C1 = a.W + 640;
   a.n_terms = c->ace.n_terms;
   a.rc2 = (R)(c->cfg.ace_rc * c->cfg.ace_rc);
   a.inv_rc = (R)(1.0 / c->cfg.ace_rc);
@@ -650,7 +707,7 @@ void run_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_pre
   if (!configured[pi][fi]) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kWarps<R> * 32, smem);
     blocks_per_sm[pi][fi] = b > 0 ? b : 1;
     configured[pi][fi] = 1;
   }
@@ -662,7 +719,7 @@ void run_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_pre
   }
   cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   int grid = c->num_sms * blocks_per_sm[pi][fi];
-  kern<<<grid, kWarps * 32, smem, s>>>(a);
+  kern<<<grid, kWarps<R> * 32, smem, s>>>(a);
   c->kernels += 1;
 }
 
@@ -671,17 +728,20 @@ void run_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_pre
 void upload_ace_tables(ap_ctx* c) {
   const AceTables& t = c->ace;
   std::vector<float> cf32(t.term_coef.begin(), t.term_coef.end());
-  std::vector<float> w32(c->cfg.ace_W, c->cfg.ace_W + 320);
+  std::vector<double> p64(c->cfg.ace_W, c->cfg.ace_W + 320);
+  p64.insert(p64.end(), t.m2.begin(), t.m2.end());
+  p64.insert(p64.end(), t.c1.begin(), t.c1.end());
+  std::vector<float> p32(p64.begin(), p64.end());
   cudaMalloc(&c->d_term_idx, sizeof(int) * t.n_terms);
   cudaMalloc(&c->d_term_coef32, sizeof(float) * t.n_terms);
   cudaMalloc(&c->d_term_coef64, sizeof(double) * t.n_terms);
-  cudaMalloc(&c->d_W32, sizeof(float) * 320);
-  cudaMalloc(&c->d_W64, sizeof(double) * 320);
+  cudaMalloc(&c->d_W32, sizeof(float) * p32.size());
+  cudaMalloc(&c->d_W64, sizeof(double) * p64.size());
   cudaMemcpy(c->d_term_idx, t.term_idx.data(), sizeof(int) * t.n_terms, cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_term_coef32, cf32.data(), sizeof(float) * t.n_terms, cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_term_coef64, t.term_coef.data(), sizeof(double) * t.n_terms, cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_W32, w32.data(), sizeof(float) * 320, cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_W64, c->cfg.ace_W, sizeof(double) * 320, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_W32, p32.data(), sizeof(float) * p32.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_W64, p64.data(), sizeof(double) * p64.size(), cudaMemcpyHostToDevice);
 }
 
 void launch_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_prec, bool forces, cudaStream_t s) {

@@ -5,9 +5,13 @@
 //   force:   F_i = sum_j g_ij (x_j - x_i)/r_ij with
 //            g_ij = (lambda_i xi'_i + lambda_j xi'_j) zeta'(r_ij) + (lambda_i + lambda_j)/2 Phi'(r_ij),
 //            which is -grad_i sum_k lambda_k E_k^(f) gathered without atomics;
-//            E_i^(f) = xi_i + 1/2 sum_j Phi(r_ij).
+//            E_i^(f) = xi_i + 1/2 sum_j Phi(r_ij)  (the Phi sum reduced in FP64).
 // Analytic forms: zeta(r) = exp(-beta (r/r0 - 1)) psi, Phi(r) = D (e^{-2a(r-rp)} -
 // 2 e^{-a(r-rp)}) psi, xi(rho) = -A sqrt(rho), psi = u^4/(1+u^4), u = (r - rc)/h < 0.
+//
+// Pair displacements come from cell-relative shadows: d = k h + s_j - s_i with k
+// the pair's cell offset, either stored per entry (small periodic boxes) or
+// unwrapped from the packed cell codes (branch-free, per-atom constants hoisted).
 #include "ap_internal.cuh"
 
 namespace ap {
@@ -49,45 +53,69 @@ __device__ inline float rexp(float v) { return __expf(v); }
 __device__ inline double rexp(double v) { return exp(v); }
 __device__ inline float rsqrt_(float v) { return rsqrtf(v); }
 __device__ inline double rsqrt_(double v) { return rsqrt(v); }
+__device__ inline float rcp_(float v) { return __frcp_rn(v); }
+__device__ inline double rcp_(double v) { return 1.0 / v; }
 
-__device__ inline const SysInfo& sys_of(const SysInfo* sys, const int* atom_sys, int i) {
-  return sys[atom_sys ? atom_sys[i] : 0];
-}
+// Per-atom frame: cell code and box constants of atom i, held in registers.
+template <typename R, bool STORED>
+struct Frame {
+  R hx, hy, hz;
+  int cx, cy, cz;
+  int nx, ny, nz;
+  int halfx, halfy, halfz;   // nc/2 in periodic dimensions, a huge value otherwise
+  R sx, sy, sz;
 
-template <typename R, typename S4>
-__device__ inline void pair_disp(const SysInfo& S, const S4& si, const S4& sj, const int* off, size_t e, R d[3]) {
-  int k0, k1, k2;
-  if (off) {
-    int p = off[e];
-    k0 = off_x(p);
-    k1 = off_y(p);
-    k2 = off_z(p);
-  } else {
-    int wi = Shadow<R>::code(si), wj = Shadow<R>::code(sj);
-    k0 = wrap_off(cell_x(wj) - cell_x(wi), S.nc[0], S.periodic[0]);
-    k1 = wrap_off(cell_y(wj) - cell_y(wi), S.nc[1], S.periodic[1]);
-    k2 = wrap_off(cell_z(wj) - cell_z(wi), S.nc[2], S.periodic[2]);
+  template <typename S4>
+  __device__ inline Frame(const SysInfo& S, const S4& si) {
+    if constexpr (sizeof(R) == 4) {
+      hx = S.hf[0];
+      hy = S.hf[1];
+      hz = S.hf[2];
+    } else {
+      hx = S.h[0];
+      hy = S.h[1];
+      hz = S.h[2];
+    }
+    int w = Shadow<R>::code(si);
+    cx = cell_x(w);
+    cy = cell_y(w);
+    cz = cell_z(w);
+    nx = S.nc[0];
+    ny = S.nc[1];
+    nz = S.nc[2];
+    halfx = S.periodic[0] ? nx / 2 : 0x3fffffff;
+    halfy = S.periodic[1] ? ny / 2 : 0x3fffffff;
+    halfz = S.periodic[2] ? nz / 2 : 0x3fffffff;
+    sx = si.x;
+    sy = si.y;
+    sz = si.z;
   }
-  if constexpr (sizeof(R) == 4) {
-    d[0] = (R)k0 * S.hf[0] + (sj.x - si.x);
-    d[1] = (R)k1 * S.hf[1] + (sj.y - si.y);
-    d[2] = (R)k2 * S.hf[2] + (sj.z - si.z);
-  } else {
-    d[0] = (R)k0 * S.h[0] + (sj.x - si.x);
-    d[1] = (R)k1 * S.h[1] + (sj.y - si.y);
-    d[2] = (R)k2 * S.h[2] + (sj.z - si.z);
-  }
-}
 
-// psi(u) = u^4/(1+u^4) and dpsi/du, for u < 0
-template <typename R>
-__device__ inline void psi_fn(R u, R& ps, R& dps) {
-  R u2 = u * u;
-  R u4 = u2 * u2;
-  R inv = R(1) / (R(1) + u4);
-  ps = u4 * inv;
-  dps = R(4) * u2 * u * inv * inv;
-}
+  __device__ static inline int unwrap(int d, int n, int half) {
+    d += (d < -half) ? n : 0;
+    d -= (d > half) ? n : 0;
+    return d;
+  }
+
+  template <typename S4>
+  __device__ inline void disp(const S4& sj, const int* __restrict__ off, size_t e, R d[3]) const {
+    int kx, ky, kz;
+    if constexpr (STORED) {
+      int p = off[e];
+      kx = off_x(p);
+      ky = off_y(p);
+      kz = off_z(p);
+    } else {
+      int w = Shadow<R>::code(sj);
+      kx = unwrap(cell_x(w) - cx, nx, halfx);
+      ky = unwrap(cell_y(w) - cy, ny, halfy);
+      kz = unwrap(cell_z(w) - cz, nz, halfz);
+    }
+    d[0] = (R)kx * hx + (sj.x - sx);
+    d[1] = (R)ky * hy + (sj.y - sy);
+    d[2] = (R)kz * hz + (sj.z - sz);
+  }
+};
 
 template <typename T, int G>
 __device__ inline T group_sum(T v) {
@@ -96,7 +124,7 @@ __device__ inline T group_sum(T v) {
   return v;
 }
 
-template <typename R, int G>
+template <typename R, int G, bool STORED>
 __global__ void __launch_bounds__(256) k_eam_density(int n, const SysInfo* __restrict__ sys,
                                                      const int* __restrict__ atom_sys,
                                                      const typename Shadow<R>::T* __restrict__ sh,
@@ -108,39 +136,41 @@ __global__ void __launch_bounds__(256) k_eam_density(int n, const SysInfo* __res
   const int sub = threadIdx.x & (G - 1);
   const bool active = gid < n;
   const int i = active ? gid : n - 1;
-  const SysInfo& S = sys_of(sys, atom_sys, i);
   const auto si = sh[i];
+  const Frame<R, STORED> fr(sys[atom_sys ? atom_sys[i] : 0], si);
   const int c = active ? cnt[i] : 0;
   const size_t row = (size_t)i * cap;
   R rho = R(0);
+#pragma unroll 4
   for (int t = sub; t < c; t += G) {
-    int j = nbr[row + t];
-    auto sj = sh[j];
+    const int j = nbr[row + t];
+    const auto sj = sh[j];
     R d[3];
-    pair_disp<R>(S, si, sj, off, row + t, d);
-    R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    fr.disp(sj, off, row + t, d);
+    const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     if (r2 < p.rc2) {
-      R r = r2 * rsqrt_(r2);
-      R ps, dps;
-      psi_fn<R>((r - p.rc) * p.inv_h, ps, dps);
-      rho += rexp(p.beta - p.beta_r0 * r) * ps;
+      const R r = r2 * rsqrt_(r2);
+      const R u = (r - p.rc) * p.inv_h;
+      const R u2 = u * u;
+      const R u4 = u2 * u2;
+      rho += rexp(p.beta - p.beta_r0 * r) * (u4 * rcp_(R(1) + u4));
     }
   }
-  double rho_d = group_sum<double, G>((double)rho);
+  rho = group_sum<R, G>(rho);
   if (active && sub == 0) {
-    double li = lam ? lam[i] : 1.0;
-    double xi = 0.0, dxi = 0.0;
-    if (rho_d > 0.0) {
-      double s = sqrt(rho_d);
-      xi = -(double)p.A * s;
-      dxi = -(double)p.A / (2.0 * s);
+    const R li = lam ? (R)lam[i] : R(1);
+    R xi = R(0), dxi = R(0);
+    if (rho > R(0)) {
+      const R s = sqrt(rho);
+      xi = -p.A * s;
+      dxi = R(-0.5) * p.A * rcp_(s);
     }
-    q[i] = Q2<R>::make((R)(li * dxi), (R)li);
-    xi_out[i] = xi;
+    q[i] = Q2<R>::make(li * dxi, li);
+    xi_out[i] = (double)xi;
   }
 }
 
-template <typename R, int G>
+template <typename R, int G, bool STORED>
 __global__ void __launch_bounds__(256) k_eam_force(int n, const SysInfo* __restrict__ sys,
                                                    const int* __restrict__ atom_sys,
                                                    const typename Shadow<R>::T* __restrict__ sh,
@@ -153,55 +183,59 @@ __global__ void __launch_bounds__(256) k_eam_force(int n, const SysInfo* __restr
   const int sub = threadIdx.x & (G - 1);
   const bool active = gid < n;
   const int i = active ? gid : n - 1;
-  const SysInfo& S = sys_of(sys, atom_sys, i);
   const auto si = sh[i];
+  const Frame<R, STORED> fr(sys[atom_sys ? atom_sys[i] : 0], si);
   const auto qi = q[i];
   const int c = active ? cnt[i] : 0;
   const size_t row = (size_t)i * cap;
   R fx = R(0), fy = R(0), fz = R(0), phi = R(0);
+#pragma unroll 4
   for (int t = sub; t < c; t += G) {
-    int j = nbr[row + t];
-    auto sj = sh[j];
+    const int j = nbr[row + t];
+    const auto sj = sh[j];
+    const auto qj = q[j];
     R d[3];
-    pair_disp<R>(S, si, sj, off, row + t, d);
-    R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    fr.disp(sj, off, row + t, d);
+    const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     if (r2 < p.rc2) {
-      auto qj = q[j];
-      R inv_r = rsqrt_(r2);
-      R r = r2 * inv_r;
-      R ps, dps;
-      psi_fn<R>((r - p.rc) * p.inv_h, ps, dps);
-      dps *= p.inv_h;
-      R ez = rexp(p.beta - p.beta_r0 * r);
-      R dzeta = ez * (dps - p.beta_r0 * ps);
-      R e1 = rexp(-p.alpha * (r - p.rp));
-      R e2 = e1 * e1;
-      R m = p.D * (e2 - R(2) * e1);
-      R dm = R(2) * p.alpha * p.D * (e1 - e2);
-      R dphi = dm * ps + m * dps;
+      const R inv_r = rsqrt_(r2);
+      const R r = r2 * inv_r;
+      const R u = (r - p.rc) * p.inv_h;
+      const R u2 = u * u;
+      const R u4 = u2 * u2;
+      const R inv = rcp_(R(1) + u4);
+      const R ps = u4 * inv;
+      const R dps = R(4) * u2 * u * inv * inv * p.inv_h;
+      const R ez = rexp(p.beta - p.beta_r0 * r);
+      const R dzeta = ez * (dps - p.beta_r0 * ps);
+      const R e1 = rexp(-p.alpha * (r - p.rp));
+      const R e2 = e1 * e1;
+      const R m = p.D * (e2 - R(2) * e1);
+      const R dm = R(2) * p.alpha * p.D * (e1 - e2);
+      const R dphi = dm * ps + m * dps;
       phi += m * ps;
-      R g = (qi.x + qj.x) * dzeta + R(0.5) * (qi.y + qj.y) * dphi;
-      R s = g * inv_r;
+      const R g = (qi.x + qj.x) * dzeta + R(0.5) * (qi.y + qj.y) * dphi;
+      const R s = g * inv_r;
       fx += s * d[0];
       fy += s * d[1];
       fz += s * d[2];
     }
   }
-  double Fx = group_sum<double, G>((double)fx);
-  double Fy = group_sum<double, G>((double)fy);
-  double Fz = group_sum<double, G>((double)fz);
-  double Ph = group_sum<double, G>((double)phi);
+  fx = group_sum<R, G>(fx);
+  fy = group_sum<R, G>(fy);
+  fz = group_sum<R, G>(fz);
+  const double ph = group_sum<double, G>((double)phi);
   if (active && sub == 0) {
     if (accumulate) {
-      f[3 * i + 0] += Fx;
-      f[3 * i + 1] += Fy;
-      f[3 * i + 2] += Fz;
+      f[3 * i + 0] += (double)fx;
+      f[3 * i + 1] += (double)fy;
+      f[3 * i + 2] += (double)fz;
     } else {
-      f[3 * i + 0] = Fx;
-      f[3 * i + 1] = Fy;
-      f[3 * i + 2] = Fz;
+      f[3 * i + 0] = (double)fx;
+      f[3 * i + 1] = (double)fy;
+      f[3 * i + 2] = (double)fz;
     }
-    if (e_fast) e_fast[i] = xi[i] + 0.5 * Ph;
+    if (e_fast) e_fast[i] = xi[i] + 0.5 * ph;
   }
 }
 
@@ -220,7 +254,7 @@ EamP<R> make_params(const ap_config& c) {
   return p;
 }
 
-template <typename R>
+template <typename R, bool STORED>
 void run_eam(ap_ctx* c, const typename Shadow<R>::T* sh, const double* d_lam, double* d_e_fast, double* d_f,
              bool accumulate, cudaStream_t s) {
   constexpr int G = 8;
@@ -228,12 +262,12 @@ void run_eam(ap_ctx* c, const typename Shadow<R>::T* sh, const double* d_lam, do
   int blocks = (int)((c->n * G + threads - 1) / threads);
   EamP<R> p = make_params<R>(c->cfg);
   auto* q = reinterpret_cast<typename Q2<R>::T*>(c->d_q);
-  const int* off = c->stored_off ? c->d_off_eam : nullptr;
-  k_eam_density<R, G><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam, off,
-                                                 c->d_cnt_eam, c->cap_eam, p, d_lam, q, c->d_xi);
-  k_eam_force<R, G><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam, off,
-                                               c->d_cnt_eam, c->cap_eam, p, q, c->d_xi, d_e_fast, d_f,
-                                               accumulate ? 1 : 0);
+  const int* off = STORED ? c->d_off_eam : nullptr;
+  k_eam_density<R, G, STORED><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam,
+                                                         off, c->d_cnt_eam, c->cap_eam, p, d_lam, q, c->d_xi);
+  k_eam_force<R, G, STORED><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam, off,
+                                                       c->d_cnt_eam, c->cap_eam, p, q, c->d_xi, d_e_fast, d_f,
+                                                       accumulate ? 1 : 0);
   c->kernels += 2;
 }
 
@@ -241,10 +275,17 @@ void run_eam(ap_ctx* c, const typename Shadow<R>::T* sh, const double* d_lam, do
 
 void launch_eam(ap_ctx* c, const double* d_lam, double* d_e_fast, double* d_f, bool accumulate, cudaStream_t s) {
   if (c->n <= 0) return;
-  if (c->cfg.precision == AP_PREC_FP64)
-    run_eam<double>(c, c->d_sh64, d_lam, d_e_fast, d_f, accumulate, s);
-  else
-    run_eam<float>(c, c->d_sh32, d_lam, d_e_fast, d_f, accumulate, s);
+  if (c->cfg.precision == AP_PREC_FP64) {
+    if (c->stored_off)
+      run_eam<double, true>(c, c->d_sh64, d_lam, d_e_fast, d_f, accumulate, s);
+    else
+      run_eam<double, false>(c, c->d_sh64, d_lam, d_e_fast, d_f, accumulate, s);
+  } else {
+    if (c->stored_off)
+      run_eam<float, true>(c, c->d_sh32, d_lam, d_e_fast, d_f, accumulate, s);
+    else
+      run_eam<float, false>(c, c->d_sh32, d_lam, d_e_fast, d_f, accumulate, s);
+  }
 }
 
 }  // namespace ap

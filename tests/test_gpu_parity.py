@@ -226,7 +226,7 @@ def test_md_fixed_lambda_energy_conservation_fp64():
     # lambda held constant (update period longer than the run): conservative (section 2.3)
     w = I.config_c1()
     hyb = I.HybridParams(r_lo=2.0, r_hi=3.5, n_csp_avg=1, n_lam_avg=1, sample_every=100000)
-    ctx = ctx_for(w, ap.PREC_FP64, hyb=hyb, dt=1.0)
+    ctx = ctx_for(w, ap.PREC_FP64, hyb=hyb, dt=1.0, rebuild_every=10)
     v0 = I.maxwell_boltzmann(w.mass, np.ones(w.n, bool), 300.0, I.rng_for(1, 3))
     x, v = T(w.x), T(v0)
     f = torch.zeros_like(x)
