@@ -231,6 +231,29 @@ ap_status ap_blend_forces(ap_ctx* ctx, int64_t n, const double* d_lam, const dou
 ap_status ap_step(ap_ctx* ctx, int64_t n, double* d_x, double* d_v, double* d_f, const double* d_mass,
                   const uint8_t* d_fixed, double* d_lam, int64_t nsteps, ap_step_stats* h_stats, void* stream);
 
+/* ----------------------------------------------------------------- allocation-free EAM */
+
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory at all (for instance code that runs inside a
+ * process whose device memory belongs to another runtime's pool, or a
+ * deployment whose memory budget is fixed before it starts).  It computes what
+ * ap_eval_eam computes -- d_e_fast[i] = xi(rho_i) + 1/2 sum_j Phi(r_ij) (written)
+ * and d_f[i] += -grad_i sum_k lambda_k E_k^(f) at fixed lambda (accumulated) --
+ * for one system of at most 32768 atoms, in FP64, with pairs found by brute force
+ * over all atoms and periodic images (O(n^2): meant for small systems).  It needs
+ * no context and calls no allocator.  Only the EAM fields of h_cfg are read.
+ * d_x [n][3], d_lam [n] (NULL = all 1), d_e_fast [n], d_f [n][3]: device
+ * pointers owned by the caller; h_cfg, h_box: host.
+ * Scratch: one fixed array of 32768 x 3 doubles (768 KiB) inside the library,
+ * held by every GPU that loads the library until the process exits.  All calls
+ * share it, so calls whose kernels overlap on the GPU (e.g. on two streams)
+ * race: serialise them.  The first call on each device looks up the array's
+ * device address (with that device current); make that first call before any
+ * stream capture.  Errors: AP_ERR_ARG for n > 32768, n < 0, null pointers or a
+ * bad box/config; AP_ERR_CUDA if the address lookup or a launch fails. */
+ap_status ap_eval_eam_static(const ap_config* h_cfg, int64_t n, const double* d_x, const ap_box* h_box,
+                             const double* d_lam, double* d_e_fast, double* d_f, void* stream);
+
 /* ----------------------------------------------------------------- profiling */
 
 /* Phases timed by ap_step when profiling is on (CUDA events on the call's stream). */

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("ap_eval_ace", I32, [P, I64, P, P, P, P, P, P, P]),
     ("ap_blend_forces", I32, [P, I64, P, P, P, P, P, P]),
     ("ap_step", I32, [P, I64, P, P, P, P, P, P, I64, P, P]),
+    ("ap_eval_eam_static", I32, [P, I64, P, P, P, P, P, P]),
     ("ap_profile_enable", I32, [P, I32]),
     ("ap_profile_read", I32, [P, P, P, P, P, P]),
     ("ap_state_export", I32, [P, P, P]),
