@@ -96,6 +96,12 @@ struct AceTables {
   int n_terms = 0;
   std::vector<double> c1;        // [8] nu = 1 coefficients
   std::vector<double> m2;        // [5][8][8] nu = 2 symmetric coupling matrices
+  // nu = 3 gradient programs: entry (k, lane) at [k * 32 + lane]; packed
+  // b | c << 6 | out << 12 | flush << 24 over the 48 A entries with n <= 2, l <= 3,
+  // value coef: dE3/dA[out] += coef * A[b] * A[c].
+  std::vector<uint32_t> e3_idx;
+  std::vector<double> e3_coef;
+  int e3_len = 0;                // entries per lane program (padded)
 };
 void build_ace_tables(const ap_config& cfg, AceTables& t);
 
@@ -177,8 +183,11 @@ struct ap_ctx {
   int* d_term_idx = nullptr;
   float* d_term_coef32 = nullptr;
   double* d_term_coef64 = nullptr;
-  float* d_W32 = nullptr;        // [5][8][8]
+  float* d_W32 = nullptr;        // [W (320) | M2 (320) | C1 (8)]
   double* d_W64 = nullptr;
+  uint32_t* d_e3_idx = nullptr;  // nu = 3 gradient programs
+  float* d_e3_coef32 = nullptr;
+  double* d_e3_coef64 = nullptr;
 
   // scan scratch
   int* d_scan_tmp = nullptr;

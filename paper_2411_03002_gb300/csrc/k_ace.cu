@@ -17,6 +17,7 @@
 //   stage C  lanes recompute g, g', Y, grad Y per neighbour (no A tiles stored),
 //            contract with u and scatter -w_i p_ij to neighbour j, +w_i sum p to i.
 #include <complex>
+#include <algorithm>
 #include <cmath>
 
 #include "ap_internal.cuh"
@@ -175,6 +176,41 @@ void build_ace_tables(const ap_config& cfg, AceTables& t) {
     if (!any) break;
   }
   t.n_terms = (int)t.term_idx.size();
+
+  // nu = 3 gradient as 32 balanced per-lane programs.  Each term coef*A1*A2*A3
+  // contributes coef*A2*A3 to dE/dA1, coef*A1*A3 to dE/dA2 and coef*A1*A2 to dE/dA3;
+  // the entries are sorted by output, cut into 32 contiguous ranges of equal
+  // length, and a lane flushes its register sum whenever its output changes.
+  auto c48 = [](int a) { return (a / 25) * 16 + (a % 25); };   // n <= 2, lm < 16
+  struct E3 {
+    int out, b, c;
+    double coef;
+  };
+  std::vector<E3> ent;
+  for (int k = 0; k < t.n_terms; ++k) {
+    int pk = t.term_idx[k];
+    int a1 = c48(pk & 255), a2 = c48((pk >> 8) & 255), a3 = c48((pk >> 16) & 255);
+    double cf = t.term_coef[k];
+    ent.push_back({a1, a2, a3, cf});
+    ent.push_back({a2, a1, a3, cf});
+    ent.push_back({a3, a1, a2, cf});
+  }
+  std::stable_sort(ent.begin(), ent.end(), [](const E3& x, const E3& y) { return x.out < y.out; });
+  const int total = (int)ent.size();
+  const int per = (total + 31) / 32;
+  t.e3_len = per;
+  t.e3_idx.assign((size_t)per * 32, 0u);
+  t.e3_coef.assign((size_t)per * 32, 0.0);
+  for (int lane = 0; lane < 32; ++lane) {
+    int b0 = lane * per, b1 = std::min(total, b0 + per);
+    for (int q = b0; q < b1; ++q) {
+      bool flush = (q + 1 == b1) || ent[q + 1].out != ent[q].out;
+      uint32_t p = (uint32_t)ent[q].b | ((uint32_t)ent[q].c << 6) | ((uint32_t)ent[q].out << 12) |
+                   (flush ? (1u << 24) : 0u);
+      t.e3_idx[(size_t)(q - b0) * 32 + lane] = p;
+      t.e3_coef[(size_t)(q - b0) * 32 + lane] = ent[q].coef;
+    }
+  }
 }
 
 // ------------------------------------------------------------------ device code
@@ -183,7 +219,7 @@ namespace {
 constexpr int kCols = 36;            // 32 neighbour slots + 4 pad (16-byte rows, conflict-free)
 constexpr int kRows = 33;            // 8 radial + 25 angular rows
 template <typename R>
-constexpr int kWarps = sizeof(R) == 4 ? 10 : 4;   // warps per CTA: two CTAs fit per SM in FP32
+constexpr int kWarps = sizeof(R) == 4 ? 12 : 4;   // warps per CTA: two CTAs fit per SM in FP32
 
 template <typename R>
 struct V;
@@ -420,6 +456,9 @@ struct AceArgs {
   const int* term_idx;
   const R* term_coef;
   int n_terms;
+  const uint32_t* e3_idx;
+  const R* e3_coef;
+  int e3_len;
   const R* W;
   const R* M2;
   const R* C1;
@@ -433,17 +472,15 @@ struct AceArgs {
 template <typename R, bool FORCES>
 __global__ void __launch_bounds__(kWarps<R> * 32) k_ace(AceArgs<R> a) {
   // Shared memory (every region a multiple of 32 bytes, so 4-wide FP64 loads stay aligned):
-  //   W [320] | M2 [320] | C1 [8] | nu=3 coefficients [t8] | nu=3 indices [t8] |
+  //   W [320] | M2 [320] | C1 [8] |
   //   per warp: compacted neighbours [kListCap][4] | tile [kRows][kCols]
-  // A, dA, U and the G scratch alias the tile once stage A's contraction is done.
+  // A, dA, U, the G scratch and the 48 nu=3 inputs alias the tile once stage A's
+  // contraction is done.  The nu=3 gradient programs stay in global memory (L1).
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int t8 = (a.n_terms + 7) & ~7;
   R* Ws = reinterpret_cast<R*>(smem_raw);
   R* M2 = Ws + 320;
   R* C1 = M2 + 320;
-  R* coef = C1 + 8;
-  int* tidx = reinterpret_cast<int*>(coef + t8);
-  R* wbase = reinterpret_cast<R*>(tidx + t8);
+  R* wbase = C1 + 8;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   R* list = wbase + warp * (4 * kListCap + kRows * kCols);
   R* tile = list + 4 * kListCap;
@@ -451,15 +488,12 @@ __global__ void __launch_bounds__(kWarps<R> * 32) k_ace(AceArgs<R> a) {
   R* dA = tile + 200;
   R* U = tile + 400;
   R* Gs = tile + 600;
+  R* A48 = tile + 800;
   for (int t = threadIdx.x; t < 320; t += blockDim.x) {
     Ws[t] = a.W[t];
     M2[t] = a.M2[t];
   }
   if (threadIdx.x < 8) C1[threadIdx.x] = a.C1[threadIdx.x];
-  for (int t = threadIdx.x; t < a.n_terms; t += blockDim.x) {
-    coef[t] = a.term_coef[t];
-    tidx[t] = a.term_idx[t];
-  }
   __syncthreads();
   const int m = a.sc->n_precise;
   const int kq = lane & 7, grp = lane >> 3;
@@ -562,21 +596,31 @@ __global__ void __launch_bounds__(kWarps<R> * 32) k_ace(AceArgs<R> a) {
     __syncwarp();
 
     // ---------------- stage B: E and dE/dA
-    // nu = 3 terms (atomics into dA), then nu = 2 and nu = 1 per owned output
-    R e = R(0);
-    for (int t = lane; t < a.n_terms; t += 32) {
-      const int pk = tidx[t];
-      const R cf = coef[t];
-      const R A1 = A[pk & 255], A2 = A[(pk >> 8) & 255], A3 = A[(pk >> 16) & 255];
-      const R p12 = cf * A1 * A2;
-      e += p12 * A3;
-      if (FORCES) {
-        atomicAdd(&dA[pk & 255], cf * A2 * A3);
-        atomicAdd(&dA[(pk >> 8) & 255], cf * A1 * A3);
-        atomicAdd(&dA[(pk >> 16) & 255], p12);
+    // nu = 3: each lane runs its gradient program over the 48 A entries with
+    // n <= 2, l <= 3 and flushes one register sum per output; E3 follows from
+    // Euler's identity for a homogeneous cubic, E3 = (1/3) sum_a A_a dE3/dA_a.
+    // Then nu = 2 and nu = 1 for the outputs each lane owns.
+    for (int v = lane; v < 48; v += 32) A48[v] = A[(v >> 4) * 25 + (v & 15)];
+    __syncwarp();
+    {
+      R acc = R(0);
+      const uint32_t* pi = a.e3_idx + lane;
+      const R* pc = a.e3_coef + lane;
+      for (int k = 0; k < a.e3_len; ++k) {
+        const uint32_t p = __ldg(pi + 32 * k);
+        const R cf = __ldg(pc + 32 * k);
+        acc += cf * A48[p & 63u] * A48[(p >> 6) & 63u];
+        if (p & (1u << 24)) {
+          const int o = (int)((p >> 12) & 63u);
+          atomicAdd(&dA[(o >> 4) * 25 + (o & 15)], acc);
+          acc = R(0);
+        }
       }
     }
     __syncwarp();
+    R e = R(0);
+    for (int v = lane; v < 48; v += 32) e += A48[v] * dA[(v >> 4) * 25 + (v & 15)];
+    e *= R(1.0 / 3.0);
     for (int o = lane; o < 200; o += 32) {
       const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
       const R* mrow = &M2[l * 64 + n * 8];
@@ -655,10 +699,8 @@ __global__ void k_ace_finalize64(int n, const double* __restrict__ acc, double* 
 }
 
 template <typename R>
-size_t ace_smem(int n_terms) {
-  size_t t8 = (size_t)((n_terms + 7) & ~7);
-  return sizeof(R) * (320 + 320 + 8) + sizeof(R) * t8 + sizeof(int) * t8 +
-         sizeof(R) * kWarps<R> * (4 * kListCap + kRows * kCols);
+size_t ace_smem() {
+  return sizeof(R) * (320 + 320 + 8) + sizeof(R) * kWarps<R> * (4 * kListCap + kRows * kCols);
 }
 
 template <typename R>
@@ -694,12 +736,18 @@ void run_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_pre
   a.M2 = a.W + 320;   // the parameter block is [W (320) | M2 (320) | C1 (8)]
   a.C1 = a.W + 640;
   a.n_terms = c->ace.n_terms;
+  a.e3_idx = c->d_e3_idx;
+  a.e3_len = c->ace.e3_len;
+  if constexpr (sizeof(R) == 4)
+    a.e3_coef = c->d_e3_coef32;
+  else
+    a.e3_coef = c->d_e3_coef64;
   a.rc2 = (R)(c->cfg.ace_rc * c->cfg.ace_rc);
   a.inv_rc = (R)(1.0 / c->cfg.ace_rc);
   a.inv_n0 = (R)(1.0 / c->cfg.ace_n0);
   a.mode = c->cfg.fcut_mode;
   a.e_prec = d_e_prec;
-  size_t smem = ace_smem<R>(a.n_terms);
+  size_t smem = ace_smem<R>();
   auto kern = forces ? k_ace<R, true> : k_ace<R, false>;
   static int configured[2][2] = {{0, 0}, {0, 0}};
   static int blocks_per_sm[2][2] = {{0, 0}, {0, 0}};
@@ -742,6 +790,14 @@ void upload_ace_tables(ap_ctx* c) {
   cudaMemcpy(c->d_term_coef64, t.term_coef.data(), sizeof(double) * t.n_terms, cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_W32, p32.data(), sizeof(float) * p32.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_W64, p64.data(), sizeof(double) * p64.size(), cudaMemcpyHostToDevice);
+  const size_t ne = t.e3_idx.size();
+  std::vector<float> e32(t.e3_coef.begin(), t.e3_coef.end());
+  cudaMalloc(&c->d_e3_idx, sizeof(uint32_t) * ne);
+  cudaMalloc(&c->d_e3_coef32, sizeof(float) * ne);
+  cudaMalloc(&c->d_e3_coef64, sizeof(double) * ne);
+  cudaMemcpy(c->d_e3_idx, t.e3_idx.data(), sizeof(uint32_t) * ne, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_e3_coef32, e32.data(), sizeof(float) * ne, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_e3_coef64, t.e3_coef.data(), sizeof(double) * ne, cudaMemcpyHostToDevice);
 }
 
 void launch_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_prec, bool forces, cudaStream_t s) {
