@@ -417,7 +417,7 @@ void ap_destroy(ap_ctx* c) {
                   c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected,
                   c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_efast, c->d_eprec,
                   c->d_eatom, c->d_eext, c->d_changeable, c->d_term_idx, c->d_term_coef32, c->d_term_coef64,
-                  c->d_W32, c->d_W64, c->d_e3_idx, c->d_e3_coef32, c->d_e3_coef64, c->d_scan_tmp, c->d_red,
+                  c->d_W32, c->d_W64, c->d_e3_idx, c->d_e3_coef32, c->d_e3_coef64, c->d_e3_pack, c->d_scan_tmp, c->d_red,
                   c->d_sc};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -186,6 +186,7 @@ struct ap_ctx {
   float* d_W32 = nullptr;        // [W (320) | M2 (320) | C1 (8)]
   double* d_W64 = nullptr;
   uint32_t* d_e3_idx = nullptr;  // nu = 3 gradient programs
+  uint2* d_e3_pack = nullptr;    // same, FP32 coefficient packed with the index
   float* d_e3_coef32 = nullptr;
   double* d_e3_coef64 = nullptr;
 

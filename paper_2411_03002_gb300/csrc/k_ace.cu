@@ -11,13 +11,16 @@
 // needs only u_klm = (1/N0) sum_n W[l][n][k] dE/dA_nlm per atom:
 //   dE_i/dr_ij = sum_lm [ (sum_k u_klm g'_k) Y_lm r^ + (sum_k u_klm g_k) grad Y_lm ].
 // One warp per precise atom, persistent CTAs pulling atoms from the queue:
-//   stage A  lanes evaluate g and Y for 32 neighbours into shared memory, then
+//   pass 0   the row entries inside r_c are compacted (j and r_ij) into shared memory;
+//   stage A  lanes evaluate g and Y for 32 neighbours into a shared tile, then
 //            contract G = g^T Y with 4-wide vector loads along the neighbour axis;
-//   stage B  E and dE/dA from a flattened product-term table in shared memory;
+//   stage B  nu=3 through per-lane gradient programs (no atomics per term), nu=2 as
+//            symmetric 8x8 matrix-vector products per (l,m), nu=1 directly;
 //   stage C  lanes recompute g, g', Y, grad Y per neighbour (no A tiles stored),
 //            contract with u and scatter -w_i p_ij to neighbour j, +w_i sum p to i.
 #include <complex>
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 
 #include "ap_internal.cuh"
@@ -458,6 +461,7 @@ struct AceArgs {
   int n_terms;
   const uint32_t* e3_idx;
   const R* e3_coef;
+  const uint2* e3_pack;   // FP32 programs as (index, coefficient bits) pairs
   int e3_len;
   const R* W;
   const R* M2;
@@ -606,9 +610,19 @@ __global__ void __launch_bounds__(kWarps<R> * 32) k_ace(AceArgs<R> a) {
       R acc = R(0);
       const uint32_t* pi = a.e3_idx + lane;
       const R* pc = a.e3_coef + lane;
+      const uint2* pp = a.e3_pack + lane;
+#pragma unroll 4
       for (int k = 0; k < a.e3_len; ++k) {
-        const uint32_t p = __ldg(pi + 32 * k);
-        const R cf = __ldg(pc + 32 * k);
+        uint32_t p;
+        R cf;
+        if constexpr (sizeof(R) == 4) {
+          const uint2 v = __ldg(pp + 32 * k);   // index and FP32 coefficient in one load
+          p = v.x;
+          cf = __uint_as_float(v.y);
+        } else {
+          p = __ldg(pi + 32 * k);
+          cf = __ldg(pc + 32 * k);
+        }
         acc += cf * A48[p & 63u] * A48[(p >> 6) & 63u];
         if (p & (1u << 24)) {
           const int o = (int)((p >> 12) & 63u);
@@ -737,6 +751,7 @@ void run_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_pre
   a.C1 = a.W + 640;
   a.n_terms = c->ace.n_terms;
   a.e3_idx = c->d_e3_idx;
+  a.e3_pack = c->d_e3_pack;
   a.e3_len = c->ace.e3_len;
   if constexpr (sizeof(R) == 4)
     a.e3_coef = c->d_e3_coef32;
@@ -798,6 +813,15 @@ void upload_ace_tables(ap_ctx* c) {
   cudaMemcpy(c->d_e3_idx, t.e3_idx.data(), sizeof(uint32_t) * ne, cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_e3_coef32, e32.data(), sizeof(float) * ne, cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_e3_coef64, t.e3_coef.data(), sizeof(double) * ne, cudaMemcpyHostToDevice);
+  std::vector<uint2> pack(ne);
+  for (size_t k = 0; k < ne; ++k) {
+    float cf = (float)t.e3_coef[k];
+    uint32_t bits;
+    std::memcpy(&bits, &cf, sizeof(bits));
+    pack[k] = make_uint2(t.e3_idx[k], bits);
+  }
+  cudaMalloc(&c->d_e3_pack, sizeof(uint2) * ne);
+  cudaMemcpy(c->d_e3_pack, pack.data(), sizeof(uint2) * ne, cudaMemcpyHostToDevice);
 }
 
 void launch_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_prec, bool forces, cudaStream_t s) {

@@ -33,6 +33,16 @@ __device__ inline double fcut_exact(double x, int mode) {
   return p;
 }
 
+// f_cut in FP32, used only to screen candidates.
+__device__ inline float fcut_f(float x, int mode) {
+  if (x < 0.f) return 1.f;
+  if (x > 1.f) return 0.f;
+  const float t = mode == 1 ? 2.f * x - 1.f : x;
+  const float t2 = t * t;
+  const float p = 1.f - 1.875f * t + 1.25f * t2 * t - 0.375f * t2 * t2 * t;
+  return mode == 1 ? 0.5f * p : p;
+}
+
 // Cell offset k of a row entry.
 __device__ inline void entry_offset(const int* off, size_t e, const SysInfo& S, int wi, int wj, int k[3]) {
   if (off) {
@@ -76,7 +86,35 @@ __device__ inline void image_of(const SysInfo& S, const int4& ci, const int4& cj
   for (int a = 0; a < 3; ++a) s[a] = S.periodic[a] ? (k[a] - (cu_j[a] - cu_i[a])) / S.nc[a] : 0;
 }
 
+// Row position q of atom i's entry -> exact FP64 displacement.
+__device__ inline void exact_entry(const double* __restrict__ x, const SysInfo& S, int i, const int4& ci,
+                                   const int* __restrict__ nbr, const int* __restrict__ off,
+                                   const int4* __restrict__ cunw, size_t row, int q, double d[3], int& j,
+                                   int s[3]) {
+  j = nbr[row + q];
+  const int4 cj = cunw[j];
+  int k[3];
+  entry_offset(off, row + q, S, ci.w, cj.w, k);
+  exact_disp(x, S, i, j, ci, cj, k, d);
+  image_of(S, ci, cj, k, s);
+}
+
+// (r2, j, s) ordering of two row entries with equal or different exact r2.
+__device__ inline bool entry_less(const double* __restrict__ x, const SysInfo& S, int i, const int4& ci,
+                                  const int* __restrict__ nbr, const int* __restrict__ off,
+                                  const int4* __restrict__ cunw, size_t row, double ra, int qa, double rb, int qb) {
+  if (ra != rb) return ra < rb;
+  if (qb < 0) return true;
+  double d[3];
+  int ja, jb, sa[3], sb[3];
+  exact_entry(x, S, i, ci, nbr, off, cunw, row, qa, d, ja, sa);
+  exact_entry(x, S, i, ci, nbr, off, cunw, row, qb, d, jb, sb);
+  return cand_less(ra, ja, sa, rb, jb, sb);
+}
+
 // ------------------------------------------------------------------ CSP
+// One thread per atom.  All selection arrays are indexed with compile-time
+// indices (fully unrolled insertion), so they live in registers.
 __global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x, const uint8_t* __restrict__ ch,
                                              const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
                                              const float4* __restrict__ s32, const int4* __restrict__ cunw,
@@ -105,14 +143,14 @@ __global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x
   }
   int n_in = 0;
   for (int q = 0; q < c; ++q) {
-    int j = nbr[row + q];
-    float4 sj = s32[j];
+    const int j = nbr[row + q];
+    const float4 sj = s32[j];
     int k[3];
     entry_offset(off, row + q, S, ci.w, __float_as_int(sj.w), k);
-    float dx = (float)k[0] * S.hf[0] + sj.x - si.x;
-    float dy = (float)k[1] * S.hf[1] + sj.y - si.y;
-    float dz = (float)k[2] * S.hf[2] + sj.z - si.z;
-    float r2 = dx * dx + dy * dy + dz * dz;
+    const float dx = (float)k[0] * S.hf[0] + sj.x - si.x;
+    const float dy = (float)k[1] * S.hf[1] + sj.y - si.y;
+    const float dz = (float)k[2] * S.hf[2] + sj.z - si.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
     if (r2 > rsf2 + kBand) continue;
     if (r2 >= rsf2 - kBand) {
       double d[3];
@@ -121,143 +159,152 @@ __global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x
     }
     ++n_in;
     if (r2 < tr[kNN]) {
-      int p = kNN;
-      while (p > 0 && tr[p - 1] > r2) {
-        tr[p] = tr[p - 1];
-        tq[p] = tq[p - 1];
-        --p;
+      tr[kNN] = r2;
+      tq[kNN] = q;
+#pragma unroll
+      for (int p = kNN; p > 0; --p) {
+        if (tr[p] < tr[p - 1]) {
+          const float t = tr[p];
+          tr[p] = tr[p - 1];
+          tr[p - 1] = t;
+          const int u = tq[p];
+          tq[p] = tq[p - 1];
+          tq[p - 1] = u;
+        }
       }
-      tr[p] = r2;
-      tq[p] = q;
     }
   }
   if (n_in < kNN) {
     csp[i] = INFINITY;
     return;
   }
-  // 2. exact selection when the 12/13 boundary lies within the guard band
-  bool exact_sel = (n_in > kNN) && (tr[kNN] - tr[kNN - 1] <= 2.f * kBand);
-  if (exact_sel) {
+  // 2. exact (r2, j, s) selection when the 12/13 boundary lies within the guard band
+  if (n_in > kNN && tr[kNN] - tr[kNN - 1] <= 2.f * kBand) {
     double br[kNN];
-    int bj[kNN], bs[kNN][3], bq[kNN];
+    int bq[kNN];
+#pragma unroll
     for (int a = 0; a < kNN; ++a) {
       br[a] = INFINITY;
-      bj[a] = 0x7fffffff;
       bq[a] = -1;
-      bs[a][0] = bs[a][1] = bs[a][2] = 0x7fffffff;
     }
     for (int q = 0; q < c; ++q) {
-      int j = nbr[row + q];
-      int4 cj = cunw[j];
-      int k[3];
-      entry_offset(off, row + q, S, ci.w, cj.w, k);
       double d[3];
-      exact_disp(x, S, i, j, ci, cj, k, d);
-      double r2 = norm2_exact(d);
+      int j, s[3];
+      exact_entry(x, S, i, ci, nbr, off, cunw, row, q, d, j, s);
+      const double r2 = norm2_exact(d);
       if (!(r2 < rs2)) continue;
-      int s[3];
-      image_of(S, ci, cj, k, s);
-      if (!cand_less(r2, j, s, br[kNN - 1], bj[kNN - 1], bs[kNN - 1])) continue;
-      int p = kNN - 1;
-      while (p > 0 && cand_less(r2, j, s, br[p - 1], bj[p - 1], bs[p - 1])) {
-        br[p] = br[p - 1];
-        bj[p] = bj[p - 1];
-        bq[p] = bq[p - 1];
-        bs[p][0] = bs[p - 1][0];
-        bs[p][1] = bs[p - 1][1];
-        bs[p][2] = bs[p - 1][2];
-        --p;
+      if (!entry_less(x, S, i, ci, nbr, off, cunw, row, r2, q, br[kNN - 1], bq[kNN - 1])) continue;
+      br[kNN - 1] = r2;
+      bq[kNN - 1] = q;
+#pragma unroll
+      for (int p = kNN - 1; p > 0; --p) {
+        if (entry_less(x, S, i, ci, nbr, off, cunw, row, br[p], bq[p], br[p - 1], bq[p - 1])) {
+          const double t = br[p];
+          br[p] = br[p - 1];
+          br[p - 1] = t;
+          const int u = bq[p];
+          bq[p] = bq[p - 1];
+          bq[p - 1] = u;
+        }
       }
-      br[p] = r2;
-      bj[p] = j;
-      bq[p] = q;
-      bs[p][0] = s[0];
-      bs[p][1] = s[1];
-      bs[p][2] = s[2];
     }
+#pragma unroll
     for (int a = 0; a < kNN; ++a) tq[a] = bq[a];
   }
-  // 3. vectors of the 12 (FP32 for the pair selection)
+  // 3. FP32 vectors of the 12 and the 7 smallest pair values |r_a + r_b|^2
   float vx[kNN], vy[kNN], vz[kNN];
+#pragma unroll
   for (int a = 0; a < kNN; ++a) {
-    int j = nbr[row + tq[a]];
-    float4 sj = s32[j];
+    const int j = nbr[row + tq[a]];
+    const float4 sj = s32[j];
     int k[3];
     entry_offset(off, row + tq[a], S, ci.w, __float_as_int(sj.w), k);
     vx[a] = (float)k[0] * S.hf[0] + sj.x - si.x;
     vy[a] = (float)k[1] * S.hf[1] + sj.y - si.y;
     vz[a] = (float)k[2] * S.hf[2] + sj.z - si.z;
   }
-  // 4. the 7 smallest FP32 pair values |r_a + r_b|^2
   float pv[kHalf + 1];
-  int pc[kHalf + 1];
+  int pc[kHalf + 1];   // row positions qa | qb << 16
+#pragma unroll
   for (int a = 0; a <= kHalf; ++a) {
     pv[a] = INFINITY;
-    pc[a] = -1;
+    pc[a] = 0;
   }
+#pragma unroll
   for (int a = 0; a < kNN; ++a)
+#pragma unroll
     for (int b = a + 1; b < kNN; ++b) {
-      float sx = vx[a] + vx[b], sy = vy[a] + vy[b], sz = vz[a] + vz[b];
-      float v = sx * sx + sy * sy + sz * sz;
+      const float sx = vx[a] + vx[b], sy = vy[a] + vy[b], sz = vz[a] + vz[b];
+      const float v = sx * sx + sy * sy + sz * sz;
       if (v < pv[kHalf]) {
-        int p = kHalf;
-        while (p > 0 && pv[p - 1] > v) {
-          pv[p] = pv[p - 1];
-          pc[p] = pc[p - 1];
-          --p;
+        pv[kHalf] = v;
+        pc[kHalf] = tq[a] | (tq[b] << 16);
+#pragma unroll
+        for (int p = kHalf; p > 0; --p) {
+          if (pv[p] < pv[p - 1]) {
+            const float t = pv[p];
+            pv[p] = pv[p - 1];
+            pv[p - 1] = t;
+            const int u = pc[p];
+            pc[p] = pc[p - 1];
+            pc[p - 1] = u;
+          }
         }
-        pv[p] = v;
-        pc[p] = a * 16 + b;
       }
     }
-  // exact vectors of the 12 (FP64) computed on demand
-  auto exact_vec = [&](int a, double d[3]) {
-    int q = tq[a];
-    int j = nbr[row + q];
-    int4 cj = cunw[j];
-    int k[3];
-    entry_offset(off, row + q, S, ci.w, cj.w, k);
-    exact_disp(x, S, i, j, ci, cj, k, d);
-  };
+  // 4. exact values of the six smallest pairs (all 66 in FP64 if the 6/7 boundary is ambiguous)
   double chosen[kHalf];
   if (pv[kHalf] - pv[kHalf - 1] > 2.f * kBand) {
+#pragma unroll
     for (int t = 0; t < kHalf; ++t) {
       double da[3], db[3];
-      exact_vec(pc[t] >> 4, da);
-      exact_vec(pc[t] & 15, db);
-      double s3[3] = {__dadd_rn(da[0], db[0]), __dadd_rn(da[1], db[1]), __dadd_rn(da[2], db[2])};
+      int ja, jb, sa[3], sb[3];
+      exact_entry(x, S, i, ci, nbr, off, cunw, row, pc[t] & 0xffff, da, ja, sa);
+      exact_entry(x, S, i, ci, nbr, off, cunw, row, pc[t] >> 16, db, jb, sb);
+      const double s3[3] = {__dadd_rn(da[0], db[0]), __dadd_rn(da[1], db[1]), __dadd_rn(da[2], db[2])};
       chosen[t] = norm2_exact(s3);
     }
   } else {
-    // all 66 in FP64, keep the 6 smallest
+#pragma unroll
     for (int t = 0; t < kHalf; ++t) chosen[t] = INFINITY;
     double ex[kNN][3];
-    for (int a = 0; a < kNN; ++a) exact_vec(a, ex[a]);
+#pragma unroll
+    for (int a = 0; a < kNN; ++a) {
+      int j, s[3];
+      exact_entry(x, S, i, ci, nbr, off, cunw, row, tq[a], ex[a], j, s);
+    }
+#pragma unroll
     for (int a = 0; a < kNN; ++a)
+#pragma unroll
       for (int b = a + 1; b < kNN; ++b) {
-        double s3[3] = {__dadd_rn(ex[a][0], ex[b][0]), __dadd_rn(ex[a][1], ex[b][1]), __dadd_rn(ex[a][2], ex[b][2])};
-        double v = norm2_exact(s3);
+        const double s3[3] = {__dadd_rn(ex[a][0], ex[b][0]), __dadd_rn(ex[a][1], ex[b][1]),
+                              __dadd_rn(ex[a][2], ex[b][2])};
+        const double v = norm2_exact(s3);
         if (v < chosen[kHalf - 1]) {
-          int p = kHalf - 1;
-          while (p > 0 && chosen[p - 1] > v) {
-            chosen[p] = chosen[p - 1];
-            --p;
+          chosen[kHalf - 1] = v;
+#pragma unroll
+          for (int p = kHalf - 1; p > 0; --p) {
+            if (chosen[p] < chosen[p - 1]) {
+              const double t = chosen[p];
+              chosen[p] = chosen[p - 1];
+              chosen[p - 1] = t;
+            }
           }
-          chosen[p] = v;
         }
       }
   }
   // 5. ascending sum of the six values
-  for (int a = 1; a < kHalf; ++a) {
-    double t = chosen[a];
-    int p = a - 1;
-    while (p >= 0 && chosen[p] > t) {
-      chosen[p + 1] = chosen[p];
-      --p;
-    }
-    chosen[p + 1] = t;
-  }
+#pragma unroll
+  for (int a = 1; a < kHalf; ++a)
+#pragma unroll
+    for (int p = a; p > 0; --p)
+      if (chosen[p] < chosen[p - 1]) {
+        const double t = chosen[p];
+        chosen[p] = chosen[p - 1];
+        chosen[p - 1] = t;
+      }
   double sum = chosen[0];
+#pragma unroll
   for (int a = 1; a < kHalf; ++a) sum = __dadd_rn(sum, chosen[a]);
   csp[i] = sum;
 }
@@ -324,6 +371,7 @@ __global__ void __launch_bounds__(256) k_spread(const int* __restrict__ det, con
   const double rh2 = __dmul_rn(r_hi, r_hi);
   const float rhf2 = (float)rh2;
   const double width = __dsub_rn(r_hi, r_lo);
+  const float r_lo_f = (float)r_lo, inv_w_f = (float)(1.0 / width);
   const int wx = 2 * sx + 1, wy = 2 * sy + 1, wz = 2 * sz + 1;
   const int ncell = wx * wy * wz;
   for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < m; w += warps) {
@@ -332,6 +380,7 @@ __global__ void __launch_bounds__(256) k_spread(const int* __restrict__ det, con
     const float4 si = s32[i];
     const int4 ci = cunw[i];
     const double one_minus = __dsub_rn(1.0, lam0[i]);
+    const float one_minus_f = (float)one_minus;
     const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
     for (int t = lane; t < ncell; t += 32) {
       int dx = t % wx - sx;
@@ -366,6 +415,13 @@ __global__ void __launch_bounds__(256) k_spread(const int* __restrict__ det, con
         float ddx = ox + sj.x, ddy = oy + sj.y, ddz = oz + sj.z;
         float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
         if (r2f > rhf2 + kBand) continue;
+        // FP32 estimate of the candidate value (error < 1e-5): if even its lower
+        // bound cannot go below the current lambda_min,j (which only decreases),
+        // the exact evaluation cannot change the final minimum; skip it.
+        {
+          const float vf = 1.f - one_minus_f * fcut_f((sqrtf(r2f) - r_lo_f) * inv_w_f, mode);
+          if ((double)vf - 1e-4 >= __ldcg(&lam_min[j])) continue;
+        }
         int4 cj = cunw[j];
         double d[3];
         // image relative to the input positions: S = img + nwrap_i - nwrap_j

@@ -193,7 +193,83 @@ __device__ inline bool exact_within(const double* __restrict__ x, const SysInfo&
   return r2 < rc2;
 }
 
-// Scan the 5x5x5 stencil around atom i and append accepted (j, offset) to a row.
+// One warp builds one row (used for the long ACE rows): lanes take stencil cells (5x5x5 around atom i, pruned
+// by the cell-box distance), iterate their cells' atoms in lock-step and append
+// accepted (j, offset) with ballot compaction.  Entry order: (cell round, atom
+// slot, lane) -- deterministic.  Returns the full count (may exceed cap).
+__device__ inline int build_row_warp(int i, const double* __restrict__ x, const SysInfo& S,
+                                     const float4* __restrict__ s32, const int4* __restrict__ cunw,
+                                     const int* __restrict__ cstart, const int* __restrict__ catoms, float rcf2,
+                                     double rc2, float band, int cap, int* __restrict__ row,
+                                     int* __restrict__ offrow) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const float4 si = s32[i];
+  const int4 ci = cunw[i];
+  const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
+  const float rmax2 = rcf2 + band;
+  constexpr int W = 2 * kStencil + 1;
+  int cnt = 0;
+  for (int t0 = 0; t0 < W * W * W; t0 += 32) {
+    const int t = t0 + lane;
+    const int dx = t % W - kStencil, dy = (t / W) % W - kStencil, dz = t / (W * W) - kStencil;
+    int tc[3] = {cw[0] + dx, cw[1] + dy, cw[2] + dz};
+    int img[3] = {0, 0, 0};
+    bool valid = t < W * W * W;
+    for (int d = 0; d < 3 && valid; ++d) {
+      if (S.periodic[d]) {
+        img[d] = floor_div(tc[d], S.nc[d]);
+        tc[d] -= img[d] * S.nc[d];
+      } else if (tc[d] < 0 || tc[d] >= S.nc[d]) {
+        valid = false;
+      }
+    }
+    if (valid) {
+      const float gx = fmaxf(0.f, fmaxf((float)dx * S.hf[0] - si.x, si.x - (float)(dx + 1) * S.hf[0]));
+      const float gy = fmaxf(0.f, fmaxf((float)dy * S.hf[1] - si.y, si.y - (float)(dy + 1) * S.hf[1]));
+      const float gz = fmaxf(0.f, fmaxf((float)dz * S.hf[2] - si.z, si.z - (float)(dz + 1) * S.hf[2]));
+      valid = gx * gx + gy * gy + gz * gz <= rmax2;
+    }
+    int b = 0, len = 0;
+    if (valid) {
+      const int cid = S.cell_base + (tc[2] * S.nc[1] + tc[1]) * S.nc[0] + tc[0];
+      b = cstart[cid];
+      len = cstart[cid + 1] - b;
+    }
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    const float ox = (float)dx * S.hf[0] - si.x;
+    const float oy = (float)dy * S.hf[1] - si.y;
+    const float oz = (float)dz * S.hf[2] - si.z;
+    const bool self_cell = dx == 0 && dy == 0 && dz == 0;
+    for (int k = 0; k < maxlen; ++k) {
+      bool take = false;
+      int j = 0;
+      if (k < len) {
+        j = catoms[b + k];
+        if (!(j == i && self_cell)) {
+          const float4 sj = s32[j];
+          const float ddx = ox + sj.x, ddy = oy + sj.y, ddz = oz + sj.z;
+          const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
+          if (r2f < rcf2 - band) {
+            take = true;
+          } else if (r2f <= rcf2 + band) {
+            take = exact_within(x, S, i, j, ci, cunw[j], img, rc2);
+          }
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, take);
+      const int pos = cnt + __popc(m & lt);
+      if (take && pos < cap) {
+        row[pos] = j;
+        if (offrow) offrow[pos] = pack_off(dx, dy, dz);
+      }
+      cnt += __popc(m);
+    }
+  }
+  return cnt;
+}
+
+// One thread builds one row (EAM rows of all atoms): scan the 5x5x5 stencil around atom i and append accepted (j, offset) to a row.
 __device__ inline int build_row(int i, const double* __restrict__ x, const SysInfo& S, const float4* __restrict__ s32,
                                 const int4* __restrict__ cunw, const int* __restrict__ cstart,
                                 const int* __restrict__ catoms, float rcf2, double rc2, float band, int cap,
@@ -281,22 +357,26 @@ __global__ void k_build_eam(int n, const double* __restrict__ x, const SysInfo* 
   }
 }
 
-__global__ void k_build_ace(const int* __restrict__ queue, const int* __restrict__ nq, const double* __restrict__ x,
-                            const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
-                            const float4* __restrict__ s32, const int4* __restrict__ cunw,
-                            const int* __restrict__ cstart, const int* __restrict__ catoms, float rcf2, double rc2,
-                            float band, int cap, int* __restrict__ nbr, int* __restrict__ off, int* __restrict__ cnt,
-                            DevScalars* sc) {
+__global__ void __launch_bounds__(256) k_build_ace(const int* __restrict__ queue, const int* __restrict__ nq,
+                                                   const double* __restrict__ x, const SysInfo* __restrict__ sys,
+                                                   const int* __restrict__ atom_sys, const float4* __restrict__ s32,
+                                                   const int4* __restrict__ cunw, const int* __restrict__ cstart,
+                                                   const int* __restrict__ catoms, float rcf2, double rc2,
+                                                   float band, int cap, int* __restrict__ nbr, int* __restrict__ off,
+                                                   int* __restrict__ cnt, DevScalars* sc) {
   const int m = *nq;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
-    int i = queue[q];
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < m; q += warps) {
+    const int i = queue[q];
     const SysInfo& S = sys_of(sys, atom_sys, i);
-    int c = build_row(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, band, cap, nbr + (size_t)q * cap,
-                      off ? off + (size_t)q * cap : nullptr);
-    cnt[q] = c < cap ? c : cap;
-    if (c > cap) {
-      atomicMax(&sc->need_ace, c);
-      atomicOr(&sc->err, kErrCapacity);
+    const int c = build_row_warp(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, band, cap, nbr + (size_t)q * cap,
+                                 off ? off + (size_t)q * cap : nullptr);
+    if ((threadIdx.x & 31) == 0) {
+      cnt[q] = c < cap ? c : cap;
+      if (c > cap) {
+        atomicMax(&sc->need_ace, c);
+        atomicOr(&sc->err, kErrCapacity);
+      }
     }
   }
 }
@@ -388,7 +468,7 @@ void launch_build_ace(ap_ctx* c, const double* d_x, const int* d_queue, const in
   double r = c->cfg.ace_rc + c->cfg.skin;
   double rc2 = r * r;
   int grid = c->num_sms * 8;
-  k_build_ace<<<grid, 128, 0, s>>>(d_queue, d_nq, d_x, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
+  k_build_ace<<<grid, 256, 0, s>>>(d_queue, d_nq, d_x, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
                                    c->d_cell_start, c->d_cell_atoms, (float)rc2, rc2, kBand, c->cap_ace,
                                    c->d_nbr_ace, c->stored_off ? c->d_off_ace : nullptr, c->d_cnt_ace, c->d_sc);
   c->kernels += 1;
