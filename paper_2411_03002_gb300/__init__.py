@@ -6,7 +6,8 @@ include/ap.h).  This package is its Python binding.
 from .api import (Context, StepStats, ace_basis_desc, ace_gaunt, ace_nbasis, ap_blend_forces, ap_build_neighbors,
                   ap_classify, ap_create, ap_eval_ace, ap_eval_eam, ap_step, make_box, make_config)
 from ._native import ApConfig, ApError, PREC_FP64, PREC_MIXED
+from . import autograd
 
 __all__ = ["Context", "StepStats", "ApConfig", "ApError", "PREC_FP64", "PREC_MIXED", "make_box", "make_config",
            "ace_nbasis", "ace_basis_desc", "ace_gaunt", "ap_create", "ap_build_neighbors", "ap_classify",
-           "ap_eval_eam", "ap_eval_ace", "ap_blend_forces", "ap_step"]
+           "ap_eval_eam", "ap_eval_ace", "ap_blend_forces", "ap_step", "autograd"]

@@ -1,0 +1,65 @@
+"""torch.autograd.Function over the CUDA energy kernels.
+
+forward:  E_tot = sum_i [lambda_i E_i^(f) + (1 - lambda_i) E_i^(p)]  (Eq. energy_hyb) at
+          fixed lambda, from ap_eval_eam and the energy-only ACE kernel (no adjoint);
+backward: dE_tot/dx = -F with F the fixed-lambda force of Eq. F_i_d, from the
+          hand-written adjoint kernels (ap_eval_eam force pass and the ACE force
+          stage).  The A-basis is recomputed in backward, not stored.
+
+lambda is an input that receives no gradient (the paper neglects grad lambda).  The
+neighbour rows are rebuilt for every new x inside forward, so the function can be
+called on arbitrary positions (finite differences, optimisers).
+"""
+from __future__ import annotations
+
+import torch
+
+from .api import Context
+
+
+def _queue(lam: torch.Tensor):
+    idx = torch.nonzero(lam < 1.0).flatten().to(torch.int32).contiguous()
+    cnt = torch.tensor([idx.numel()], dtype=torch.int64, device=lam.device)
+    if idx.numel() == 0:
+        idx = torch.zeros(1, dtype=torch.int32, device=lam.device)
+    return idx, cnt
+
+
+class APEnergy(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, x: torch.Tensor, lam: torch.Tensor, ctx: Context, box=None, batch=None):
+        x = x.detach().contiguous()
+        lam = lam.detach().contiguous()
+        if batch is not None:
+            offsets, boxes = batch
+            ctx.build_neighbors_batch(x, offsets, boxes)
+        else:
+            ctx.build_neighbors(x, box)
+        idx, cnt = _queue(lam)
+        e_fast, _ = ctx.eval_eam(x, lam)
+        e_prec, _ = ctx.eval_ace(x, lam, idx, cnt, forces=False)
+        _, e_tot = ctx.blend_forces(lam, e_fast, e_prec)
+        fctx.save_for_backward(x, lam)
+        fctx.apctx = ctx
+        fctx.box = box
+        fctx.batch = batch
+        return e_tot[0].clone()
+
+    @staticmethod
+    def backward(fctx, grad_out: torch.Tensor):
+        x, lam = fctx.saved_tensors
+        ctx = fctx.apctx
+        if fctx.batch is not None:
+            ctx.build_neighbors_batch(x, *fctx.batch)
+        else:
+            ctx.build_neighbors(x, fctx.box)
+        idx, cnt = _queue(lam)
+        _, f = ctx.eval_eam(x, lam)
+        _, f = ctx.eval_ace(x, lam, idx, cnt, f=f)
+        return (-grad_out * f, None, None, None, None)
+
+
+def energy(x: torch.Tensor, lam: torch.Tensor, ctx: Context, box=None, batch=None) -> torch.Tensor:
+    """Total blended energy with a gradient w.r.t. x through the adjoint kernels.
+    batch = (offsets, boxes) evaluates independent cells in one launch."""
+    return APEnergy.apply(x, lam, ctx, box, batch)

@@ -1,0 +1,108 @@
+"""Parity at the full benchmark size (needs a GPU).
+
+The 4,000,000-atom nanoindentation-shaped slab is prepared exactly as bench.py
+times it (mixed precision, Hyb2, lambda every 10 steps, indenter), and sampled
+atoms are checked against the oracle evaluated on local clusters:
+  * lambda (and CSP, lambda_0) of the sampled atom: bit-exact, from a cluster of
+    radius 28 A (the 20 A spread radius plus the 6.5 A CSP search around every
+    atom that can reach the centre);
+  * the force on the sampled atom: within 1 meV/A, from a 16 A cluster (EAM needs
+    densities of neighbours within 5.5 A, ACE needs site energies within 7 A).
+Samples keep 30 A from the periodic x/y edges so that no image shift enters the
+cluster coordinates and the FP64 displacements are the ones the GPU computes.
+"""
+import numpy as np
+import pytest
+import torch
+
+import ap_inputs as I
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_2411_03002_gb300 as ap
+
+
+def open_cluster(x, centre_idx, radius):
+    d = x - x[centre_idx][None, :]
+    sel = np.nonzero((d * d).sum(1) < radius * radius)[0]
+    xc = x[sel]
+    box = I.Box(lo=xc.min(0) - 20.0, hi=xc.max(0) + 20.0, periodic=np.array([False, False, False]))
+    k0 = int(np.nonzero(sel == centre_idx)[0][0])
+    return xc, sel, k0, box
+
+
+@pytest.fixture(scope="module")
+def prepared():
+    w = I.config_c5(100, hyb=I.HYB2)
+    cfg = ap.make_config(I.eam_params(0), I.ace_params(0), w.hyb, precision=ap.PREC_MIXED, indenter=w.indenter,
+                         lambda_every=10, dt=w.dt)
+    ctx = ap.Context(cfg)
+    dev = "cuda"
+    x = torch.as_tensor(w.x, device=dev).clone()
+    v = torch.as_tensor(w.v, device=dev).clone()
+    f = torch.zeros((w.n, 3), dtype=torch.float64, device=dev)
+    lam = torch.empty(w.n, dtype=torch.float64, device=dev)
+    ctx.build_neighbors(x, w.box)
+    stats = ctx.step(x, v, f, torch.as_tensor(w.mass, device=dev), torch.as_tensor(w.fixed, device=dev), lam, 0)
+    st = ctx.get_lambda_state()
+    out = dict(w=w, x=x.cpu().numpy(), f=f.cpu().numpy(), lam=lam.cpu().numpy(),
+               csp=st["csp"].cpu().numpy(), lam0=st["lam0"].cpu().numpy(), stats=stats)
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def samples(p, count_each=8):
+    w = p["w"]
+    x = p["x"]
+    L = w.box.hi - w.box.lo
+    inner = (x[:, 0] > 30.0) & (x[:, 0] < L[0] - 30.0) & (x[:, 1] > 30.0) & (x[:, 1] < L[1] - 30.0)
+    g = np.random.Generator(np.random.PCG64(I.seed_for(5, 9)))
+    groups = [np.nonzero(inner & (p["lam0"] < 1.0))[0],            # detected (surface)
+              np.nonzero(inner & (p["lam"] < 1.0) & (p["lam"] > 0.0))[0],   # switching zone
+              np.nonzero(inner & (p["lam"] == 0.0))[0],              # precise
+              np.nonzero(inner & (p["lam"] == 1.0))[0]]              # fast bulk
+    out = []
+    for grp in groups:
+        if len(grp):
+            out.extend(g.choice(grp, size=min(count_each, len(grp)), replace=False).tolist())
+    return out
+
+
+def test_precise_fraction_in_expected_range(prepared):
+    s = prepared["stats"]
+    frac = s.n_precise / prepared["w"].n
+    assert 0.02 < frac < 0.10, frac
+    assert s.n_detected > 0
+
+
+def test_lambda_bit_exact_on_samples(prepared):
+    w = prepared["w"]
+    x = prepared["x"]
+    for i in samples(prepared, 6):
+        xc, sel, k0, box = open_cluster(x, i, 28.0)
+        ch = (w.fixed[sel] == 0).astype(np.uint8)
+        st = O.LambdaState(len(sel), w.hyb.n_csp_avg, w.hyb.n_lam_avg)
+        lam_o, l0_o, csp_o, *_ = O.classify(st, xc, box, w.hyb, changeable=ch)
+        assert csp_o[k0] == prepared["csp"][i], i
+        assert l0_o[k0] == prepared["lam0"][i], i
+        assert lam_o[k0] == prepared["lam"][i], i
+
+
+def test_forces_on_samples_mixed(prepared):
+    w = prepared["w"]
+    x = prepared["x"]
+    ace = O.ACE(I.ace_params(0))
+    p = I.eam_params(0)
+    worst = 0.0
+    for i in samples(prepared, 6):
+        xc, sel, k0, box = open_cluster(x, i, 16.0)
+        e, f, _, _ = O.hybrid(xc, box, prepared["lam"][sel], p, ace)
+        fi = f[k0].copy()
+        _, fi_ind = O.indenter(xc[k0:k0 + 1], w.indenter.center0, w.indenter.radius, w.indenter.k)
+        fi += fi_ind[0]
+        d = float(np.linalg.norm(prepared["f"][i] - fi))
+        worst = max(worst, d)
+    assert worst <= 1e-3, worst
