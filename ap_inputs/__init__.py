@@ -156,6 +156,25 @@ def ace_params(seed_config: int = 0, k: int = 2, c_std: float = 0.01) -> ACEPara
     return ACEParams(W=W, c=c)
 
 
+ANCHOR_FILE = __import__("os").path.join(__import__("os").path.dirname(__file__), "ace_anchor.npz")
+
+
+def ace_params_anchored() -> ACEParams:
+    """EAM-anchored ACE for the molecular-dynamics workloads: the stored
+    coefficients c = c_fit + N(0, 0.01^2) written by oracle/fit_ace_anchor.py (a
+    ridge fit of the linear ACE to the synthetic EAM on bulk snapshots) with the
+    same radial mixing W as ace_params(0).  Loaded from a data file; nothing is
+    computed here."""
+    d = np.load(ANCHOR_FILE)
+    return ACEParams(W=np.array(d["W"]), c=np.array(d["c"]))
+
+
+def ace_for_config(config: int) -> ACEParams:
+    """Random coefficients for the single-evaluation cells (1, 3), anchored ones
+    for the dynamics workloads (2, 4, 5)."""
+    return ace_params_anchored() if config in (2, 4, 5) else ace_params(0)
+
+
 def maxwell_boltzmann(mass: np.ndarray, mobile: np.ndarray, T: float, g: np.random.Generator) -> np.ndarray:
     """v ~ N(0, kT/m) per component, COM removed, rescaled to T with 3N_mobile - 3 DOF."""
     n = mass.shape[0]

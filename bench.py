@@ -122,7 +122,7 @@ def oracle_sample(hyb: I.HybridParams, reps: int = 1):
     import oracle as O
     w = I.config_c5(100, hyb=hyb, nxy=6)
     ch = (w.fixed == 0).astype(np.uint8)
-    eam, ace = I.eam_params(0), O.ACE(I.ace_params(0))
+    eam, ace = I.eam_params(0), O.ACE(I.ace_for_config(5))
     times = []
     for _ in range(reps):
         st = O.LambdaState(w.n, hyb.n_csp_avg, hyb.n_lam_avg)
@@ -165,7 +165,7 @@ def run_ours(args, ws, rank, local):
     prec = ap.PREC_MIXED if args.precision == "mixed" else ap.PREC_FP64
     w = I.config_c5(args.ncell, hyb=I.HYB2)
     hyb = hyb_for(args.mode, w.hyb)
-    eam, acep = I.eam_params(0), I.ace_params(0)
+    eam, acep = I.eam_params(0), I.ace_for_config(5)
 
     def new_ctx(h, p=prec):
         return ap.Context(ap.make_config(eam, acep, h, precision=p, indenter=w.indenter, lambda_every=MD_PER_STEP,

@@ -36,7 +36,7 @@ def open_cluster(x, centre_idx, radius):
 @pytest.fixture(scope="module")
 def prepared():
     w = I.config_c5(100, hyb=I.HYB2)
-    cfg = ap.make_config(I.eam_params(0), I.ace_params(0), w.hyb, precision=ap.PREC_MIXED, indenter=w.indenter,
+    cfg = ap.make_config(I.eam_params(0), I.ace_for_config(5), w.hyb, precision=ap.PREC_MIXED, indenter=w.indenter,
                          lambda_every=10, dt=w.dt)
     ctx = ap.Context(cfg)
     dev = "cuda"
@@ -94,7 +94,7 @@ def test_lambda_bit_exact_on_samples(prepared):
 def test_forces_on_samples_mixed(prepared):
     w = prepared["w"]
     x = prepared["x"]
-    ace = O.ACE(I.ace_params(0))
+    ace = O.ACE(I.ace_for_config(5))
     p = I.eam_params(0)
     worst = 0.0
     for i in samples(prepared, 6):

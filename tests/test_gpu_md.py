@@ -1,0 +1,94 @@
+"""Molecular dynamics on the 32,000-atom slab with the EAM-anchored ACE (needs a GPU).
+
+* Full ACE (every atom precise) at fixed lambda, FP64, 200 steps of 1 fs from
+  300 K: the dynamics is conservative (section 2.3), so |E(t) - E(0)|/N stays
+  below 1e-4 eV/atom and nothing blows up at the free surfaces.
+The 0.3 A-disordered hemisphere melts in the first ~50 fs (atoms move ~0.05 A/fs
+there, with EAM as with ACE), so the lists are rebuilt every 5 steps to keep
+every displacement between rebuilds below skin/2 = 0.5 A.
+* Adaptive run (Hyb1, lambda every 10 steps) for 200 steps in FP64 and in mixed
+  precision from the same start: both stay finite, the precise fraction stays in
+  a sane range, and the final FP64 forces match the oracle on sampled atoms
+  (same tolerance as the other FP64 parity tests), the mixed ones within 1 meV/A.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import ap_inputs as I
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_2411_03002_gb300 as ap
+
+
+def run(w, hyb, prec, nsteps, lambda_every, rebuild_every=5):
+    cfg = ap.make_config(I.eam_params(0), I.ace_for_config(2), hyb, precision=prec, dt=w.dt,
+                         lambda_every=lambda_every, rebuild_every=rebuild_every)
+    ctx = ap.Context(cfg)
+    x = torch.as_tensor(w.x, device="cuda").clone()
+    v = torch.as_tensor(w.v, device="cuda").clone()
+    f = torch.zeros_like(x)
+    lam = torch.empty(w.n, dtype=torch.float64, device="cuda")
+    m = torch.as_tensor(w.mass, device="cuda")
+    ctx.build_neighbors(x, w.box)
+    s0 = ctx.step(x, v, f, m, None, lam, 0)
+    s1 = ctx.step(x, v, f, m, None, lam, nsteps)
+    return s0, s1, x.cpu().numpy(), f.cpu().numpy(), lam.cpu().numpy()
+
+
+def test_full_ace_nve_is_stable_fp64():
+    w = I.config_c2()
+    hyb = dataclasses.replace(w.hyb, csp_lo=-2.0, csp_hi=-1.0)      # every atom detected: lambda = 0
+    s0, s1, x, f, lam = run(w, hyb, ap.PREC_FP64, 200, lambda_every=10 ** 6)
+    assert np.all(lam == 0.0)
+    drift = abs((s1.e_pot + s1.e_kin) - (s0.e_pot + s0.e_kin)) / w.n
+    assert np.isfinite(s1.e_pot) and drift < 1e-4, drift
+    assert s1.max_disp < 0.5
+
+
+@pytest.fixture(scope="module")
+def adaptive_runs():
+    w = I.config_c2()
+    return w, run(w, w.hyb, ap.PREC_FP64, 200, 10), run(w, w.hyb, ap.PREC_MIXED, 200, 10)
+
+
+def test_adaptive_runs_fp64_and_mixed(adaptive_runs):
+    w, r64, r32 = adaptive_runs
+    for s0, s1, x, f, lam in (r64, r32):
+        assert np.isfinite(s1.e_pot) and np.isfinite(s1.e_kin)
+        assert 0.02 < s1.n_precise / w.n < 0.8
+    # the two precisions follow the same trajectory closely over 200 fs; the melted
+    # hemisphere is chaotic, so its few largest deviations get a looser bound
+    dev = np.linalg.norm(r64[2] - r32[2], axis=1)
+    assert np.percentile(dev, 99) < 1e-2 and dev.max() < 0.2, (np.percentile(dev, 99), dev.max())
+
+
+@pytest.mark.parametrize("which", ["fp64", "mixed"])
+def test_final_forces_match_oracle(adaptive_runs, which):
+    w, r64, r32 = adaptive_runs
+    s0, s1, x, f, lam = r64 if which == "fp64" else r32
+    ace = O.ACE(I.ace_for_config(2))
+    p = I.eam_params(0)
+    g = np.random.Generator(np.random.PCG64(I.seed_for(2, 9)))
+    L = w.box.hi - w.box.lo
+    inner = np.nonzero((x[:, 0] > 20) & (x[:, 0] < L[0] - 20) & (x[:, 1] > 20) & (x[:, 1] < L[1] - 20))[0]
+    pick = np.concatenate([g.choice(inner[lam[inner] < 1.0], 8, replace=False),
+                           g.choice(inner[lam[inner] == 1.0], 4, replace=False)])
+    worst = 0.0
+    for i in pick:
+        d = x - x[i]
+        sel = np.nonzero((d * d).sum(1) < 16.0 ** 2)[0]
+        xc = x[sel]
+        box = I.Box(lo=xc.min(0) - 20, hi=xc.max(0) + 20, periodic=np.array([False] * 3))
+        k0 = int(np.nonzero(sel == i)[0][0])
+        _, fo, _, _ = O.hybrid(xc, box, lam[sel], p, ace)
+        err = np.linalg.norm(f[i] - fo[k0])
+        if which == "fp64":
+            assert err <= 1e-5 * (np.linalg.norm(fo[k0]) + 0.01), (i, err)
+        worst = max(worst, err)
+    assert worst <= 1e-3, worst
