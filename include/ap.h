@@ -43,7 +43,7 @@ typedef int32_t ap_status;
 #define AP_ERR_CUDA 2       /* a CUDA runtime call failed                              */
 #define AP_ERR_CAPACITY 3   /* a neighbour row exceeded its capacity; see ap_need()    */
 #define AP_ERR_NONFINITE 4  /* NaN/Inf found in positions or forces                    */
-#define AP_ERR_TIMEOUT 5    /* a bounded device wait gave up                           */
+#define AP_ERR_TIMEOUT 5    /* a bounded device wait gave up (the kernel returned early) */
 #define AP_ERR_STATE 6      /* call order violated (e.g. evaluation before neighbours) */
 #define AP_ERR_RADICAND 7   /* reserved: negative radicand in the local thermostat     */
 #define AP_ERR_BOX 8        /* an atom lies outside a non-periodic box dimension       */
@@ -51,6 +51,13 @@ typedef int32_t ap_status;
 
 #define AP_PREC_FP64 0      /* all potential arithmetic in FP64                        */
 #define AP_PREC_MIXED 1     /* FP32 potentials; FP64 integration and energy sums       */
+
+#define AP_DETECT_CSP 0      /* f_cut argument from the averaged centro-symmetry (Eq. lambda_1_i) */
+#define AP_DETECT_SELECTOR 1 /* f_cut argument from the averaged selector score p (ap_sel_*)     */
+
+#define AP_SEL_NFEAT 24      /* selector features per atom                              */
+#define AP_SEL_NHID 64       /* hidden width of the selector MLP                        */
+#define AP_SEL_NPARAMS 5825  /* 24*64 + 64 + 64*64 + 64 + 64 + 1                        */
 
 #define AP_FCUT_PRINTED 0   /* f_cut(x) = 1 - 1.875x + 1.25x^3 - 0.375x^5 as printed    */
 #define AP_FCUT_C2 1        /* C2-symmetric reading 0.5*p(2x-1)                         */
@@ -100,6 +107,13 @@ typedef struct {
   double ind_c0[3], ind_v[3], ind_R, ind_k;   /* centre at t=0 (A), velocity (A/fs), R (A), k (eV/A^3) */
   int32_t rebuild_every;     /* neighbour rebuild period (steps); 0 = lambda_every.  Every
                                 lambda update also rebuilds, so the CSP sees fresh rows. */
+  /* Detector behind lambda_0 (Appendix B allows any detector whose f_cut argument
+   * is 0 for precise and 1 for fast atoms).  AP_DETECT_SELECTOR pushes the
+   * selector's p_i in [0,1] into the history in place of CSP_i and uses
+   * lambda_0 = 1 - f_cut((sel_p_hi - p_avg)/(sel_p_hi - sel_p_lo)); it needs a
+   * model (ap_sel_set_model).  Ignored with AP_DETECT_CSP. */
+  int32_t detector;
+  double sel_p_lo, sel_p_hi;
 } ap_config;
 
 typedef struct ap_ctx ap_ctx;
@@ -230,6 +244,64 @@ ap_status ap_blend_forces(ap_ctx* ctx, int64_t n, const double* d_lam, const dou
  * (an atom moved more than skin/2 before a rebuild) and AP_ERR_NONFINITE. */
 ap_status ap_step(ap_ctx* ctx, int64_t n, double* d_x, double* d_v, double* d_f, const double* d_mass,
                   const uint8_t* d_fixed, double* d_lam, int64_t nsteps, ap_step_stats* h_stats, void* stream);
+
+/* ----------------------------------------------------------------- selector */
+
+/* The selector is a learned detection score that can replace the centro-symmetry
+ * argument of f_cut (Appendix B: any detector whose argument is 0 for atoms to be
+ * computed precisely and 1 for atoms to be computed fast).  The paper prescribes no
+ * detector of this kind; its definition is this library's:
+ *   features (24 per atom, FP32, from the EAM rows; N = pairs with r < 5.5 A,
+ *   S1 r < 3.09, S2 3.09 <= r < 4.02, S3 4.02 <= r < 4.77 A; empty sets give 0):
+ *     0 rho_i  1 xi(rho_i)  2 xi'(rho_i)  3 1/2 sum_N Phi  4-6 |S1| |S2| |S3|
+ *     7 min(CSP_i, 100)  8 sum_{j in S2} min(r_j^2, min_{k in S2\j} |r_j + r_k|^2)
+ *     9-11 |sum r_j| over S1, S2, N  12 |sum_N zeta'(r_j) r_j/r_j|
+ *     13 rho_i - mean_{S1} rho_j  14-17 mean, std, min, max of r over S1
+ *     18-21 mean, std, third and fourth central moments of r over N  22 |N|
+ *     23 mean_N xi'_j - xi'_i
+ *   network: x~ = bf16((x - mu) * inv_sigma) (FP32 arithmetic);
+ *     h1 = bf16(relu(x~ W1 + b1)); h2 = relu(h1 W2 + b2); z = h2 . w3 + b3;
+ *     p = 1/(1 + exp(-z)), with W1, W2, w3 used as bf16 and FP32 accumulation
+ *     (tcgen05 tensor cores for the two hidden layers).
+ *   training: loss = sum_b w_b [softplus(z_b) - y_b z_b] (weights as given, e.g.
+ *     normalised to sum 1), gradient straight through the bf16 roundings, Adam
+ *     with bias correction on FP32 master weights (m = b1 m + (1-b1) g,
+ *     v = b2 v + (1-b2) g^2, theta -= lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps)).
+ * Flat parameter layout (AP_SEL_NPARAMS floats): W1 [24][64] (input-major), b1 [64],
+ * W2 [64][64] (input-major), b2 [64], w3 [64], b3. */
+
+/* Load a model: h_params [AP_SEL_NPARAMS], h_mu [24], h_inv_sigma [24] (host FP32,
+ * finite).  Resets the Adam state.  Synchronises.  Errors: AP_ERR_ARG. */
+ap_status ap_sel_set_model(ap_ctx* ctx, const float* h_params, const float* h_mu, const float* h_inv_sigma);
+
+/* Copy the FP32 master parameters (and mu, inv_sigma; any pointer may be NULL)
+ * to host memory.  Synchronises.  Errors: AP_ERR_STATE without a model. */
+ap_status ap_sel_get_model(ap_ctx* ctx, float* h_params, float* h_mu, float* h_inv_sigma);
+
+/* Raw features d_feat [n][24] FP32 of every atom at positions d_x.  Requires
+ * ap_build_neighbors on the same n and positions.  Computes the CSP sample of
+ * every changeable atom (d_changeable as in ap_classify) on the way, which
+ * replaces the one ap_get_lambda_state returns. */
+ap_status ap_sel_features(ap_ctx* ctx, int64_t n, const double* d_x, const uint8_t* d_changeable, float* d_feat,
+                          void* stream);
+
+/* p = sigmoid(z) of n raw feature rows d_feat [n][24]: d_p [n] FP32 (may be NULL),
+ * d_logit [n] FP32 (may be NULL).  Errors: AP_ERR_STATE without a model. */
+ap_status ap_sel_predict(ap_ctx* ctx, int64_t n, const float* d_feat, float* d_p, float* d_logit, void* stream);
+
+/* One Adam step on a batch of b samples: rows d_idx[0..b) of d_feat [*][24],
+ * d_label [*] (0 or 1) and d_weight [*] (d_idx NULL: rows 0..b).  d_loss (device
+ * float, may be NULL) receives the batch loss before the step.  The gradient is
+ * reduced in a fixed order (bitwise reproducible on one GPU model).
+ * Errors: AP_ERR_STATE without a model, AP_ERR_ARG for b < 1. */
+ap_status ap_sel_train_step(ap_ctx* ctx, int64_t b, const float* d_feat, const int32_t* d_idx, const float* d_label,
+                            const float* d_weight, float lr, float beta1, float beta2, float eps, float* d_loss,
+                            void* stream);
+
+/* Gradient (h_grad [AP_SEL_NPARAMS], may be NULL) and loss (*h_loss, may be NULL)
+ * of the last ap_sel_train_step.  Synchronises; reports AP_ERR_TIMEOUT if a
+ * tensor-core wait gave up. */
+ap_status ap_sel_get_grad(ap_ctx* ctx, float* h_grad, float* h_loss);
 
 /* ----------------------------------------------------------------- allocation-free EAM */
 

@@ -81,6 +81,7 @@ def lib():
         _lib.orc_lambda0.argtypes = [ctypes.c_int, P, ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P]
         _lib.orc_lambda_min.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int, P]
         _lib.orc_eam.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int, P, P, P, P, P, P]
+        _lib.orc_eam_pair.argtypes = [P, ctypes.c_int, P, P, P, P, P]
         _lib.orc_ace_create.restype = P
         _lib.orc_ace_create.argtypes = [P, P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
         _lib.orc_ace_destroy.argtypes = [P]
@@ -231,15 +232,20 @@ class LambdaState:
         return pos
 
 
-def classify(state: LambdaState, x, box, hyb, changeable=None, r_search: float = 6.5):
+def classify(state: LambdaState, x, box, hyb, changeable=None, r_search: float = 6.5, score=None,
+             score_lo: float = 0.0, score_hi: float = 1.0):
     """One lambda update (Appendix B): CSP -> CSP_avg -> lambda_0 -> lambda_min ->
-    lambda_avg -> lambda_avg,msz.  Returns (lam, lam0, csp_sample, csp_avg, lam_min, lam_avg)."""
+    lambda_avg -> lambda_avg,msz.  Returns (lam, lam0, csp_sample, csp_avg, lam_min, lam_avg).
+    With ``score`` (another detector's per-atom score, larger = more in need of the
+    precise potential), that score replaces CSP in the history and in the f_cut
+    argument, with thresholds (score_lo, score_hi) in place of (CSP_lo, CSP_hi)."""
     x = _f64(x)
     ch = None if changeable is None else np.ascontiguousarray(changeable, dtype=np.uint8)
-    c = csp(x, box, r_search, ch)
+    c = csp(x, box, r_search, ch) if score is None else _f64(score)
+    lo, hi = (hyb.csp_lo, hyb.csp_hi) if score is None else (score_lo, score_hi)
     state.pos_csp = state.push(state.csp_hist, state.pos_csp, c)
     cavg = canonical_mean(state.csp_hist, state.pos_csp)
-    l0 = lambda0(cavg, hyb.csp_lo, hyb.csp_hi, hyb.fcut_mode, ch)
+    l0 = lambda0(cavg, lo, hi, hyb.fcut_mode, ch)
     lmin = lambda_min(x, box, l0, hyb.r_lo, hyb.r_hi, hyb.fcut_mode, ch)
     state.pos_lam = state.push(state.lam_hist, state.pos_lam, lmin)
     lavg = canonical_mean(state.lam_hist, state.pos_lam)
@@ -271,6 +277,15 @@ def eam(x, box, p, weights=None, nl: Optional[NeighborList] = None):
     lib().orc_eam(n, _p(x), ctypes.byref(_box(box)), _p(nl.cnt), _p(nl.j), _p(nl.s), nl.cap, ctypes.byref(pp),
                   _p(w), _p(e), _p(f), _p(rho), _p(dxi))
     return e, f, rho, dxi
+
+
+def eam_pair(p, r):
+    """zeta(r), zeta'(r), Phi(r), Phi'(r) of the analytic EAM at the distances r."""
+    r = _f64(r).reshape(-1)
+    out = [np.zeros(r.shape[0]) for _ in range(4)]
+    pp = _EAM(p.beta, p.alpha, p.A, p.D, p.rp, p.r0, p.rc, p.h)
+    lib().orc_eam_pair(ctypes.byref(pp), r.shape[0], _p(r), *[_p(o) for o in out])
+    return tuple(out)
 
 
 class ACE:

@@ -353,6 +353,14 @@ static void eam_xi(const orc_eam_params* p, double rho, double* xi, double* dxi)
   *dxi = -p->A / (2.0 * s);
 }
 
+/* zeta, zeta', Phi, Phi' at m distances (the selector features use the pair terms). */
+void orc_eam_pair(const orc_eam_params* p, int m, const double* r, double* z, double* dz, double* ph, double* dph) {
+  for (int k = 0; k < m; ++k) {
+    eam_zeta(p, r[k], &z[k], &dz[k]);
+    eam_phi(p, r[k], &ph[k], &dph[k]);
+  }
+}
+
 /* EAM site energies E_i^f = xi(sum_j zeta) + 1/2 sum_j Phi (Eq. energy_eam) and the
  * weighted force F_k = -grad_k sum_i wt_i E_i^f.  The neighbour list (cap, cnt,
  * jl, sl) may use a radius >= rc; pairs with r >= rc contribute nothing.

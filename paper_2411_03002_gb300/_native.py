@@ -16,6 +16,11 @@ ERRORS = {1: "AP_ERR_ARG", 2: "AP_ERR_CUDA", 3: "AP_ERR_CAPACITY", 4: "AP_ERR_NO
           6: "AP_ERR_STATE", 7: "AP_ERR_RADICAND", 8: "AP_ERR_BOX", 9: "AP_ERR_SKIN"}
 PREC_FP64 = 0
 PREC_MIXED = 1
+DETECT_CSP = 0
+DETECT_SELECTOR = 1
+SEL_NFEAT = 24
+SEL_NPARAMS = 5825
+F32 = ctypes.c_float
 
 
 class ApBox(ctypes.Structure):
@@ -29,7 +34,7 @@ class ApConfig(ctypes.Structure):
                    ("n_csp_avg", I32), ("n_lam_avg", I32), ("fcut_mode", I32), ("skin", F64), ("cap_eam", I32),
                    ("cap_ace", I32), ("precision", I32), ("dt", F64), ("lambda_every", I32), ("indenter_on", I32),
                    ("ind_c0", F64 * 3), ("ind_v", F64 * 3), ("ind_R", F64), ("ind_k", F64),
-                   ("rebuild_every", I32)])
+                   ("rebuild_every", I32), ("detector", I32), ("sel_p_lo", F64), ("sel_p_hi", F64)])
 
 
 class ApStepStats(ctypes.Structure):
@@ -67,6 +72,12 @@ SIGNATURES = [
     ("ap_profile_read", I32, [P, P, P, P, P, P]),
     ("ap_state_export", I32, [P, P, P]),
     ("ap_state_import", I32, [P, P, ctypes.c_size_t]),
+    ("ap_sel_set_model", I32, [P, P, P, P]),
+    ("ap_sel_get_model", I32, [P, P, P, P]),
+    ("ap_sel_features", I32, [P, I64, P, P, P, P]),
+    ("ap_sel_predict", I32, [P, I64, P, P, P, P]),
+    ("ap_sel_train_step", I32, [P, I64, P, P, P, P, F32, F32, F32, F32, P, P]),
+    ("ap_sel_get_grad", I32, [P, P, P]),
 ]
 
 _lib = None

@@ -41,7 +41,8 @@ def make_box(lo, hi, periodic) -> ApBox:
 
 def make_config(eam, ace, hyb, precision: int = N.PREC_MIXED, skin: float = 1.0, dt: float = 1.0,
                 indenter=None, cap_eam: int = 0, cap_ace: int = 0, lambda_every: Optional[int] = None,
-                rebuild_every: int = 0) -> ApConfig:
+                rebuild_every: int = 0, detector: int = N.DETECT_CSP, sel_p_lo: float = 0.5,
+                sel_p_hi: float = 0.9) -> ApConfig:
     """Fill an ap_config from parameter objects with the attribute names of
     the EAM (beta, alpha, A, D, rp, r0, rc, h), ACE (W, c, rc, n0) and switching
     (csp_lo, csp_hi, r_lo, r_hi, dlam_min, n_csp_avg, n_lam_avg, fcut_mode,
@@ -72,6 +73,8 @@ def make_config(eam, ace, hyb, precision: int = N.PREC_MIXED, skin: float = 1.0,
     c.dt = float(dt)
     c.lambda_every = int(lambda_every if lambda_every is not None else hyb.sample_every)
     c.rebuild_every = int(rebuild_every)
+    c.detector = int(detector)
+    c.sel_p_lo, c.sel_p_hi = float(sel_p_lo), float(sel_p_hi)
     if indenter is not None:
         c.indenter_on = 1
         for k in range(3):
@@ -259,6 +262,51 @@ class Context:
         buf = ctypes.create_string_buffer(data, len(data))
         self._ck(self.lib.ap_state_import(self.h, buf, len(data)))
 
+    # ---------------------------------------------------------------- selector
+    def sel_set_model(self, params, mu, inv_sigma):
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        m = np.ascontiguousarray(mu, dtype=np.float32).reshape(-1)
+        s = np.ascontiguousarray(inv_sigma, dtype=np.float32).reshape(-1)
+        if p.size != N.SEL_NPARAMS or m.size != N.SEL_NFEAT or s.size != N.SEL_NFEAT:
+            raise ValueError("selector model: expected 5825 parameters and 24 mu / inv_sigma values")
+        self._ck(self.lib.ap_sel_set_model(self.h, p.ctypes.data, m.ctypes.data, s.ctypes.data))
+
+    def sel_get_model(self):
+        p = np.zeros(N.SEL_NPARAMS, np.float32)
+        m = np.zeros(N.SEL_NFEAT, np.float32)
+        s = np.zeros(N.SEL_NFEAT, np.float32)
+        self._ck(self.lib.ap_sel_get_model(self.h, p.ctypes.data, m.ctypes.data, s.ctypes.data))
+        return p, m, s
+
+    def sel_features(self, x, changeable=None, feat=None, stream=None) -> torch.Tensor:
+        n = x.shape[0]
+        if feat is None:
+            feat = torch.empty((n, N.SEL_NFEAT), dtype=torch.float32, device=x.device)
+        self._ck(self.lib.ap_sel_features(self.h, n, _ptr(x), _ptr(changeable), _ptr(feat), _stream(stream)))
+        return feat
+
+    def sel_predict(self, feat, p=None, logit=None, stream=None):
+        n = feat.shape[0]
+        if p is None:
+            p = torch.empty(n, dtype=torch.float32, device=feat.device)
+        if logit is None:
+            logit = torch.empty(n, dtype=torch.float32, device=feat.device)
+        self._ck(self.lib.ap_sel_predict(self.h, n, _ptr(feat), _ptr(p), _ptr(logit), _stream(stream)))
+        return p, logit
+
+    def sel_train_step(self, feat, label, weight, idx=None, b: Optional[int] = None, lr: float = 1e-3,
+                       beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, loss=None, stream=None):
+        bb = int(b if b is not None else (idx.shape[0] if idx is not None else feat.shape[0]))
+        self._ck(self.lib.ap_sel_train_step(self.h, bb, _ptr(feat), _ptr(idx), _ptr(label), _ptr(weight),
+                                            float(lr), float(beta1), float(beta2), float(eps), _ptr(loss),
+                                            _stream(stream)))
+
+    def sel_get_grad(self):
+        g = np.zeros(N.SEL_NPARAMS, np.float32)
+        loss = ctypes.c_float()
+        self._ck(self.lib.ap_sel_get_grad(self.h, g.ctypes.data, ctypes.byref(loss)))
+        return g, float(loss.value)
+
 
 # Module-level calls with the C-ABI names.
 def ap_create(cfg: ApConfig) -> Context:
@@ -287,3 +335,27 @@ def ap_blend_forces(ctx: Context, lam, e_fast, e_prec, stream=None):
 
 def ap_step(ctx: Context, x, v, f, mass, fixed, lam, nsteps: int, stream=None) -> StepStats:
     return ctx.step(x, v, f, mass, fixed, lam, nsteps, stream)
+
+
+def ap_sel_set_model(ctx: Context, params, mu, inv_sigma):
+    return ctx.sel_set_model(params, mu, inv_sigma)
+
+
+def ap_sel_get_model(ctx: Context):
+    return ctx.sel_get_model()
+
+
+def ap_sel_features(ctx: Context, x, changeable=None, feat=None, stream=None):
+    return ctx.sel_features(x, changeable, feat, stream)
+
+
+def ap_sel_predict(ctx: Context, feat, p=None, logit=None, stream=None):
+    return ctx.sel_predict(feat, p, logit, stream)
+
+
+def ap_sel_train_step(ctx: Context, feat, label, weight, idx=None, **kw):
+    return ctx.sel_train_step(feat, label, weight, idx, **kw)
+
+
+def ap_sel_get_grad(ctx: Context):
+    return ctx.sel_get_grad()

@@ -1,6 +1,7 @@
 // C-ABI entry points (include/ap.h) and the host-side orchestration.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -54,6 +55,9 @@ ap_status validate(const ap_config& g, std::string& why) {
   if (g.cap_eam < 0 || g.cap_ace < 0 || g.cap_eam > 4096 || g.cap_ace > 4096) return bad("row capacity out of range");
   if (g.lambda_every < 1) return bad("lambda_every must be >= 1");
   if (g.rebuild_every < 0) return bad("rebuild_every must be >= 0");
+  if (g.detector != AP_DETECT_CSP && g.detector != AP_DETECT_SELECTOR) return bad("unknown detector");
+  if (g.detector == AP_DETECT_SELECTOR && !(g.sel_p_lo >= 0 && g.sel_p_hi > g.sel_p_lo))
+    return bad("need 0 <= sel_p_lo < sel_p_hi");
   return AP_OK;
 }
 
@@ -207,6 +211,7 @@ ap_status check_err_bits(ap_ctx* c) {
     return fail(c, AP_ERR_CAPACITY, "neighbour row capacity exceeded");
   }
   if (e & kErrSkin) return fail(c, AP_ERR_SKIN, "an atom moved more than skin/2 between rebuilds");
+  if (e & kErrTimeout) return fail(c, AP_ERR_TIMEOUT, "a bounded tensor-core wait gave up");
   return AP_OK;
 }
 
@@ -361,10 +366,33 @@ void collect_profile(ap_ctx* c) {
   c->ev_used = 0;
 }
 
+// Selector scratch for n atoms (features, pre-pass densities, score).
+ap_status ensure_sel_feat(ap_ctx* c, int64_t n) {
+  if (n <= c->sel_feat_cap && c->d_sel_feat) return AP_OK;
+  CK(dalloc(c->d_sel_rho, n));
+  CK(dalloc(c->d_sel_feat, 24 * n));
+  CK(dalloc(c->d_sel_score, n));
+  c->sel_feat_cap = n;
+  return AP_OK;
+}
+
+// What the configured detector needs before a classification.
+ap_status prep_detector(ap_ctx* c) {
+  if (c->cfg.detector != AP_DETECT_SELECTOR) return AP_OK;
+  if (!c->sel_ready) return fail(c, AP_ERR_STATE, "detector = selector needs ap_sel_set_model first");
+  return ensure_sel_feat(c, c->n);
+}
+
 void classify_async(ap_ctx* c, const double* d_x, const uint8_t* d_ch, double* d_lam, int* d_queue,
                     int64_t* d_nq64, cudaStream_t s) {
   launch_csp(c, d_x, d_ch, s);
-  launch_lambda0(c, d_ch, s);
+  if (c->cfg.detector == AP_DETECT_SELECTOR) {
+    launch_sel_features(c, c->d_sel_feat, s);
+    launch_sel_mlp(c, c->n, c->d_sel_feat, nullptr, nullptr, c->d_sel_score, nullptr, nullptr, nullptr, s);
+    launch_lambda0(c, d_ch, c->d_sel_score, c->cfg.sel_p_lo, c->cfg.sel_p_hi, s);
+  } else {
+    launch_lambda0(c, d_ch, c->d_csp, c->cfg.csp_lo, c->cfg.csp_hi, s);
+  }
   launch_spread(c, d_x, d_ch, s);
   launch_lambda_final(c, d_ch, d_lam, d_queue, d_nq64, s);
 }
@@ -418,7 +446,8 @@ void ap_destroy(ap_ctx* c) {
                   c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_efast, c->d_eprec,
                   c->d_eatom, c->d_eext, c->d_changeable, c->d_term_idx, c->d_term_coef32, c->d_term_coef64,
                   c->d_W32, c->d_W64, c->d_e3_idx, c->d_e3_coef32, c->d_e3_coef64, c->d_e3_pack, c->d_scan_tmp, c->d_red,
-                  c->d_sc};
+                  c->d_sel_model, c->d_sel_master, c->d_sel_m1, c->d_sel_m2, c->d_sel_grad, c->d_sel_partial,
+                  c->d_sel_rho, c->d_sel_feat, c->d_sel_score, c->d_sel_z, c->d_sel_h1, c->d_sel_h2, c->d_sc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_sc) cudaFreeHost(c->h_sc);
@@ -519,6 +548,8 @@ ap_status ap_classify(ap_ctx* c, int64_t n, const double* d_x, const uint8_t* d_
     CK(cudaMemsetAsync(&c->d_sc->n_precise, 0, sizeof(int), s));
     return AP_OK;
   }
+  ap_status st = prep_detector(c);
+  if (st) return st;
   launch_shadow(c, d_x, s);
   classify_async(c, d_x, d_changeable, d_lam, d_precise_idx, d_n_precise, s);
   CK(cudaGetLastError());
@@ -609,7 +640,8 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
     ch = c->d_changeable;
   }
   const ap_config& g = c->cfg;
-  ap_status st;
+  ap_status st = prep_detector(c);
+  if (st) return st;
   if (!c->md_ready) {
     launch_wrap_positions(c, d_x, s);
     st = build_checked(c, d_x, nullptr, s);
@@ -699,6 +731,121 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
     h_stats->max_disp = std::sqrt((double)d2);
     h_stats->error_bits = c->h_sc->err;
   }
+  return check_err_bits(c);
+}
+
+// ---------------------------------------------------------------------- selector
+ap_status ap_sel_set_model(ap_ctx* c, const float* h_params, const float* h_mu, const float* h_inv_sigma) {
+  if (!c) return AP_ERR_ARG;
+  if (!h_params || !h_mu || !h_inv_sigma) return fail(c, AP_ERR_ARG, "null model array");
+  for (int k = 0; k < AP_SEL_NPARAMS; ++k)
+    if (!std::isfinite(h_params[k])) return fail(c, AP_ERR_ARG, "non-finite model parameter");
+  for (int k = 0; k < AP_SEL_NFEAT; ++k)
+    if (!std::isfinite(h_mu[k]) || !std::isfinite(h_inv_sigma[k])) return fail(c, AP_ERR_ARG, "non-finite mu or inv_sigma");
+  CK(sel_mlp_attr());
+  if (!c->d_sel_model) {
+    CK(dalloc(c->d_sel_model, 1));
+    CK(dalloc(c->d_sel_master, AP_SEL_NPARAMS));
+    CK(dalloc(c->d_sel_m1, AP_SEL_NPARAMS));
+    CK(dalloc(c->d_sel_m2, AP_SEL_NPARAMS));
+    CK(dalloc(c->d_sel_grad, AP_SEL_NPARAMS + 1));
+    CK(dalloc(c->d_sel_partial, sel_partial_floats(c)));
+  }
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemset(c->d_sel_model, 0, sizeof(SelDev)));
+  CK(cudaMemset(c->d_sel_m1, 0, sizeof(float) * AP_SEL_NPARAMS));
+  CK(cudaMemset(c->d_sel_m2, 0, sizeof(float) * AP_SEL_NPARAMS));
+  CK(cudaMemset(c->d_sel_grad, 0, sizeof(float) * (AP_SEL_NPARAMS + 1)));
+  CK(cudaMemcpy(c->d_sel_master, h_params, sizeof(float) * AP_SEL_NPARAMS, cudaMemcpyHostToDevice));
+  float* vec = reinterpret_cast<float*>(reinterpret_cast<char*>(c->d_sel_model) + offsetof(SelDev, vec));
+  CK(cudaMemcpy(vec + SelDev::kMu, h_mu, sizeof(float) * AP_SEL_NFEAT, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(vec + SelDev::kInvS, h_inv_sigma, sizeof(float) * AP_SEL_NFEAT, cudaMemcpyHostToDevice));
+  launch_sel_adam(c, false, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, 0);
+  CK(cudaGetLastError());
+  CK(cudaDeviceSynchronize());
+  c->sel_ready = true;
+  c->sel_t = 0;
+  return AP_OK;
+}
+
+ap_status ap_sel_get_model(ap_ctx* c, float* h_params, float* h_mu, float* h_inv_sigma) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->sel_ready) return fail(c, AP_ERR_STATE, "no selector model");
+  CK(cudaDeviceSynchronize());
+  const float* vec = reinterpret_cast<const float*>(reinterpret_cast<const char*>(c->d_sel_model) + offsetof(SelDev, vec));
+  if (h_params) CK(cudaMemcpy(h_params, c->d_sel_master, sizeof(float) * AP_SEL_NPARAMS, cudaMemcpyDeviceToHost));
+  if (h_mu) CK(cudaMemcpy(h_mu, vec + SelDev::kMu, sizeof(float) * AP_SEL_NFEAT, cudaMemcpyDeviceToHost));
+  if (h_inv_sigma) CK(cudaMemcpy(h_inv_sigma, vec + SelDev::kInvS, sizeof(float) * AP_SEL_NFEAT, cudaMemcpyDeviceToHost));
+  return AP_OK;
+}
+
+ap_status ap_sel_features(ap_ctx* c, int64_t n, const double* d_x, const uint8_t* d_changeable, float* d_feat,
+                          void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->built || n != c->n) return fail(c, AP_ERR_STATE, "ap_sel_features needs ap_build_neighbors on the same atoms");
+  if (n == 0) return AP_OK;
+  if (!d_x || !d_feat) return fail(c, AP_ERR_ARG, "null argument");
+  ap_status st = ensure_sel_feat(c, n);
+  if (st) return st;
+  cudaStream_t s = S(stream);
+  launch_shadow(c, d_x, s);
+  launch_csp(c, d_x, d_changeable, s);
+  launch_sel_features(c, d_feat, s);
+  CK(cudaGetLastError());
+  return AP_OK;
+}
+
+ap_status ap_sel_predict(ap_ctx* c, int64_t n, const float* d_feat, float* d_p, float* d_logit, void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->sel_ready) return fail(c, AP_ERR_STATE, "no selector model");
+  if (n < 0 || n > 0x7fffffff) return fail(c, AP_ERR_ARG, "n out of range");
+  if (n == 0) return AP_OK;
+  if (!d_feat) return fail(c, AP_ERR_ARG, "null features");
+  launch_sel_mlp(c, n, d_feat, nullptr, d_p, nullptr, d_logit, nullptr, nullptr, S(stream));
+  CK(cudaGetLastError());
+  return AP_OK;
+}
+
+ap_status ap_sel_train_step(ap_ctx* c, int64_t b, const float* d_feat, const int32_t* d_idx, const float* d_label,
+                            const float* d_weight, float lr, float beta1, float beta2, float eps, float* d_loss,
+                            void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->sel_ready) return fail(c, AP_ERR_STATE, "no selector model");
+  if (b < 1 || b > 0x7fffffff / 64) return fail(c, AP_ERR_ARG, "batch size out of range");
+  if (!d_feat || !d_label || !d_weight) return fail(c, AP_ERR_ARG, "null argument");
+  if (!(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+    return fail(c, AP_ERR_ARG, "bad Adam hyper-parameters");
+  cudaStream_t s = S(stream);
+  if (b > c->sel_train_cap) {
+    CK(cudaStreamSynchronize(s));
+    CK(dalloc(c->d_sel_z, b));
+    float* h1 = nullptr;
+    if (c->d_sel_h1) cudaFree(c->d_sel_h1);
+    c->d_sel_h1 = nullptr;
+    CK(cudaMalloc((void**)&h1, sizeof(uint16_t) * 64 * (size_t)b));
+    c->d_sel_h1 = h1;
+    CK(dalloc(c->d_sel_h2, 64 * (size_t)b));
+    c->sel_train_cap = b;
+  }
+  launch_sel_mlp(c, b, d_feat, d_idx, nullptr, nullptr, c->d_sel_z, c->d_sel_h1, c->d_sel_h2, s);
+  launch_sel_backward(c, b, d_feat, d_idx, d_label, d_weight, s);
+  c->sel_t += 1;
+  const double bc1 = 1.0 - std::pow((double)beta1, (double)c->sel_t);
+  const double bc2 = 1.0 - std::pow((double)beta2, (double)c->sel_t);
+  launch_sel_adam(c, true, lr, beta1, beta2, eps, (float)(1.0 / bc1), (float)(1.0 / bc2), s);
+  if (d_loss) CK(cudaMemcpyAsync(d_loss, c->d_sel_grad + AP_SEL_NPARAMS, sizeof(float), cudaMemcpyDeviceToDevice, s));
+  CK(cudaGetLastError());
+  return AP_OK;
+}
+
+ap_status ap_sel_get_grad(ap_ctx* c, float* h_grad, float* h_loss) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->sel_ready) return fail(c, AP_ERR_STATE, "no selector model");
+  CK(cudaDeviceSynchronize());
+  if (h_grad) CK(cudaMemcpy(h_grad, c->d_sel_grad, sizeof(float) * AP_SEL_NPARAMS, cudaMemcpyDeviceToHost));
+  if (h_loss) CK(cudaMemcpy(h_loss, c->d_sel_grad + AP_SEL_NPARAMS, sizeof(float), cudaMemcpyDeviceToHost));
+  ap_status st = read_scalars(c, 0);
+  if (st) return st;
   return check_err_bits(c);
 }
 

@@ -57,6 +57,7 @@ enum : int {
   kErrBox = 1 << AP_ERR_BOX,
   kErrSkin = 1 << AP_ERR_SKIN,
   kErrArg = 1 << AP_ERR_ARG,
+  kErrTimeout = 1 << AP_ERR_TIMEOUT,
 };
 
 // ------------------------------------------------------------------ device buffers
@@ -104,6 +105,24 @@ struct AceTables {
   int e3_len = 0;                // entries per lane program (padded)
 };
 void build_ace_tables(const ap_config& cfg, AceTables& t);
+
+// ------------------------------------------------------------------ selector model
+// Device image of the selector MLP 24-64-64-1.  Flat FP32 parameter layout (the
+// ABI's): W1 [24][64] input-major, b1 [64], W2 [64][64], b2 [64], w3 [64], b3.
+struct SelDev {
+  static constexpr int kParams = AP_SEL_NPARAMS;
+  static constexpr int kOffB1 = 24 * 64, kOffW2 = kOffB1 + 64, kOffB2 = kOffW2 + 64 * 64, kOffW3 = kOffB2 + 64,
+                       kOffB3 = kOffW3 + 64;
+  // FP32 vectors: w3 (bf16-valued), b1, b2, b3, mu, 1/sigma
+  static constexpr int kW3 = 0, kB1 = 64, kB2 = 128, kB3 = 192, kMu = 196, kInvS = 220, kVec = 244;
+  // bf16 operand images in the canonical no-swizzle K-major layout: W1^T (64 x 32,
+  // K padded with zeros) then W2^T (64 x 64); core matrix (row block rb, K block kb)
+  // at (kb * 8 + rb) * 128 bytes.
+  alignas(16) uint8_t img[4096 + 8192];
+  alignas(16) float vec[256];
+  alignas(16) float W2r[64 * 64];   // bf16-valued W2 [k][n] for the backward pass
+};
+static_assert(SelDev::kOffB3 + 1 == SelDev::kParams, "selector parameter layout");
 
 // ------------------------------------------------------------------ context
 }  // namespace ap
@@ -196,6 +215,24 @@ struct ap_ctx {
   double* d_red = nullptr;       // reduction partials
   int red_cap = 0;
 
+  // selector (learned detection score)
+  ap::SelDev* d_sel_model = nullptr;
+  float* d_sel_master = nullptr;   // [kParams] FP32 master weights
+  float* d_sel_m1 = nullptr;       // Adam first moments
+  float* d_sel_m2 = nullptr;       // Adam second moments
+  float* d_sel_grad = nullptr;     // [kParams + 1] gradient and loss of the last training step
+  float* d_sel_partial = nullptr;  // [2 * num_sms][kParams + 1]
+  float2* d_sel_rho = nullptr;     // [n] FP32 (rho, xi'(rho)) of the feature pre-pass
+  float* d_sel_feat = nullptr;     // [n][24] features of the classification path
+  double* d_sel_score = nullptr;   // [n] selector score p of the classification path
+  float* d_sel_z = nullptr;        // [train_cap] logits of the last training forward pass
+  void* d_sel_h1 = nullptr;        // [train_cap][64] bf16 hidden layer 1
+  float* d_sel_h2 = nullptr;       // [train_cap][64] FP32 hidden layer 2
+  int64_t sel_train_cap = 0;
+  int64_t sel_feat_cap = 0;
+  bool sel_ready = false;
+  int64_t sel_t = 0;               // Adam steps taken
+
   ap::DevScalars* d_sc = nullptr;
   ap::DevScalars* h_sc = nullptr;  // pinned mirror
 
@@ -232,7 +269,7 @@ void launch_wrap_positions(ap_ctx* c, double* d_x, cudaStream_t s);
 
 // k_classify.cu
 void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s);
-void launch_lambda0(ap_ctx* c, const uint8_t* d_ch, cudaStream_t s);
+void launch_lambda0(ap_ctx* c, const uint8_t* d_ch, const double* d_score, double lo, double hi, cudaStream_t s);
 void launch_spread(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s);
 void launch_lambda_final(ap_ctx* c, const uint8_t* d_ch, double* d_lam, int* d_queue, int64_t* d_nq64,
                          cudaStream_t s);
@@ -244,6 +281,18 @@ void launch_eam(ap_ctx* c, const double* d_lam, double* d_e_fast, double* d_f, b
 void upload_ace_tables(ap_ctx* c);
 void launch_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_prec, bool forces, cudaStream_t s);
 void launch_ace_finalize(ap_ctx* c, double* d_f, cudaStream_t s);
+
+// k_selector.cu
+void launch_sel_features(ap_ctx* c, float* d_feat, cudaStream_t s);   // needs c->d_csp of the same positions
+cudaError_t sel_mlp_attr();
+void launch_sel_mlp(ap_ctx* c, int64_t n, const float* d_feat, const int* d_idx, float* d_p, double* d_score,
+                    float* d_z, void* d_h1, float* d_h2, cudaStream_t s);
+int sel_bwd_parts(ap_ctx* c, int64_t b);
+void launch_sel_backward(ap_ctx* c, int64_t b, const float* d_feat, const int* d_idx, const float* d_label,
+                         const float* d_weight, cudaStream_t s);
+void launch_sel_adam(ap_ctx* c, bool update, float lr, float beta1, float beta2, float eps, float inv_bc1,
+                     float inv_bc2, cudaStream_t s);
+size_t sel_partial_floats(ap_ctx* c);
 
 // k_md.cu
 void launch_vv_first(ap_ctx* c, double* d_x, double* d_v, const double* d_f, const double* d_mass,

@@ -481,14 +481,15 @@ void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t 
   c->kernels += 1;
 }
 
-void launch_lambda0(ap_ctx* c, const uint8_t* d_ch, cudaStream_t s) {
+// d_score: the detection score pushed into the history (CSP, or the selector's p),
+// with thresholds (lo, hi) in the f_cut argument (hi - avg)/(hi - lo).
+void launch_lambda0(ap_ctx* c, const uint8_t* d_ch, const double* d_score, double lo, double hi, cudaStream_t s) {
   int ns = c->cfg.n_csp_avg;
   int fill = c->hist_started ? 0 : 1;
   int pos = fill ? 0 : (c->csp_pos + 1) % ns;
   c->csp_pos = pos;
-  k_lambda0<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_ch, c->d_csp, c->d_csp_hist, ns, pos, fill, c->cfg.csp_lo,
-                                            c->cfg.csp_hi, c->cfg.fcut_mode, c->d_csp_avg, c->d_lam0, c->d_lam_min,
-                                            c->d_flag);
+  k_lambda0<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_ch, d_score, c->d_csp_hist, ns, pos, fill, lo, hi,
+                                            c->cfg.fcut_mode, c->d_csp_avg, c->d_lam0, c->d_lam_min, c->d_flag);
   c->kernels += 2 + scan_exclusive(c->d_flag, c->d_scan, (int)c->n, c->d_scan_tmp, s);
   k_compact<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, c->d_flag, c->d_scan, c->d_detected, &c->d_sc->n_detected,
                                             nullptr);

@@ -35,8 +35,9 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ap.h"\nint main(){'
-                    'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(ap_config), sizeof(ap_box), sizeof(ap_step_stats),'
-                    ' offsetof(ap_config, ace_nc), offsetof(ap_config, dt), offsetof(ap_config, ind_k));return 0;}')
+                    'printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ap_config), sizeof(ap_box), sizeof(ap_step_stats),'
+                    ' offsetof(ap_config, ace_nc), offsetof(ap_config, dt), offsetof(ap_config, ind_k),'
+                    ' offsetof(ap_config, detector), offsetof(ap_config, sel_p_hi));return 0;}')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
@@ -47,6 +48,8 @@ def test_struct_layouts_match_header(tmp_path):
     assert sz[3] == N.ApConfig.ace_nc.offset
     assert sz[4] == N.ApConfig.dt.offset
     assert sz[5] == N.ApConfig.ind_k.offset
+    assert sz[6] == N.ApConfig.detector.offset
+    assert sz[7] == N.ApConfig.sel_p_hi.offset
 
 
 def test_basis_enumeration_matches_oracle():
