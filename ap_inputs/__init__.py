@@ -215,9 +215,10 @@ def config_c1() -> Workload:
     return Workload("c1_fcc4_void", x, box, np.full(n, MASS_CU), np.zeros(n, np.uint8), hyb=SINGLE_EVAL)
 
 
-def config_c2(hyb: HybridParams = HYB1) -> Workload:
-    """32,000-atom slab with a hemispherical 0.3 A disordered region; 300 K velocities."""
-    g = rng_for(2, 0)
+def config_c2(hyb: HybridParams = HYB1, variant: int = 0) -> Workload:
+    """32,000-atom slab with a hemispherical 0.3 A disordered region; 300 K velocities.
+    variant > 0 draws the disorder and velocities from other seeds (held-out slabs)."""
+    g = rng_for(2, 0 if variant == 0 else 20 + 2 * variant)
     nx = ny = nz = 20
     x = fcc_lattice(nx, ny, nz)
     box = _slab_box(nx, ny, nz)
@@ -227,8 +228,9 @@ def config_c2(hyb: HybridParams = HYB1) -> Workload:
     x[dis] += 0.3 * g.standard_normal((int(dis.sum()), 3))
     n = x.shape[0]
     mass = np.full(n, MASS_CU)
-    v = maxwell_boltzmann(mass, np.ones(n, bool), 300.0, rng_for(2, 1))
-    return Workload("c2_slab20", x, box, mass, np.zeros(n, np.uint8), v=v, hyb=hyb)
+    v = maxwell_boltzmann(mass, np.ones(n, bool), 300.0, rng_for(2, 1 if variant == 0 else 21 + 2 * variant))
+    name = "c2_slab20" if variant == 0 else f"c2_slab20_v{variant}"
+    return Workload(name, x, box, mass, np.zeros(n, np.uint8), v=v, hyb=hyb)
 
 
 def config_c3() -> Workload:
@@ -275,6 +277,81 @@ def config_c5(ncell: int = 100, hyb: HybridParams = HYB2, T: float = 300.0, nxy:
     ind = Indenter(center0=np.array([nx * A_CU / 2, ny * A_CU / 2, ztop + R]),
                    velocity=np.array([0.0, 0.0, -2.0e-4]), radius=R, k=10.0)
     return Workload(f"c5_indent{ncell}", x, box, mass, fixed, v=v, indenter=ind, hyb=hyb)
+
+
+# ----------------------------------------------------------------------------- selector data (c4)
+# Orthorhombic repeat cells of FCC with a (100), (110) or (111) surface normal to z:
+# unit vectors of x, y, z in cubic coordinates, repeat lengths (units of a), atoms per cell.
+_ORIENT = {
+    100: (np.eye(3), np.array([1.0, 1.0, 1.0]), 4),
+    110: (np.array([[0.0, 0.0, 1.0], [1.0, -1.0, 0.0] / np.sqrt(2.0), [1.0, 1.0, 0.0] / np.sqrt(2.0)]),
+          np.array([1.0, 1.0 / np.sqrt(2.0), 1.0 / np.sqrt(2.0)]), 2),
+    111: (np.array([[1.0, -1.0, 0.0] / np.sqrt(2.0), [1.0, 1.0, -2.0] / np.sqrt(6.0), [1.0, 1.0, 1.0] / np.sqrt(3.0)]),
+          np.array([1.0 / np.sqrt(2.0), np.sqrt(6.0) / 2.0, np.sqrt(3.0)]), 6),
+}
+
+
+def fcc_oriented(surface: int, nx: int, ny: int, nz: int, a: float = A_CU):
+    """FCC sites of nx x ny x nz orthorhombic repeat cells whose z axis is the
+    [100], [110] or [111] direction.  Returns (positions sorted by z, y, x; box lengths)."""
+    E, per, per_cell = _ORIENT[surface]
+    L = per * a * np.array([nx, ny, nz])
+    m = int(np.ceil(np.linalg.norm(L) / a)) + 2
+    c = np.arange(-m, m + 1)
+    k, j, i = np.meshgrid(c, c, c, indexing="ij")
+    cells = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(np.float64)
+    sites = ((cells[:, None, :] + _FCC_BASIS[None, :, :]).reshape(-1, 3) * a) @ E.T
+    eps = 1e-6
+    keep = np.all((sites >= -eps) & (sites < L - eps), axis=1)
+    x = sites[keep]
+    if x.shape[0] != per_cell * nx * ny * nz:
+        raise RuntimeError("oriented FCC cell count mismatch")
+    order = np.lexsort((np.round(x[:, 0], 6), np.round(x[:, 1], 6), np.round(x[:, 2], 6)))
+    return x[order], L
+
+
+def config_c4(k: int) -> Workload:
+    """Selector training structure k in [0, 200), about 5,000 atoms, 40 per category:
+    0 bulk with thermal-like Gaussian displacements (sigma 0.05-0.09 A);
+    1 bulk with 0.5-2 % vacancies (sigma 0.04-0.09 A);
+    2 slabs with (100), (110), (111) surfaces in turn (sigma 0.04-0.09 A, 10 A vacuum);
+    3 bulk with disorder sigma 0.05-0.5 A;
+    4 starting points of 300-1200 K EAM molecular dynamics (bulk for even k, (100)
+      slab for odd k; lattice sites plus sigma 0.02 A, Maxwell-Boltzmann velocities at T).
+    Categories 0-3 carry no velocities."""
+    if not 0 <= k < 200:
+        raise ValueError("k in [0, 200)")
+    g = rng_for(4, k)
+    cat = k // 40
+    mass_of = lambda x: np.full(x.shape[0], MASS_CU)
+    if cat in (0, 1, 3):
+        x = fcc_lattice(11, 11, 10)
+        box = _periodic_box(11, 11, 10)
+        if cat == 1:
+            nv = int(round(g.uniform(0.005, 0.02) * x.shape[0]))
+            x = np.delete(x, g.choice(x.shape[0], nv, replace=False), axis=0)
+        sigma = g.uniform(0.05, 0.5) if cat == 3 else g.uniform(0.04 if cat == 1 else 0.05, 0.09)
+        x = x + sigma * g.standard_normal(x.shape)
+        return Workload(f"c4_{k}", x, box, mass_of(x), np.zeros(x.shape[0], np.uint8), hyb=HYB1)
+    if cat == 2:
+        surface = (100, 110, 111)[k % 3]
+        dims = {100: (11, 11, 10), 110: (10, 14, 18), 111: (12, 7, 10)}[surface]
+        x, L = fcc_oriented(surface, *dims)
+        x = x + g.uniform(0.04, 0.09) * g.standard_normal(x.shape)
+        box = Box(lo=np.array([0.0, 0.0, -10.0]), hi=np.array([L[0], L[1], L[2] + 10.0]),
+                  periodic=np.array([True, True, False]))
+        return Workload(f"c4_{k}_s{surface}", x, box, mass_of(x), np.zeros(x.shape[0], np.uint8), hyb=HYB1)
+    T = g.uniform(300.0, 1200.0)
+    if k % 2 == 0:
+        x = fcc_lattice(11, 11, 10)
+        box = _periodic_box(11, 11, 10)
+    else:
+        x = fcc_lattice(11, 11, 10)
+        box = _slab_box(11, 11, 10)
+    x = x + 0.02 * g.standard_normal(x.shape)
+    m = mass_of(x)
+    v = maxwell_boltzmann(m, np.ones(x.shape[0], bool), T, g)
+    return Workload(f"c4_{k}_md{int(T)}", x, box, m, np.zeros(x.shape[0], np.uint8), v=v, hyb=HYB1)
 
 
 def sample_atoms(n: int, count: int, config: int, k: int = 7) -> np.ndarray:
