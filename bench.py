@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--mode", default="adaptive", choices=["adaptive", "full-ace", "full-eam"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-extras", action="store_true", help="skip full-ACE/full-EAM, error and CPU baseline legs")
+    p.add_argument("--detector", default="csp", choices=["csp", "selector"],
+                   help="detector behind lambda_0 in the timed run (centro-symmetry or the stored selector)")
     return p.parse_args()
 
 
@@ -167,9 +169,15 @@ def run_ours(args, ws, rank, local):
     hyb = hyb_for(args.mode, w.hyb)
     eam, acep = I.eam_params(0), I.ace_for_config(5)
 
-    def new_ctx(h, p=prec):
-        return ap.Context(ap.make_config(eam, acep, h, precision=p, indenter=w.indenter, lambda_every=MD_PER_STEP,
-                                         dt=w.dt))
+    sel = np.load(os.path.join(ROOT, "paper_2411_03002_gb300", "selector_cu.npz"))
+
+    def new_ctx(h, p=prec, detector=ap.DETECT_CSP):
+        c = ap.Context(ap.make_config(eam, acep, h, precision=p, indenter=w.indenter, lambda_every=MD_PER_STEP,
+                                      dt=w.dt, detector=detector, sel_p_lo=float(sel["p_lo"]),
+                                      sel_p_hi=float(sel["p_hi"])))
+        if detector == ap.DETECT_SELECTOR:
+            c.sel_set_model(sel["params"], sel["mu"], sel["inv_sigma"])
+        return c
 
     def tensors():
         return (torch.as_tensor(w.x, device=dev).clone(), torch.as_tensor(w.v, device=dev).clone(),
@@ -182,7 +190,7 @@ def run_ours(args, ws, rank, local):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    ctx = new_ctx(hyb)
+    ctx = new_ctx(hyb, detector=ap.DETECT_SELECTOR if args.detector == "selector" else ap.DETECT_CSP)
     x, v, f, mass, fixed, lam = tensors()
     ctx.build_neighbors(x, w.box)
     stats = ctx.step(x, v, f, mass, fixed, lam, 0)
@@ -263,12 +271,35 @@ def run_ours(args, ws, rank, local):
         d = (fh_ - fa_)[detected]
         extras["force_err_rms_meV_A_detected"] = float(torch.sqrt((d * d).mean()).item() * 1e3)
         extras["force_err_max_meV_A_detected"] = float(d.abs().max().item() * 1e3)
+        # atoms whose full-ACE and full-EAM forces differ by more than the selector's label threshold
+        _, fe_ = ev.eval_eam(xs, torch.ones_like(lams))
+        mobile = torch.as_tensor(w.fixed, device=dev) == 0
+        pos = (torch.linalg.vector_norm(fa_ - fe_, dim=1) > float(sel["tau"])) & mobile
+        dp = (fh_ - fa_)[pos]
         ev.close()
         del ev
+        # the same positions classified by the selector instead of CSP
+        es = new_ctx(hyb, detector=ap.DETECT_SELECTOR)
+        es.build_neighbors(xs, w.box)
+        lam_s, q_s, n_s = es.classify(xs, mobile.to(torch.uint8))
+        _, fs_ = es.eval_eam(xs, lam_s)
+        _, fs_ = es.eval_ace(xs, lam_s, q_s, n_s, f=fs_)
+        ds = (fs_ - fa_)[pos]
+        extras["selector"] = {
+            "model": "paper_2411_03002_gb300/selector_cu.npz (p_lo %.2f, p_hi %.2f)" % (sel["p_lo"], sel["p_hi"]),
+            "label_positive_fraction_of_mobile": float((pos.sum() / mobile.sum()).item()),
+            "precise_fraction": float((lam_s < 1.0).float().mean().item()),
+            "force_err_rms_meV_A_label_positive": float(torch.sqrt((ds * ds).mean()).item() * 1e3),
+            "csp_force_err_rms_meV_A_label_positive": float(torch.sqrt((dp * dp).mean()).item() * 1e3),
+            "csp_precise_fraction": float((lams < 1.0).float().mean().item()),
+        }
+        es.close()
+        del es, fs_, fa_, fe_, fh_
         torch.cuda.empty_cache()
-        # full-ACE and full-EAM on the same GPU, same workload, same code path
-        for mode in ("full-ace", "full-eam"):
-            c2 = new_ctx(hyb_for(mode, w.hyb))
+        # full-ACE, full-EAM and selector-driven adaptive MD on the same GPU, same workload, same code path
+        for mode in ("full-ace", "full-eam", "selector"):
+            c2 = (new_ctx(hyb, detector=ap.DETECT_SELECTOR) if mode == "selector"
+                  else new_ctx(hyb_for(mode, w.hyb)))
             x2, v2, f2, m2, fx2, l2 = tensors()
             c2.build_neighbors(x2, w.box)
             c2.step(x2, v2, f2, m2, fx2, l2, 0)
@@ -281,7 +312,11 @@ def run_ours(args, ws, rank, local):
                 c2.step(x2, v2, f2, m2, fx2, l2, MD_PER_STEP)
             b.record(stream)
             torch.cuda.synchronize()
-            extras[mode.replace("-", "_") + "_atom_steps_s"] = w.n * MD_PER_STEP * k2 / (a.elapsed_time(b) / 1e3)
+            rate = w.n * MD_PER_STEP * k2 / (a.elapsed_time(b) / 1e3)
+            if mode == "selector":
+                extras["selector"]["atom_steps_s"] = rate
+            else:
+                extras[mode.replace("-", "_") + "_atom_steps_s"] = rate
             c2.close()
             del c2, x2, v2, f2, m2, fx2, l2
             torch.cuda.empty_cache()
@@ -298,7 +333,8 @@ def run_ours(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == ap.PREC_MIXED else "f64", "data": "synthetic",
             "config": {"workload": f"nanoindentation-shaped FCC slab {args.ncell}^3 cells ({w.n} atoms), Hyb2 "
-                                   f"(r_lambda 8/20 A), {args.mode}, {args.precision} precision",
+                                   f"(r_lambda 8/20 A), {args.mode}, {args.precision} precision"
+                                   + (", selector detector" if args.detector == "selector" else ""),
                        "atoms": w.n, "md_steps_per_step": MD_PER_STEP, "lambda_every": MD_PER_STEP,
                        "precision": "FP32 potentials, FP64 integration and energy sums" if prec == ap.PREC_MIXED
                        else "FP64", "l2": "inputs larger than L2 (no flush)",
