@@ -198,6 +198,14 @@ ap_status ap_get_neighbors(ap_ctx* ctx, int32_t which, int32_t* d_cnt, int32_t* 
 ap_status ap_classify(ap_ctx* ctx, int64_t n, const double* d_x, const uint8_t* d_changeable, double* d_lam,
                       int32_t* d_precise_idx, int64_t* d_n_precise, void* stream);
 
+/* The precise work queue of a given lambda (section 2.4: only atoms with
+ * lambda_i < 1 need the precise potential): d_queue[0..k) = the ascending
+ * indices i with d_lam[i] < 1, *d_n_queue (device int64) = k.  d_lam [n] FP64,
+ * d_queue [n] int32.  Uses the context's scratch: needs a neighbour build on at
+ * least n atoms before (AP_ERR_STATE otherwise). */
+ap_status ap_precise_queue(ap_ctx* ctx, int64_t n, const double* d_lam, int32_t* d_queue, int64_t* d_n_queue,
+                           void* stream);
+
 /* Forget the CSP/lambda histories and the previous lambda. */
 ap_status ap_reset_lambda(ap_ctx* ctx);
 

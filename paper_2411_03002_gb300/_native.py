@@ -62,6 +62,7 @@ SIGNATURES = [
     ("ap_get_neighbors", I32, [P, I32, P, P, P, I64, P]),
     ("ap_classify", I32, [P, I64, P, P, P, P, P, P]),
     ("ap_reset_lambda", I32, [P]),
+    ("ap_precise_queue", I32, [P, I64, P, P, P, P]),
     ("ap_get_lambda_state", I32, [P, P, P, P, P, P, P]),
     ("ap_eval_eam", I32, [P, I64, P, P, P, P, P]),
     ("ap_eval_ace", I32, [P, I64, P, P, P, P, P, P, P]),

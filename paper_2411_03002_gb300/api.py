@@ -190,6 +190,14 @@ class Context:
                                       _stream(stream)))
         return lam, idx, cnt
 
+    def precise_queue(self, lam, stream=None):
+        """(queue int32 [max(n,1)], count int64 [1]) of the atoms with lambda < 1."""
+        n = lam.shape[0]
+        idx = torch.empty(max(n, 1), dtype=torch.int32, device=lam.device)
+        cnt = torch.empty(1, dtype=torch.int64, device=lam.device)
+        self._ck(self.lib.ap_precise_queue(self.h, n, _ptr(lam), _ptr(idx), _ptr(cnt), _stream(stream)))
+        return idx, cnt
+
     def reset_lambda(self):
         self._ck(self.lib.ap_reset_lambda(self.h))
 

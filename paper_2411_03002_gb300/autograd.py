@@ -17,14 +17,6 @@ import torch
 from .api import Context
 
 
-def _queue(lam: torch.Tensor):
-    idx = torch.nonzero(lam < 1.0).flatten().to(torch.int32).contiguous()
-    cnt = torch.tensor([idx.numel()], dtype=torch.int64, device=lam.device)
-    if idx.numel() == 0:
-        idx = torch.zeros(1, dtype=torch.int32, device=lam.device)
-    return idx, cnt
-
-
 class APEnergy(torch.autograd.Function):
     @staticmethod
     def forward(fctx, x: torch.Tensor, lam: torch.Tensor, ctx: Context, box=None, batch=None):
@@ -35,7 +27,7 @@ class APEnergy(torch.autograd.Function):
             ctx.build_neighbors_batch(x, offsets, boxes)
         else:
             ctx.build_neighbors(x, box)
-        idx, cnt = _queue(lam)
+        idx, cnt = ctx.precise_queue(lam)
         e_fast, _ = ctx.eval_eam(x, lam)
         e_prec, _ = ctx.eval_ace(x, lam, idx, cnt, forces=False)
         _, e_tot = ctx.blend_forces(lam, e_fast, e_prec)
@@ -53,7 +45,7 @@ class APEnergy(torch.autograd.Function):
             ctx.build_neighbors_batch(x, *fctx.batch)
         else:
             ctx.build_neighbors(x, fctx.box)
-        idx, cnt = _queue(lam)
+        idx, cnt = ctx.precise_queue(lam)
         _, f = ctx.eval_eam(x, lam)
         _, f = ctx.eval_ace(x, lam, idx, cnt, f=f)
         return (-grad_out * f, None, None, None, None)

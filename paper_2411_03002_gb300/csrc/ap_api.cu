@@ -318,6 +318,17 @@ __global__ void k_compact_q(int n, const int* flag, const int* scan, int* out, i
   if (i == 0) *count32 = scan[n];
 }
 
+__global__ void k_flag_lam(int n, const double* lam, int* flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = lam[i] < 1.0 ? 1 : 0;
+}
+
+__global__ void k_compact_q64(int n, const int* flag, const int* scan, int* out, long long* count) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) out[scan[i]] = i;
+  if (i == 0) *count = scan[n];
+}
+
 // Precise queue from an imported lambda (restart without a new lambda sample).
 void queue_from_lambda(ap_ctx* c, cudaStream_t s) {
   int n = (int)c->n;
@@ -554,6 +565,24 @@ ap_status ap_classify(ap_ctx* c, int64_t n, const double* d_x, const uint8_t* d_
   classify_async(c, d_x, d_changeable, d_lam, d_precise_idx, d_n_precise, s);
   CK(cudaGetLastError());
   c->lam_ready = true;
+  return AP_OK;
+}
+
+ap_status ap_precise_queue(ap_ctx* c, int64_t n, const double* d_lam, int32_t* d_queue, int64_t* d_n_queue,
+                           void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (n < 0 || !d_n_queue || (n > 0 && (!d_lam || !d_queue))) return fail(c, AP_ERR_ARG, "null argument");
+  if (n > c->n_cap) return fail(c, AP_ERR_STATE, "ap_precise_queue needs a neighbour build on at least n atoms");
+  cudaStream_t s = S(stream);
+  if (n == 0) {
+    CK(cudaMemsetAsync(d_n_queue, 0, sizeof(int64_t), s));
+    return AP_OK;
+  }
+  const int nn = (int)n;
+  k_flag_lam<<<(nn + 255) / 256, 256, 0, s>>>(nn, d_lam, c->d_flag);
+  scan_exclusive(c->d_flag, c->d_scan, nn, c->d_scan_tmp, s);
+  k_compact_q64<<<(nn + 255) / 256, 256, 0, s>>>(nn, c->d_flag, c->d_scan, d_queue, (long long*)d_n_queue);
+  CK(cudaGetLastError());
   return AP_OK;
 }
 

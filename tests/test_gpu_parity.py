@@ -275,3 +275,16 @@ def test_md_matches_oracle_trajectory_fp64():
     lg = lam.cpu().numpy()
     assert np.abs(lg - lam_o).max() < 1e-8
     assert np.array_equal(lg < 1.0, lam_o < 1.0)
+
+
+def test_precise_queue_from_lambda(c1):
+    ctx = ctx_for(c1, ap.PREC_MIXED)
+    ctx.build_neighbors(T(c1.x), c1.box)
+    g = np.random.Generator(np.random.PCG64(I.seed_for(1, 31)))
+    lam = np.where(g.random(c1.n) < 0.5, 1.0, g.random(c1.n))
+    lam[[0, 5, c1.n - 1]] = [1.0, np.nextafter(1.0, 0.0), 0.0]     # exact edges
+    idx, cnt = ctx.precise_queue(T(lam))
+    k = int(cnt.item())
+    assert np.array_equal(idx[:k].cpu().numpy(), np.nonzero(lam < 1.0)[0])
+    idx, cnt = ctx.precise_queue(T(np.ones(c1.n)))
+    assert int(cnt.item()) == 0
