@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--mode", default="adaptive", choices=["adaptive", "full-ace", "full-eam"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-extras", action="store_true", help="skip full-ACE/full-EAM, error and CPU baseline legs")
+    p.add_argument("--skin", type=float, default=1.0, help="neighbour-list skin (A); lists are rebuilt every "
+                   "lambda update, so skin/2 bounds the displacement over 10 MD steps")
     p.add_argument("--detector", default="csp", choices=["csp", "selector"],
                    help="detector behind lambda_0 in the timed run (centro-symmetry or the stored selector)")
     return p.parse_args()
@@ -173,7 +175,7 @@ def run_ours(args, ws, rank, local):
 
     def new_ctx(h, p=prec, detector=ap.DETECT_CSP):
         c = ap.Context(ap.make_config(eam, acep, h, precision=p, indenter=w.indenter, lambda_every=MD_PER_STEP,
-                                      dt=w.dt, detector=detector, sel_p_lo=float(sel["p_lo"]),
+                                      dt=w.dt, skin=args.skin, detector=detector, sel_p_lo=float(sel["p_lo"]),
                                       sel_p_hi=float(sel["p_hi"])))
         if detector == ap.DETECT_SELECTOR:
             c.sel_set_model(sel["params"], sel["mu"], sel["inv_sigma"])
@@ -274,7 +276,11 @@ def run_ours(args, ws, rank, local):
         # atoms whose full-ACE and full-EAM forces differ by more than the selector's label threshold
         _, fe_ = ev.eval_eam(xs, torch.ones_like(lams))
         mobile = torch.as_tensor(w.fixed, device=dev) == 0
-        pos = (torch.linalg.vector_norm(fa_ - fe_, dim=1) > float(sel["tau"])) & mobile
+        # judged region: mobile atoms with no fixed (always-EAM) atom inside the ACE cutoff,
+        # since no detector can remove the error that the fixed layers contribute
+        z_fixed = float(w.x[w.fixed != 0, 2].max()) if (w.fixed != 0).any() else -1e30
+        judged = mobile & (torch.as_tensor(w.x[:, 2], device=dev) > z_fixed + float(acep.rc))
+        pos = (torch.linalg.vector_norm(fa_ - fe_, dim=1) > float(sel["tau"])) & judged
         dp = (fh_ - fa_)[pos]
         ev.close()
         del ev
@@ -287,7 +293,7 @@ def run_ours(args, ws, rank, local):
         ds = (fs_ - fa_)[pos]
         extras["selector"] = {
             "model": "paper_2411_03002_gb300/selector_cu.npz (p_lo %.2f, p_hi %.2f)" % (sel["p_lo"], sel["p_hi"]),
-            "label_positive_fraction_of_mobile": float((pos.sum() / mobile.sum()).item()),
+            "label_positive_fraction_of_judged": float((pos.sum() / judged.sum()).item()),
             "precise_fraction": float((lam_s < 1.0).float().mean().item()),
             "force_err_rms_meV_A_label_positive": float(torch.sqrt((ds * ds).mean()).item() * 1e3),
             "csp_force_err_rms_meV_A_label_positive": float(torch.sqrt((dp * dp).mean()).item() * 1e3),

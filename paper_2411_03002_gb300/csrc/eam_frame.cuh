@@ -43,7 +43,26 @@ __device__ inline float rexp(float v) { return __expf(v); }
 __device__ inline double rexp(double v) { return exp(v); }
 __device__ inline float rsqrt_(float v) { return rsqrtf(v); }
 __device__ inline double rsqrt_(double v) { return rsqrt(v); }
-__device__ inline float rcp_(float v) { return __frcp_rn(v); }
+// Tuning parameters of the EAM passes (compile-time): lanes per atom, minimum
+// resident blocks per SM (register cap), and the FP32 reciprocal (1: approximate
+// MUFU reciprocal, 0: correctly rounded).
+#ifndef AP_EAM_LANES
+#define AP_EAM_LANES 4
+#endif
+#ifndef AP_EAM_MINB
+#define AP_EAM_MINB 6   // FP32 only: <= 42 registers, 48 resident warps per SM
+#endif
+#ifndef AP_EAM_FAST_RCP
+#define AP_EAM_FAST_RCP 0
+#endif
+
+__device__ inline float rcp_(float v) {
+#if AP_EAM_FAST_RCP
+  return __fdividef(1.f, v);
+#else
+  return __frcp_rn(v);
+#endif
+}
 __device__ inline double rcp_(double v) { return 1.0 / v; }
 
 // Per-atom frame: cell code and box constants of atom i, held in registers.

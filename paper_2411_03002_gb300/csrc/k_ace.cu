@@ -221,8 +221,16 @@ namespace {
 
 constexpr int kCols = 36;            // 32 neighbour slots + 4 pad (16-byte rows, conflict-free)
 constexpr int kRows = 33;            // 8 radial + 25 angular rows
+// Warps per CTA and the minimum resident CTAs per SM
+// the compiler budgets registers for; compile-time tuning parameters.
+#ifndef AP_ACE_WARPS
+#define AP_ACE_WARPS 6
+#endif
+#ifndef AP_ACE_MINB
+#define AP_ACE_MINB 4   // FP32 only: four 6-warp CTAs per SM (shared memory and <= 85 registers)
+#endif
 template <typename R>
-constexpr int kWarps = sizeof(R) == 4 ? 12 : 4;   // warps per CTA: two CTAs fit per SM in FP32
+constexpr int kWarps = sizeof(R) == 4 ? AP_ACE_WARPS : 4;
 
 template <typename R>
 struct V;
@@ -474,7 +482,7 @@ struct AceArgs {
 };
 
 template <typename R, bool FORCES>
-__global__ void __launch_bounds__(kWarps<R> * 32) k_ace(AceArgs<R> a) {
+__global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB : 1) k_ace(AceArgs<R> a) {
   // Shared memory (every region a multiple of 32 bytes, so 4-wide FP64 loads stay aligned):
   //   W [320] | M2 [320] | C1 [8] |
   //   per warp: compacted neighbours [kListCap][4] | tile [kRows][kCols]

@@ -20,7 +20,7 @@ namespace ap {
 namespace {
 
 template <typename R, int G, bool STORED>
-__global__ void __launch_bounds__(256) k_eam_density(int n, const SysInfo* __restrict__ sys,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? AP_EAM_MINB : 1) k_eam_density(int n, const SysInfo* __restrict__ sys,
                                                      const int* __restrict__ atom_sys,
                                                      const typename Shadow<R>::T* __restrict__ sh,
                                                      const int* __restrict__ nbr, const int* __restrict__ off,
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_eam_density(int n, const SysInfo* __res
 }
 
 template <typename R, int G, bool STORED>
-__global__ void __launch_bounds__(256) k_eam_force(int n, const SysInfo* __restrict__ sys,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? AP_EAM_MINB : 1) k_eam_force(int n, const SysInfo* __restrict__ sys,
                                                    const int* __restrict__ atom_sys,
                                                    const typename Shadow<R>::T* __restrict__ sh,
                                                    const int* __restrict__ nbr, const int* __restrict__ off,
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) k_eam_force(int n, const SysInfo* __restr
 template <typename R, bool STORED>
 void run_eam(ap_ctx* c, const typename Shadow<R>::T* sh, const double* d_lam, double* d_e_fast, double* d_f,
              bool accumulate, cudaStream_t s) {
-  constexpr int G = 8;
+  constexpr int G = AP_EAM_LANES;
   const int threads = 256;
   int blocks = (int)((c->n * G + threads - 1) / threads);
   EamP<R> p = make_params<R>(c->cfg);
