@@ -27,11 +27,15 @@ def _nvcc() -> str:
 
 
 def sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    """The library's translation units: every .cu and .cpp in csrc/ except the
+    generators (gen_*.cpp, which have a main)."""
+    cpp = [p for p in glob.glob(os.path.join(CSRC, "*.cpp")) if not os.path.basename(p).startswith("gen_")]
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + cpp)
 
 
 def _deps():
-    return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "ap.h")]
+    return (sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.inc"))
+            + [os.path.join(ROOT, "include", "ap.h")])
 
 
 def up_to_date() -> bool:
@@ -48,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(OUT, os.path.basename(src).replace(".cu", ".o"))
+        obj = os.path.join(OUT, os.path.splitext(os.path.basename(src))[0] + ".o")
         cmd = [nvcc, "-c", src, "-o", obj, "-I", os.path.join(ROOT, "include")] + NVCC_FLAGS
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

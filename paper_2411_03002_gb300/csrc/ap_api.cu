@@ -182,6 +182,20 @@ ap_status ensure_capacity(ap_ctx* c, int64_t n) {
   CK(dalloc(c->d_eatom, m));
   CK(dalloc(c->d_eext, m));
   CK(dalloc(c->d_changeable, m));
+  {
+    const size_t rb = c->cfg.precision == AP_PREC_FP64 ? sizeof(double) : sizeof(float);
+    CK(dalloc(c->d_ace_slots, (size_t)m * 192));
+    CK(dalloc(c->d_ace_nin, m));
+    CK(dalloc(c->d_ace_e12, m));
+    CK(dalloc(c->d_ace_e3, m));
+    void** bufs[3] = {&c->d_ace_a48, &c->d_ace_dA, &c->d_ace_de3};
+    const size_t per[3] = {48, 200, 48};
+    for (int k = 0; k < 3; ++k) {
+      if (*bufs[k]) cudaFree(*bufs[k]);
+      *bufs[k] = nullptr;
+      CK(cudaMalloc(bufs[k], rb * per[k] * (size_t)m));
+    }
+  }
   size_t need_tmp = scan_tmp_bytes(std::max<int64_t>(c->n_cells + 1, m + 1)) / sizeof(int) + 1;
   if (need_tmp > c->scan_tmp_cap) {
     c->scan_tmp_cap = need_tmp;
@@ -433,6 +447,10 @@ ap_status ap_create(const ap_config* h_cfg, ap_ctx** out) {
     delete c;
     return AP_ERR_ARG;
   }
+  if (!ace_nu3_matches(c->ace)) {   // the generated nu = 3 code is out of date
+    delete c;
+    return AP_ERR_STATE;
+  }
   upload_ace_tables(c);
   e = cudaMalloc(&c->d_sc, sizeof(DevScalars));
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_sc, sizeof(DevScalars));
@@ -455,8 +473,8 @@ void ap_destroy(ap_ctx* c) {
                   c->d_nbr_ace, c->d_off_ace, c->d_cnt_ace, c->d_csp, c->d_csp_avg, c->d_lam0, c->d_lam_min,
                   c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected,
                   c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_efast, c->d_eprec,
-                  c->d_eatom, c->d_eext, c->d_changeable, c->d_term_idx, c->d_term_coef32, c->d_term_coef64,
-                  c->d_W32, c->d_W64, c->d_e3_idx, c->d_e3_coef32, c->d_e3_coef64, c->d_e3_pack, c->d_scan_tmp, c->d_red,
+                  c->d_eatom, c->d_eext, c->d_changeable, c->d_W32, c->d_W64, c->d_ace_slots, c->d_ace_nin,
+                  c->d_ace_a48, c->d_ace_dA, c->d_ace_e12, c->d_ace_de3, c->d_ace_e3, c->d_scan_tmp, c->d_red,
                   c->d_sel_model, c->d_sel_master, c->d_sel_m1, c->d_sel_m2, c->d_sel_grad, c->d_sel_partial,
                   c->d_sel_rho, c->d_sel_feat, c->d_sel_score, c->d_sel_z, c->d_sel_h1, c->d_sel_h2, c->d_sc};
   for (void* p : ptrs)

@@ -75,8 +75,8 @@ struct DevScalars {
   int n_detected;     // |D|
   int n_precise;      // |P| (int32 copy used by kernels)
   int work_counter;   // persistent-kernel work counter
+  int work_counter2;  // second persistent-kernel work counter (right after work_counter)
   unsigned int max_disp2_bits;  // float bits of the largest squared displacement
-  int pad;
   long long n_precise64;
   double e_total;
   double e_kin;
@@ -97,12 +97,11 @@ struct AceTables {
   int n_terms = 0;
   std::vector<double> c1;        // [8] nu = 1 coefficients
   std::vector<double> m2;        // [5][8][8] nu = 2 symmetric coupling matrices
-  // nu = 3 gradient programs: entry (k, lane) at [k * 32 + lane]; packed
-  // b | c << 6 | out << 12 | flush << 24 over the 48 A entries with n <= 2, l <= 3,
-  // value coef: dE3/dA[out] += coef * A[b] * A[c].
-  std::vector<uint32_t> e3_idx;
-  std::vector<double> e3_coef;
-  int e3_len = 0;                // entries per lane program (padded)
+  // nu = 3 merged monomials coef * A_a A_b A_c over the 48 entries with n <= 2,
+  // l <= 3 (a <= b <= c, key c | b << 6 | a << 12, ascending keys); the
+  // lane-per-atom kernel's straight-line code (ace_nu3.inc) is generated from nu3_key.
+  std::vector<uint32_t> nu3_key;
+  std::vector<double> nu3_coef;
 };
 void build_ace_tables(const ap_config& cfg, AceTables& t);
 
@@ -199,15 +198,16 @@ struct ap_ctx {
   double* d_eext = nullptr;      // [n] indenter energy per atom (ap_step)
   uint8_t* d_changeable = nullptr;  // [n] complement of the fixed mask (ap_step)
   bool restart_pending = false;  // lambda state imported; next ap_step reuses it
-  int* d_term_idx = nullptr;
-  float* d_term_coef32 = nullptr;
-  double* d_term_coef64 = nullptr;
   float* d_W32 = nullptr;        // [W (320) | M2 (320) | C1 (8)]
   double* d_W64 = nullptr;
-  uint32_t* d_e3_idx = nullptr;  // nu = 3 gradient programs
-  uint2* d_e3_pack = nullptr;    // same, FP32 coefficient packed with the index
-  float* d_e3_coef32 = nullptr;
-  double* d_e3_coef64 = nullptr;
+  // ACE scratch per precise-queue position (sized for n atoms, working precision)
+  uint16_t* d_ace_slots = nullptr;  // [n][192] row entries inside ace_rc
+  int* d_ace_nin = nullptr;         // [n]
+  void* d_ace_a48 = nullptr;        // [n][48]
+  void* d_ace_dA = nullptr;         // [n][200]
+  double* d_ace_e12 = nullptr;      // [n]
+  void* d_ace_de3 = nullptr;        // [n][48]
+  double* d_ace_e3 = nullptr;       // [n]
 
   // scan scratch
   int* d_scan_tmp = nullptr;
@@ -279,6 +279,7 @@ void launch_eam(ap_ctx* c, const double* d_lam, double* d_e_fast, double* d_f, b
 
 // k_ace.cu
 void upload_ace_tables(ap_ctx* c);
+bool ace_nu3_matches(const AceTables& t);
 void launch_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_prec, bool forces, cudaStream_t s);
 void launch_ace_finalize(ap_ctx* c, double* d_f, cudaStream_t s);
 

@@ -10,14 +10,16 @@
 // Because R is linear in g, A = W . G with G_klm = sum_j g_k Y_lm, and the force
 // needs only u_klm = (1/N0) sum_n W[l][n][k] dE/dA_nlm per atom:
 //   dE_i/dr_ij = sum_lm [ (sum_k u_klm g'_k) Y_lm r^ + (sum_k u_klm g_k) grad Y_lm ].
-// One warp per precise atom, persistent CTAs pulling atoms from the queue:
-//   pass 0   the row entries inside r_c are compacted (j and r_ij) into shared memory;
-//   stage A  lanes evaluate g and Y for 32 neighbours into a shared tile, then
-//            contract G = g^T Y with 4-wide vector loads along the neighbour axis;
-//   stage B  nu=3 through per-lane gradient programs (no atomics per term), nu=2 as
-//            symmetric 8x8 matrix-vector products per (l,m), nu=1 directly;
-//   stage C  lanes recompute g, g', Y, grad Y per neighbour (no A tiles stored),
-//            contract with u and scatter -w_i p_ij to neighbour j, +w_i sum p to i.
+// Three kernels per evaluation, communicating through per-queue-position scratch:
+//   k_ace_basis    one warp per precise atom (persistent CTAs, atomic work counter):
+//                  row entries inside r_c compacted; G = g^T Y over 32-neighbour
+//                  shared tiles; A = (1/N0) W . G; nu = 1, 2 energy and gradient;
+//   k_ace_nu3      one lane per precise atom: the nu = 3 energy and gradient with A
+//                  and dE/dA in registers, straight-line code over the merged
+//                  monomials generated from the basis (ace_nu3.inc);
+//   k_ace_adjoint  one warp per precise atom: u = W^T dE/dA / N0; lanes recompute g,
+//                  g', Y, grad Y per in-range neighbour, contract with u, and scatter
+//                  -w_i p_ij to neighbour j and +w_i sum p to i.
 #include <complex>
 #include <algorithm>
 #include <cstring>
@@ -26,195 +28,6 @@
 #include "ap_internal.cuh"
 
 namespace ap {
-
-// ------------------------------------------------------------------ host tables
-namespace {
-
-double fact(int n) {
-  double r = 1.0;
-  for (int k = 2; k <= n; ++k) r *= (double)k;
-  return r;
-}
-
-// Wigner 3j symbol by the Racah formula.
-double wigner3j(int j1, int j2, int j3, int m1, int m2, int m3) {
-  if (m1 + m2 + m3 != 0) return 0.0;
-  if (j3 < std::abs(j1 - j2) || j3 > j1 + j2) return 0.0;
-  if (std::abs(m1) > j1 || std::abs(m2) > j2 || std::abs(m3) > j3) return 0.0;
-  double tri = fact(j1 + j2 - j3) * fact(j1 - j2 + j3) * fact(-j1 + j2 + j3) / fact(j1 + j2 + j3 + 1);
-  double pre = std::sqrt(tri * fact(j1 + m1) * fact(j1 - m1) * fact(j2 + m2) * fact(j2 - m2) * fact(j3 + m3) *
-                         fact(j3 - m3));
-  double sum = 0.0;
-  for (int k = 0; k <= j1 + j2 + j3; ++k) {
-    int a1 = j3 - j2 + k + m1, a2 = j3 - j1 + k - m2, a3 = j1 + j2 - j3 - k, a4 = j1 - k - m1, a5 = j2 - k + m2;
-    if (a1 < 0 || a2 < 0 || a3 < 0 || a4 < 0 || a5 < 0) continue;
-    sum += ((k & 1) ? -1.0 : 1.0) / (fact(k) * fact(a1) * fact(a2) * fact(a3) * fact(a4) * fact(a5));
-  }
-  int ph = j1 - j2 - m3;
-  return ((ph % 2 != 0) ? -1.0 : 1.0) * pre * sum;
-}
-
-// Integral of three complex spherical harmonics (Condon-Shortley phase).
-double gaunt_complex(int l1, int m1, int l2, int m2, int l3, int m3) {
-  double w0 = wigner3j(l1, l2, l3, 0, 0, 0);
-  if (w0 == 0.0) return 0.0;
-  return std::sqrt((2.0 * l1 + 1.0) * (2.0 * l2 + 1.0) * (2.0 * l3 + 1.0) / (4.0 * M_PI)) * w0 *
-         wigner3j(l1, l2, l3, m1, m2, m3);
-}
-
-// Real harmonic (no Condon-Shortley phase, Y_1,-1 ~ y, Y_11 ~ x) as a combination
-// of complex ones: returns the coefficient of Y_l^m in R_l,mu.
-std::complex<double> real_from_complex(int mu, int m) {
-  const double s = 1.0 / std::sqrt(2.0);
-  if (mu == 0) return m == 0 ? 1.0 : 0.0;
-  int a = std::abs(mu);
-  double sg = (a & 1) ? -1.0 : 1.0;
-  if (mu > 0) {
-    if (m == a) return sg * s;
-    if (m == -a) return s;
-    return 0.0;
-  }
-  if (m == a) return std::complex<double>(0.0, -sg * s);
-  if (m == -a) return std::complex<double>(0.0, s);
-  return 0.0;
-}
-
-double gaunt_real(int l1, int u1, int l2, int u2, int l3, int u3) {
-  std::complex<double> acc = 0.0;
-  int m1s[2] = {std::abs(u1), -std::abs(u1)};
-  int m2s[2] = {std::abs(u2), -std::abs(u2)};
-  int m3s[2] = {std::abs(u3), -std::abs(u3)};
-  for (int a = 0; a < (u1 ? 2 : 1); ++a)
-    for (int b = 0; b < (u2 ? 2 : 1); ++b)
-      for (int c = 0; c < (u3 ? 2 : 1); ++c) {
-        int m1 = m1s[a], m2 = m2s[b], m3 = m3s[c];
-        std::complex<double> k =
-            real_from_complex(u1, m1) * real_from_complex(u2, m2) * real_from_complex(u3, m3);
-        if (k == std::complex<double>(0.0, 0.0)) continue;
-        acc += k * gaunt_complex(l1, m1, l2, m2, l3, m3);
-      }
-  return acc.real();
-}
-
-inline int aidx(int n, int l, int m) { return n * 25 + l * l + l + m; }
-
-}  // namespace
-
-void build_ace_tables(const ap_config& cfg, AceTables& t) {
-  t.gaunt.assign(4 * 7 * 4 * 7 * 4 * 7, 0.0);
-  auto G = [&](int l1, int m1, int l2, int m2, int l3, int m3) -> double& {
-    return t.gaunt[((((l1 * 7 + m1 + 3) * 4 + l2) * 7 + m2 + 3) * 4 + l3) * 7 + m3 + 3];
-  };
-  for (int l1 = 0; l1 <= 3; ++l1)
-    for (int m1 = -l1; m1 <= l1; ++m1)
-      for (int l2 = 0; l2 <= 3; ++l2)
-        for (int m2 = -l2; m2 <= l2; ++m2)
-          for (int l3 = 0; l3 <= 3; ++l3)
-            for (int m3 = -l3; m3 <= l3; ++m3) G(l1, m1, l2, m2, l3, m3) = gaunt_real(l1, m1, l2, m2, l3, m3);
-  // enumeration: nu=1 by n; nu=2 by (n1 <= n2, l); nu=3 by (p1 <= p2 <= p3), p = 4n + l
-  t.desc.clear();
-  for (int n = 0; n < 8; ++n) t.desc.insert(t.desc.end(), {1, n, 0, 0, 0, 0, 0});
-  for (int n1 = 0; n1 < 8; ++n1)
-    for (int n2 = n1; n2 < 8; ++n2)
-      for (int l = 0; l <= 4; ++l) t.desc.insert(t.desc.end(), {2, n1, n2, 0, l, l, 0});
-  for (int p1 = 0; p1 < 12; ++p1)
-    for (int p2 = p1; p2 < 12; ++p2)
-      for (int p3 = p2; p3 < 12; ++p3) {
-        int l1 = p1 & 3, l2 = p2 & 3, l3 = p3 & 3;
-        if (l3 < std::abs(l1 - l2) || l3 > l1 + l2 || ((l1 + l2 + l3) & 1)) continue;
-        double mx = 0.0;
-        for (int m1 = -l1; m1 <= l1; ++m1)
-          for (int m2 = -l2; m2 <= l2; ++m2)
-            for (int m3 = -l3; m3 <= l3; ++m3) mx = std::fmax(mx, std::fabs(G(l1, m1, l2, m2, l3, m3)));
-        if (mx < 1e-12) continue;
-        t.desc.insert(t.desc.end(), {3, p1 >> 2, p2 >> 2, p3 >> 2, l1, l2, l3});
-      }
-  t.nb = (int)(t.desc.size() / 7);
-  // nu = 1: E1 = sum_n c1[n] A_n00.
-  // nu = 2: E2 = 1/2 sum_lm A_lm^T M_l A_lm with the symmetric 8x8 matrices
-  //         M_l[n1][n2] = c(n1,n2,l) (n1 != n2), M_l[n][n] = 2 c(n,n,l), so that
-  //         dE2/dA_{n,lm} = sum_n2 M_l[n][n2] A_{n2,lm}.
-  // nu = 3: flattened Gaunt product terms coef * A[a1] A[a2] A[a3] (coef = c_v G),
-  //         interleaved across functions so that neighbouring terms touch
-  //         different A entries.
-  t.c1.assign(8, 0.0);
-  t.m2.assign(5 * 64, 0.0);
-  std::vector<std::vector<std::pair<int, double>>> per_fn;
-  for (int v = 0; v < t.nb; ++v) {
-    const int* d = &t.desc[7 * v];
-    double cv = (v < cfg.ace_nc) ? cfg.ace_c[v] : 0.0;
-    if (d[0] == 1) {
-      t.c1[d[1]] = cv;
-    } else if (d[0] == 2) {
-      int l = d[4], n1 = d[1], n2 = d[2];
-      if (n1 == n2) {
-        t.m2[l * 64 + n1 * 8 + n1] = 2.0 * cv;
-      } else {
-        t.m2[l * 64 + n1 * 8 + n2] = cv;
-        t.m2[l * 64 + n2 * 8 + n1] = cv;
-      }
-    } else {
-      int l1 = d[4], l2 = d[5], l3 = d[6];
-      std::vector<std::pair<int, double>> terms;
-      for (int m1 = -l1; m1 <= l1; ++m1)
-        for (int m2 = -l2; m2 <= l2; ++m2)
-          for (int m3 = -l3; m3 <= l3; ++m3) {
-            double g = G(l1, m1, l2, m2, l3, m3);
-            if (std::fabs(g) < 1e-14) continue;
-            terms.push_back({aidx(d[1], l1, m1) | (aidx(d[2], l2, m2) << 8) | (aidx(d[3], l3, m3) << 16), cv * g});
-          }
-      per_fn.push_back(terms);
-    }
-  }
-  t.term_idx.clear();
-  t.term_coef.clear();
-  for (size_t k = 0;; ++k) {
-    bool any = false;
-    for (auto& fn : per_fn)
-      if (k < fn.size()) {
-        t.term_idx.push_back(fn[k].first);
-        t.term_coef.push_back(fn[k].second);
-        any = true;
-      }
-    if (!any) break;
-  }
-  t.n_terms = (int)t.term_idx.size();
-
-  // nu = 3 gradient as 32 balanced per-lane programs.  Each term coef*A1*A2*A3
-  // contributes coef*A2*A3 to dE/dA1, coef*A1*A3 to dE/dA2 and coef*A1*A2 to dE/dA3;
-  // the entries are sorted by output, cut into 32 contiguous ranges of equal
-  // length, and a lane flushes its register sum whenever its output changes.
-  auto c48 = [](int a) { return (a / 25) * 16 + (a % 25); };   // n <= 2, lm < 16
-  struct E3 {
-    int out, b, c;
-    double coef;
-  };
-  std::vector<E3> ent;
-  for (int k = 0; k < t.n_terms; ++k) {
-    int pk = t.term_idx[k];
-    int a1 = c48(pk & 255), a2 = c48((pk >> 8) & 255), a3 = c48((pk >> 16) & 255);
-    double cf = t.term_coef[k];
-    ent.push_back({a1, a2, a3, cf});
-    ent.push_back({a2, a1, a3, cf});
-    ent.push_back({a3, a1, a2, cf});
-  }
-  std::stable_sort(ent.begin(), ent.end(), [](const E3& x, const E3& y) { return x.out < y.out; });
-  const int total = (int)ent.size();
-  const int per = (total + 31) / 32;
-  t.e3_len = per;
-  t.e3_idx.assign((size_t)per * 32, 0u);
-  t.e3_coef.assign((size_t)per * 32, 0.0);
-  for (int lane = 0; lane < 32; ++lane) {
-    int b0 = lane * per, b1 = std::min(total, b0 + per);
-    for (int q = b0; q < b1; ++q) {
-      bool flush = (q + 1 == b1) || ent[q + 1].out != ent[q].out;
-      uint32_t p = (uint32_t)ent[q].b | ((uint32_t)ent[q].c << 6) | ((uint32_t)ent[q].out << 12) |
-                   (flush ? (1u << 24) : 0u);
-      t.e3_idx[(size_t)(q - b0) * 32 + lane] = p;
-      t.e3_coef[(size_t)(q - b0) * 32 + lane] = ent[q].coef;
-    }
-  }
-}
 
 // ------------------------------------------------------------------ device code
 namespace {
@@ -449,13 +262,20 @@ __device__ inline int unpack_j(float v) { return __float_as_int(v); }
 __device__ inline int unpack_j(double v) { return (int)__double_as_longlong(v); }
 
 constexpr int kListCap = 192;   // neighbours inside ace_rc kept per precise atom (FCC bulk: 134)
+template <typename R>
+constexpr int kWarps3 = sizeof(R) == 4 ? 8 : 4;   // warps per CTA of the adjoint kernel
 
+#include "ace_nu3.inc"
+
+// Arguments of the three ACE kernels.  Scratch indexed by the queue position q
+// carries the per-atom state from one kernel to the next.
 template <typename R>
 struct AceArgs {
   const int* queue;
   const DevScalars* sc;
   DevScalars* stats;
   int* counter;
+  int* counter2;
   const SysInfo* sys;
   const int* atom_sys;
   const typename V<R>::S4* sh;
@@ -464,13 +284,6 @@ struct AceArgs {
   const int* cnt;
   int cap;
   const double* lam;
-  const int* term_idx;
-  const R* term_coef;
-  int n_terms;
-  const uint32_t* e3_idx;
-  const R* e3_coef;
-  const uint2* e3_pack;   // FP32 programs as (index, coefficient bits) pairs
-  int e3_len;
   const R* W;
   const R* M2;
   const R* C1;
@@ -479,15 +292,32 @@ struct AceArgs {
   double* e_prec;
   float4* facc32;
   double* facc64;
+  uint16_t* slots;   // [q][kListCap] row entries inside ace_rc, in row order
+  int* nin;          // [q] their number
+  R* a48;            // [q][48] A entries with n <= 2, l <= 3 (input of nu = 3)
+  R* dA;             // [q][200] dE/dA of nu = 1, 2
+  double* e12;       // [q] E of nu = 1, 2
+  R* de3;            // [q][48] dE3/dA
+  double* e3;        // [q] E3
 };
 
-template <typename R, bool FORCES>
-__global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB : 1) k_ace(AceArgs<R> a) {
-  // Shared memory (every region a multiple of 32 bytes, so 4-wide FP64 loads stay aligned):
-  //   W [320] | M2 [320] | C1 [8] |
-  //   per warp: compacted neighbours [kListCap][4] | tile [kRows][kCols]
-  // A, dA, U, the G scratch and the 48 nu=3 inputs alias the tile once stage A's
-  // contraction is done.  The nu=3 gradient programs stay in global memory (L1).
+// nu = 3 coefficients, passed by value (kernel parameter space), in the order of kNu3Key.
+template <typename R>
+struct Nu3Coef {
+  R c[AP_NU3_N];
+};
+
+// Kernel 1, one warp per precise atom (persistent CTAs, atomic work counter):
+//   pass 0   row entries inside r_c compacted (displacement and j) into shared memory,
+//            their row positions kept for kernel 3;
+//   stage A  lanes evaluate g and Y for 32 neighbours into a shared tile, then
+//            contract G = g^T Y with 4-wide vector loads along the neighbour axis,
+//            and A = (1/N0) W . G;
+//   nu = 1, 2: E12 and dE12/dA (symmetric 8x8 matrix-vector products per (l, m)).
+template <typename R>
+__global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB : 1) k_ace_basis(AceArgs<R> a) {
+  // Shared memory: W [320] | M2 [320] | C1 [8] | per warp: list [kListCap][4] | tile [kRows][kCols]
+  // (A and the G scratch alias the tile once the contraction is done).
   extern __shared__ __align__(128) unsigned char smem_raw[];
   R* Ws = reinterpret_cast<R*>(smem_raw);
   R* M2 = Ws + 320;
@@ -497,10 +327,7 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
   R* list = wbase + warp * (4 * kListCap + kRows * kCols);
   R* tile = list + 4 * kListCap;
   R* A = tile;
-  R* dA = tile + 200;
-  R* U = tile + 400;
   R* Gs = tile + 600;
-  R* A48 = tile + 800;
   for (int t = threadIdx.x; t < 320; t += blockDim.x) {
     Ws[t] = a.W[t];
     M2[t] = a.M2[t];
@@ -521,7 +348,7 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
     const int c = a.cnt[q];
     const size_t row = (size_t)q * a.cap;
 
-    // ---------------- pass 0: compact the row entries inside ace_rc (j and r_ij)
+    // ---------------- pass 0: compact the row entries inside ace_rc
     int nin = 0;
     for (int base = 0; base < c; base += 32) {
       const int slot = base + lane;
@@ -542,6 +369,7 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
         e[1] = d[1];
         e[2] = d[2];
         e[3] = pack_j(j, R(0));
+        a.slots[(size_t)q * kListCap + pos] = (uint16_t)slot;
       }
       nin += __popc(mask);
     }
@@ -549,6 +377,7 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
       if (lane == 0) atomicOr(&a.stats->err, kErrCapacity);
       nin = kListCap;
     }
+    if (lane == 0) a.nin[q] = nin;
     __syncwarp();
 
     // ---------------- stage A: G_klm = sum_j g_k Y_lm over the compacted neighbours
@@ -589,7 +418,6 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
       }
       __syncwarp();
     }
-    // G into the scratch, then A = (1/N0) W . G
 #pragma unroll
     for (int t = 0; t < 7; ++t) {
       const int lm = grp + 4 * t;
@@ -603,46 +431,12 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
 #pragma unroll
       for (int k = 0; k < 8; ++k) s += w[k] * Gs[k * 25 + lm];
       A[o] = s * a.inv_n0;
-      dA[o] = R(0);
     }
     __syncwarp();
+    for (int v = lane; v < 48; v += 32) a.a48[(size_t)q * 48 + v] = A[(v >> 4) * 25 + (v & 15)];
 
-    // ---------------- stage B: E and dE/dA
-    // nu = 3: each lane runs its gradient program over the 48 A entries with
-    // n <= 2, l <= 3 and flushes one register sum per output; E3 follows from
-    // Euler's identity for a homogeneous cubic, E3 = (1/3) sum_a A_a dE3/dA_a.
-    // Then nu = 2 and nu = 1 for the outputs each lane owns.
-    for (int v = lane; v < 48; v += 32) A48[v] = A[(v >> 4) * 25 + (v & 15)];
-    __syncwarp();
-    {
-      R acc = R(0);
-      const uint32_t* pi = a.e3_idx + lane;
-      const R* pc = a.e3_coef + lane;
-      const uint2* pp = a.e3_pack + lane;
-#pragma unroll 4
-      for (int k = 0; k < a.e3_len; ++k) {
-        uint32_t p;
-        R cf;
-        if constexpr (sizeof(R) == 4) {
-          const uint2 v = __ldg(pp + 32 * k);   // index and FP32 coefficient in one load
-          p = v.x;
-          cf = __uint_as_float(v.y);
-        } else {
-          p = __ldg(pi + 32 * k);
-          cf = __ldg(pc + 32 * k);
-        }
-        acc += cf * A48[p & 63u] * A48[(p >> 6) & 63u];
-        if (p & (1u << 24)) {
-          const int o = (int)((p >> 12) & 63u);
-          atomicAdd(&dA[(o >> 4) * 25 + (o & 15)], acc);
-          acc = R(0);
-        }
-      }
-    }
-    __syncwarp();
+    // ---------------- nu = 1, 2: E12 and dE12/dA
     R e = R(0);
-    for (int v = lane; v < 48; v += 32) e += A48[v] * dA[(v >> 4) * 25 + (v & 15)];
-    e *= R(1.0 / 3.0);
     for (int o = lane; o < 200; o += 32) {
       const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
       const R* mrow = &M2[l * 64 + n * 8];
@@ -651,20 +445,86 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
       for (int n2 = 0; n2 < 8; ++n2) s += mrow[n2] * A[n2 * 25 + lm];
       const R lin = lm == 0 ? C1[n] : R(0);
       e += A[o] * (R(0.5) * s + lin);
-      if (FORCES) dA[o] += s + lin;
+      a.dA[(size_t)q * 200 + o] = s + lin;
     }
-    double E = warp_sum<double>((double)e);
+    const double E = warp_sum<double>((double)e);
     if (lane == 0) {
-      a.e_prec[i] = E;
+      a.e12[q] = E;
       atomicAdd(&a.stats->ace_pairs, (unsigned long long)nin);
       atomicAdd(&a.stats->ace_atoms, 1ull);
     }
-    if (!FORCES) {
-      __syncwarp();
-      continue;
-    }
     __syncwarp();
-    // ---------------- stage C: u_klm and forces over the compacted neighbours
+  }
+}
+
+// Kernel 2, one lane per precise atom: nu = 3 energy and gradient with the 48 A
+// entries and their gradient in registers, as straight-line code over the merged
+// monomials (ace_nu3.inc); coefficients are read from the parameter space.  E3
+// follows from Euler's identity for a homogeneous cubic, E3 = (1/3) sum A dE3/dA.
+template <typename R>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 128 : 64) k_ace_nu3(AceArgs<R> a, const Nu3Coef<R> P) {
+  const int m = a.sc->n_precise;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+    R A[48], dA[48];
+    const R* src = a.a48 + (size_t)q * 48;
+#pragma unroll
+    for (int v = 0; v < 48; ++v) {
+      A[v] = src[v];
+      dA[v] = R(0);
+    }
+#define NU3_GROUP_BEGIN(x, y) \
+  {                           \
+    const R p_ = A[x] * A[y]; \
+    R s_ = R(0);
+#define NU3_TERM(t, z)        \
+  s_ = fma(P.c[t], A[z], s_); \
+  dA[z] = fma(P.c[t], p_, dA[z]);
+#define NU3_GROUP_END(x, y)         \
+  dA[x] = fma(s_, A[y], dA[x]);     \
+  dA[y] = fma(s_, A[x], dA[y]);     \
+  }
+    AP_NU3_BODY
+#undef NU3_GROUP_BEGIN
+#undef NU3_TERM
+#undef NU3_GROUP_END
+    R e = R(0);
+    R* dst = a.de3 + (size_t)q * 48;
+#pragma unroll
+    for (int v = 0; v < 48; ++v) {
+      e = fma(A[v], dA[v], e);
+      dst[v] = dA[v];
+    }
+    a.e3[q] = (double)e * (1.0 / 3.0);
+  }
+}
+
+// Kernel 3, one warp per precise atom (persistent): E_i = E12 + E3 -> e_prec, then
+// u_klm = (1/N0) sum_n W[l][n][k] dE/dA_nlm and the forces: lanes recompute g, g',
+// Y, grad Y per in-range neighbour (from the kept row positions), contract with u
+// and scatter -w_i p_ij to neighbour j, +w_i sum_j p_ij to i.
+template <typename R, bool FORCES>
+__global__ void __launch_bounds__(kWarps3<R> * 32) k_ace_adjoint(AceArgs<R> a) {
+  // Shared memory: W [320] | per warp: dA [200] | U [200]
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  R* Ws = reinterpret_cast<R*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  R* dA = Ws + 320 + warp * 400;
+  R* U = dA + 200;
+  for (int t = threadIdx.x; t < 320; t += blockDim.x) Ws[t] = a.W[t];
+  __syncthreads();
+  const int m = a.sc->n_precise;
+  while (true) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(a.counter2, 1);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= m) break;
+    const int i = a.queue[q];
+    if (lane == 0) a.e_prec[i] = a.e12[q] + a.e3[q];
+    if (!FORCES) continue;
+    for (int o = lane; o < 200; o += 32) dA[o] = a.dA[(size_t)q * 200 + o];
+    __syncwarp();
+    for (int v = lane; v < 48; v += 32) dA[(v >> 4) * 25 + (v & 15)] += a.de3[(size_t)q * 48 + v];
+    __syncwarp();
     for (int o = lane; o < 200; o += 32) {
       const int lm = o >> 3, k = o & 7, l = l_of(lm);
       R s = R(0);
@@ -673,16 +533,22 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
       U[o] = s * a.inv_n0;
     }
     __syncwarp();
+    const SysInfo& S = a.sys[a.atom_sys ? a.atom_sys[i] : 0];
+    const auto si = a.sh[i];
+    const size_t row = (size_t)q * a.cap;
+    const int nin = a.nin[q];
     const R wgt = (R)(1.0 - (a.lam ? a.lam[i] : 0.0));
     R pix = R(0), piy = R(0), piz = R(0);
     for (int base = 0; base < nin; base += 32) {
       const int slot = base + lane;
       if (slot >= nin) continue;
-      auto ev = ld4<R>(&list[4 * slot]);
-      const int j = unpack_j(ev.w);
-      R r2 = ev.x * ev.x + ev.y * ev.y + ev.z * ev.z;
+      const int ent = a.slots[(size_t)q * kListCap + slot];
+      const int j = a.nbr[row + ent];
+      R d[3];
+      pair_disp<R>(S, si, a.sh[j], a.off, row + ent, d);
+      R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
       R ir = rsqrt_(r2);
-      R ux = ev.x * ir, uy = ev.y * ir, uz = ev.z * ir;
+      R ux = d[0] * ir, uy = d[1] * ir, uz = d[2] * ir;
       R g[8], dg[8];
       radial<R, true>(r2 * ir, a.inv_rc, a.mode, g, dg);
       R pr = R(0), ptx = R(0), pty = R(0), ptz = R(0);
@@ -721,8 +587,21 @@ __global__ void k_ace_finalize64(int n, const double* __restrict__ acc, double* 
 }
 
 template <typename R>
-size_t ace_smem() {
+size_t basis_smem() {
   return sizeof(R) * (320 + 320 + 8) + sizeof(R) * kWarps<R> * (4 * kListCap + kRows * kCols);
+}
+
+template <typename R>
+size_t adjoint_smem() {
+  return sizeof(R) * (320 + kWarps3<R> * 400);
+}
+
+template <typename K>
+int resident_blocks(K kern, int threads, size_t smem) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem);
+  return b > 0 ? b : 1;
 }
 
 template <typename R>
@@ -732,104 +611,82 @@ void run_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_pre
   a.sc = c->d_sc;
   a.stats = c->d_sc;
   a.counter = &c->d_sc->work_counter;
+  a.counter2 = &c->d_sc->work_counter2;
   a.sys = c->d_sys;
   a.atom_sys = c->d_atom_sys;
-  if constexpr (sizeof(R) == 4)
+  if constexpr (sizeof(R) == 4) {
     a.sh = c->d_sh32;
-  else
+    a.W = c->d_W32;
+    a.facc32 = c->d_facc32;
+    a.facc64 = nullptr;
+  } else {
     a.sh = c->d_sh64;
+    a.W = c->d_W64;
+    a.facc32 = nullptr;
+    a.facc64 = c->d_facc64;
+  }
   a.nbr = c->d_nbr_ace;
   a.off = c->stored_off ? c->d_off_ace : nullptr;
   a.cnt = c->d_cnt_ace;
   a.cap = c->cap_ace;
   a.lam = d_lam;
-  a.term_idx = c->d_term_idx;
-  if constexpr (sizeof(R) == 4) {
-    a.term_coef = c->d_term_coef32;
-    a.W = c->d_W32;
-    a.facc32 = c->d_facc32;
-    a.facc64 = nullptr;
-  } else {
-    a.term_coef = c->d_term_coef64;
-    a.W = c->d_W64;
-    a.facc32 = nullptr;
-    a.facc64 = c->d_facc64;
-  }
   a.M2 = a.W + 320;   // the parameter block is [W (320) | M2 (320) | C1 (8)]
   a.C1 = a.W + 640;
-  a.n_terms = c->ace.n_terms;
-  a.e3_idx = c->d_e3_idx;
-  a.e3_pack = c->d_e3_pack;
-  a.e3_len = c->ace.e3_len;
-  if constexpr (sizeof(R) == 4)
-    a.e3_coef = c->d_e3_coef32;
-  else
-    a.e3_coef = c->d_e3_coef64;
   a.rc2 = (R)(c->cfg.ace_rc * c->cfg.ace_rc);
   a.inv_rc = (R)(1.0 / c->cfg.ace_rc);
   a.inv_n0 = (R)(1.0 / c->cfg.ace_n0);
   a.mode = c->cfg.fcut_mode;
   a.e_prec = d_e_prec;
-  size_t smem = ace_smem<R>();
-  auto kern = forces ? k_ace<R, true> : k_ace<R, false>;
-  static int configured[2][2] = {{0, 0}, {0, 0}};
-  static int blocks_per_sm[2][2] = {{0, 0}, {0, 0}};
-  int pi = sizeof(R) == 4 ? 0 : 1, fi = forces ? 1 : 0;
-  if (!configured[pi][fi]) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kWarps<R> * 32, smem);
-    blocks_per_sm[pi][fi] = b > 0 ? b : 1;
-    configured[pi][fi] = 1;
-  }
+  a.slots = c->d_ace_slots;
+  a.nin = c->d_ace_nin;
+  a.a48 = reinterpret_cast<R*>(c->d_ace_a48);
+  a.dA = reinterpret_cast<R*>(c->d_ace_dA);
+  a.e12 = c->d_ace_e12;
+  a.de3 = reinterpret_cast<R*>(c->d_ace_de3);
+  a.e3 = c->d_ace_e3;
+  static Nu3Coef<R> P;
+  for (int t = 0; t < AP_NU3_N; ++t) P.c[t] = (R)c->ace.nu3_coef[t];
+
+  const int pi = sizeof(R) == 4 ? 0 : 1;
+  static int b1[2] = {0, 0}, b3[2][2] = {{0, 0}, {0, 0}};
+  const size_t s1 = basis_smem<R>(), s3 = adjoint_smem<R>();
+  if (!b1[pi]) b1[pi] = resident_blocks(k_ace_basis<R>, kWarps<R> * 32, s1);
+  auto k3 = forces ? k_ace_adjoint<R, true> : k_ace_adjoint<R, false>;
+  if (!b3[pi][forces]) b3[pi][forces] = resident_blocks(k3, kWarps3<R> * 32, s3);
   if (forces) {
     if constexpr (sizeof(R) == 4)
       cudaMemsetAsync(c->d_facc32, 0, sizeof(float4) * (size_t)c->n, s);
     else
       cudaMemsetAsync(c->d_facc64, 0, sizeof(double) * 3 * (size_t)c->n, s);
   }
-  cudaMemsetAsync(a.counter, 0, sizeof(int), s);
-  int grid = c->num_sms * blocks_per_sm[pi][fi];
-  kern<<<grid, kWarps<R> * 32, smem, s>>>(a);
-  c->kernels += 1;
+  cudaMemsetAsync(a.counter, 0, 2 * sizeof(int), s);   // work_counter and work_counter2
+  k_ace_basis<R><<<c->num_sms * b1[pi], kWarps<R> * 32, s1, s>>>(a);
+  const int t2 = sizeof(R) == 4 ? 128 : 64;
+  k_ace_nu3<R><<<c->num_sms * (sizeof(R) == 4 ? 8 : 16), t2, 0, s>>>(a, P);
+  k3<<<c->num_sms * b3[pi][forces], kWarps3<R> * 32, s3, s>>>(a);
+  c->kernels += 3;
 }
 
 }  // namespace
 
+// The compiled nu = 3 code must match the host enumeration of the basis.
+bool ace_nu3_matches(const AceTables& t) {
+  if (t.nu3_key.size() != (size_t)AP_NU3_N) return false;
+  for (int k = 0; k < AP_NU3_N; ++k)
+    if (t.nu3_key[k] != kNu3Key[k]) return false;
+  return true;
+}
+
 void upload_ace_tables(ap_ctx* c) {
   const AceTables& t = c->ace;
-  std::vector<float> cf32(t.term_coef.begin(), t.term_coef.end());
   std::vector<double> p64(c->cfg.ace_W, c->cfg.ace_W + 320);
   p64.insert(p64.end(), t.m2.begin(), t.m2.end());
   p64.insert(p64.end(), t.c1.begin(), t.c1.end());
   std::vector<float> p32(p64.begin(), p64.end());
-  cudaMalloc(&c->d_term_idx, sizeof(int) * t.n_terms);
-  cudaMalloc(&c->d_term_coef32, sizeof(float) * t.n_terms);
-  cudaMalloc(&c->d_term_coef64, sizeof(double) * t.n_terms);
   cudaMalloc(&c->d_W32, sizeof(float) * p32.size());
   cudaMalloc(&c->d_W64, sizeof(double) * p64.size());
-  cudaMemcpy(c->d_term_idx, t.term_idx.data(), sizeof(int) * t.n_terms, cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_term_coef32, cf32.data(), sizeof(float) * t.n_terms, cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_term_coef64, t.term_coef.data(), sizeof(double) * t.n_terms, cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_W32, p32.data(), sizeof(float) * p32.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_W64, p64.data(), sizeof(double) * p64.size(), cudaMemcpyHostToDevice);
-  const size_t ne = t.e3_idx.size();
-  std::vector<float> e32(t.e3_coef.begin(), t.e3_coef.end());
-  cudaMalloc(&c->d_e3_idx, sizeof(uint32_t) * ne);
-  cudaMalloc(&c->d_e3_coef32, sizeof(float) * ne);
-  cudaMalloc(&c->d_e3_coef64, sizeof(double) * ne);
-  cudaMemcpy(c->d_e3_idx, t.e3_idx.data(), sizeof(uint32_t) * ne, cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_e3_coef32, e32.data(), sizeof(float) * ne, cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_e3_coef64, t.e3_coef.data(), sizeof(double) * ne, cudaMemcpyHostToDevice);
-  std::vector<uint2> pack(ne);
-  for (size_t k = 0; k < ne; ++k) {
-    float cf = (float)t.e3_coef[k];
-    uint32_t bits;
-    std::memcpy(&bits, &cf, sizeof(bits));
-    pack[k] = make_uint2(t.e3_idx[k], bits);
-  }
-  cudaMalloc(&c->d_e3_pack, sizeof(uint2) * ne);
-  cudaMemcpy(c->d_e3_pack, pack.data(), sizeof(uint2) * ne, cudaMemcpyHostToDevice);
 }
 
 void launch_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_prec, bool forces, cudaStream_t s) {

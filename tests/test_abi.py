@@ -86,3 +86,16 @@ def test_null_context_calls_fail_cleanly():
     assert lib.ap_classify(None, 0, None, None, None, None, None, None) == 1
     assert lib.ap_step(None, 0, None, None, None, None, None, None, 0, None, None) == 1
     assert lib.ap_last_error(None) == b"null context"
+
+
+def test_generated_nu3_code_matches_the_basis(tmp_path):
+    """ace_nu3.inc (the straight-line nu = 3 code) is the generator's output for
+    the basis enumeration compiled into the library."""
+    csrc = os.path.join(ROOT, "paper_2411_03002_gb300", "csrc")
+    exe = tmp_path / "gen_nu3"
+    nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    subprocess.run([nvcc, "-std=c++17", "-I", os.path.join(ROOT, "include"), os.path.join(csrc, "gen_nu3.cpp"),
+                    os.path.join(csrc, "ace_tables.cpp"), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    with open(os.path.join(csrc, "ace_nu3.inc")) as fh:
+        assert fh.read() == out
