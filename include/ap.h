@@ -45,7 +45,7 @@ typedef int32_t ap_status;
 #define AP_ERR_NONFINITE 4  /* NaN/Inf found in positions or forces                    */
 #define AP_ERR_TIMEOUT 5    /* a bounded device wait gave up (the kernel returned early) */
 #define AP_ERR_STATE 6      /* call order violated (e.g. evaluation before neighbours) */
-#define AP_ERR_RADICAND 7   /* reserved: negative radicand in the local thermostat     */
+#define AP_ERR_RADICAND 7   /* a local-thermostat correction had a negative radicand   */
 #define AP_ERR_BOX 8        /* an atom lies outside a non-periodic box dimension       */
 #define AP_ERR_SKIN 9       /* an atom moved more than skin/2 between list rebuilds    */
 
@@ -114,6 +114,22 @@ typedef struct {
    * model (ap_sel_set_model).  Ignored with AP_DETECT_CSP. */
   int32_t detector;
   double sel_p_lo, sel_p_hi;
+  /* Local thermostat (section 2.3 and Appendix C), used by ap_step on every lambda
+   * update when 1.  With lambda^c the values before the update and lambda^d after
+   * it, each mobile atom's energy error
+   *   Delta E_i = Delta T_i + Delta V_i,
+   *   Delta V_i = (lambda_i^c - lambda_i^d)(E_i^f - E_i^p)                  (Eq. Delta_V_i)
+   *   Delta T_i = sum_a [dt^2/(8 m_i)(F^c_ia^2 - F^d_ia^2) + (F^c_ia - F^d_ia) v_ia(t+dt/2) dt/2]
+   * (interatomic forces only) is corrected at the end of the step by rescaling the
+   * relative momenta of Omega_i = {i} + the distinct mobile atoms of its EAM row:
+   * v_j <- v_cm + beta (v_j - v_cm), beta = sqrt(Delta E_i / K_rel + 1) (Eqs.
+   * p_resc_omega, beta_omega_i).  Rows hold at most cap_eam atoms, below the
+   * paper's 800, so no random draw is made.  Corrections run in an 8-colour sweep
+   * over cells of edge >= 2 (eam_rc + 2 skin) (ascending index inside a cell),
+   * the sub-domain order the paper leaves open; groups in cells of one colour are
+   * disjoint.  A negative radicand skips that correction and makes ap_step return
+   * AP_ERR_RADICAND.  One system only (not with ap_build_neighbors_batch). */
+  int32_t thermostat_on;
 } ap_config;
 
 typedef struct ap_ctx ap_ctx;
@@ -128,6 +144,9 @@ typedef struct {
   double e_kin;              /* sum_i m v^2 / 2, FP64 */
   double max_disp;           /* largest displacement since the last rebuild (A) */
   int32_t error_bits;        /* OR of 1 << AP_ERR_* seen on the device */
+  int64_t th_corrected;      /* local-thermostat corrections applied so far */
+  int64_t th_refused;        /* corrections refused for a negative radicand so far */
+  double th_energy;          /* sum of the corrected Delta E so far (eV) */
 } ap_step_stats;
 
 /* ----------------------------------------------------------------- lifetime */
@@ -342,7 +361,8 @@ ap_status ap_eval_eam_static(const ap_config* h_cfg, int64_t n, const double* d_
 #define AP_PHASE_EAM 2         /* EAM density + force kernels                      */
 #define AP_PHASE_ACE 3         /* fused ACE energy/adjoint/force kernel           */
 #define AP_PHASE_OTHER 4       /* integrator, finalize, indenter, reductions      */
-#define AP_NUM_PHASES 5
+#define AP_PHASE_THERMOSTAT 5  /* local thermostat: difference forces, Delta E, corrections */
+#define AP_NUM_PHASES 6
 
 /* Turn per-phase event timing in ap_step on (1) or off (0) and clear the totals.
  * No paper counterpart: instrumentation of this implementation. */

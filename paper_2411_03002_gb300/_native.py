@@ -34,12 +34,14 @@ class ApConfig(ctypes.Structure):
                    ("n_csp_avg", I32), ("n_lam_avg", I32), ("fcut_mode", I32), ("skin", F64), ("cap_eam", I32),
                    ("cap_ace", I32), ("precision", I32), ("dt", F64), ("lambda_every", I32), ("indenter_on", I32),
                    ("ind_c0", F64 * 3), ("ind_v", F64 * 3), ("ind_R", F64), ("ind_k", F64),
-                   ("rebuild_every", I32), ("detector", I32), ("sel_p_lo", F64), ("sel_p_hi", F64)])
+                   ("rebuild_every", I32), ("detector", I32), ("sel_p_lo", F64), ("sel_p_hi", F64),
+                   ("thermostat_on", I32)])
 
 
 class ApStepStats(ctypes.Structure):
     _fields_ = [("step", I64), ("n_precise", I64), ("n_detected", I64), ("rebuilds", I64), ("e_pot", F64),
-                ("e_kin", F64), ("max_disp", F64), ("error_bits", I32)]
+                ("e_kin", F64), ("max_disp", F64), ("error_bits", I32), ("th_corrected", I64), ("th_refused", I64),
+                ("th_energy", F64)]
 
 
 class ApError(RuntimeError):

@@ -42,7 +42,7 @@ def make_box(lo, hi, periodic) -> ApBox:
 def make_config(eam, ace, hyb, precision: int = N.PREC_MIXED, skin: float = 1.0, dt: float = 1.0,
                 indenter=None, cap_eam: int = 0, cap_ace: int = 0, lambda_every: Optional[int] = None,
                 rebuild_every: int = 0, detector: int = N.DETECT_CSP, sel_p_lo: float = 0.5,
-                sel_p_hi: float = 0.9) -> ApConfig:
+                sel_p_hi: float = 0.9, thermostat: bool = False) -> ApConfig:
     """Fill an ap_config from parameter objects with the attribute names of
     the EAM (beta, alpha, A, D, rp, r0, rc, h), ACE (W, c, rc, n0) and switching
     (csp_lo, csp_hi, r_lo, r_hi, dlam_min, n_csp_avg, n_lam_avg, fcut_mode,
@@ -75,6 +75,7 @@ def make_config(eam, ace, hyb, precision: int = N.PREC_MIXED, skin: float = 1.0,
     c.rebuild_every = int(rebuild_every)
     c.detector = int(detector)
     c.sel_p_lo, c.sel_p_hi = float(sel_p_lo), float(sel_p_hi)
+    c.thermostat_on = 1 if thermostat else 0
     if indenter is not None:
         c.indenter_on = 1
         for k in range(3):
@@ -117,6 +118,9 @@ class StepStats:
     e_kin: float
     max_disp: float
     error_bits: int
+    th_corrected: int = 0
+    th_refused: int = 0
+    th_energy: float = 0.0
 
 
 class Context:
@@ -243,16 +247,16 @@ class Context:
         self._ck(self.lib.ap_step(self.h, n, _ptr(x), _ptr(v), _ptr(f), _ptr(mass), _ptr(fixed), _ptr(lam),
                                   int(nsteps), ctypes.byref(st), _stream(stream)))
         return StepStats(st.step, st.n_precise, st.n_detected, st.rebuilds, st.e_pot, st.e_kin, st.max_disp,
-                         st.error_bits)
+                         st.error_bits, st.th_corrected, st.th_refused, st.th_energy)
 
-    PHASES = ("neighbors", "classify", "eam", "ace", "other")
+    PHASES = ("neighbors", "classify", "eam", "ace", "other", "thermostat")
 
     def profile_enable(self, on: bool = True):
         self._ck(self.lib.ap_profile_enable(self.h, 1 if on else 0))
 
     def profile_read(self):
-        ms = (ctypes.c_double * 5)()
-        calls = (ctypes.c_int64 * 5)()
+        ms = (ctypes.c_double * len(self.PHASES))()
+        calls = (ctypes.c_int64 * len(self.PHASES))()
         kern, pairs, atoms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         self._ck(self.lib.ap_profile_read(self.h, ms, calls, ctypes.byref(kern), ctypes.byref(pairs),
                                           ctypes.byref(atoms)))

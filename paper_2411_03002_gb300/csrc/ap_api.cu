@@ -58,6 +58,7 @@ ap_status validate(const ap_config& g, std::string& why) {
   if (g.detector != AP_DETECT_CSP && g.detector != AP_DETECT_SELECTOR) return bad("unknown detector");
   if (g.detector == AP_DETECT_SELECTOR && !(g.sel_p_lo >= 0 && g.sel_p_hi > g.sel_p_lo))
     return bad("need 0 <= sel_p_lo < sel_p_hi");
+  if (g.thermostat_on != 0 && g.thermostat_on != 1) return bad("thermostat_on must be 0 or 1");
   return AP_OK;
 }
 
@@ -226,6 +227,7 @@ ap_status check_err_bits(ap_ctx* c) {
   }
   if (e & kErrSkin) return fail(c, AP_ERR_SKIN, "an atom moved more than skin/2 between rebuilds");
   if (e & kErrTimeout) return fail(c, AP_ERR_TIMEOUT, "a bounded tensor-core wait gave up");
+  if (e & kErrRadicand) return fail(c, AP_ERR_RADICAND, "a local-thermostat correction had a negative radicand");
   return AP_OK;
 }
 
@@ -401,6 +403,63 @@ ap_status ensure_sel_feat(ap_ctx* c, int64_t n) {
   return AP_OK;
 }
 
+// Local-thermostat scratch for n atoms and the sweep cells of the current box.
+ap_status ensure_th(ap_ctx* c) {
+  const int64_t n = c->n;
+  if (n > c->th_cap || !c->d_th_lamc) {
+    CK(dalloc(c->d_th_lamc, n));
+    CK(dalloc(c->d_th_dlam, n));
+    CK(dalloc(c->d_th_w, n));
+    CK(dalloc(c->d_th_df, 3 * n));
+    CK(dalloc(c->d_th_ep, n));
+    CK(dalloc(c->d_th_de, n));
+    CK(dalloc(c->d_th_qk, n));
+    CK(dalloc(c->d_th_qe, n));
+    CK(dalloc(c->d_th_cellof, n));
+    CK(dalloc(c->d_th_atoms, n));
+    c->th_cap = n;
+  }
+  const int64_t nc = th_cell_count(c);
+  if (nc + 1 > c->th_cells_cap) {
+    CK(dalloc(c->d_th_ccount, nc + 1));
+    CK(dalloc(c->d_th_cstart, nc + 2));
+    c->th_cells_cap = nc + 1;
+  }
+  size_t need_tmp = scan_tmp_bytes(std::max<int64_t>(nc + 1, n + 1)) / sizeof(int) + 1;
+  if (need_tmp > c->scan_tmp_cap) {
+    c->scan_tmp_cap = need_tmp;
+    CK(dalloc(c->d_scan_tmp, need_tmp));
+  }
+  return AP_OK;
+}
+
+// F^c - F^d of a lambda update (linear in Delta lambda = lambda^c - lambda^d): the ACE
+// part over K = {Delta lambda != 0} with weights -Delta lambda (which also gives E^p
+// of K for Delta V), then the EAM part with weights Delta lambda.  Runs before the
+// ACE rows of the new precise queue are built.
+void th_difference(ap_ctx* c, const double* d_x, cudaStream_t s) {
+  const int n = (int)c->n;
+  launch_th_delta(c, c->d_th_lamc, c->d_lam_int, s);
+  c->kernels += scan_exclusive(c->d_flag, c->d_scan, n, c->d_scan_tmp, s) + 1;
+  k_compact_q<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_flag, c->d_scan, c->d_th_qk, &c->d_sc->n_th_k);
+  cudaMemsetAsync(c->d_th_df, 0, sizeof(double) * 3 * (size_t)n, s);
+  cudaMemsetAsync(c->d_th_ep, 0, sizeof(double) * (size_t)n, s);
+  launch_build_ace(c, d_x, c->d_th_qk, &c->d_sc->n_th_k, s);
+  launch_ace(c, nullptr, c->d_th_qk, c->d_th_ep, true, s, c->d_th_w, &c->d_sc->n_th_k);
+  launch_ace_finalize(c, c->d_th_df, s);
+  launch_eam(c, c->d_th_dlam, nullptr, c->d_th_df, true, s);
+}
+
+// Delta E of every mobile atom from F^d (interatomic forces only) and the queue of
+// atoms with Delta E != 0.
+void th_energy(ap_ctx* c, const double* d_f, const double* d_v, const double* d_mass, const uint8_t* d_fixed,
+               cudaStream_t s) {
+  const int n = (int)c->n;
+  launch_th_energy(c, d_f, d_v, d_mass, d_fixed, s);
+  c->kernels += scan_exclusive(c->d_flag, c->d_scan, n, c->d_scan_tmp, s) + 1;
+  k_compact_q<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_flag, c->d_scan, c->d_th_qe, &c->d_sc->n_th_e);
+}
+
 // What the configured detector needs before a classification.
 ap_status prep_detector(ap_ctx* c) {
   if (c->cfg.detector != AP_DETECT_SELECTOR) return AP_OK;
@@ -476,7 +535,9 @@ void ap_destroy(ap_ctx* c) {
                   c->d_eatom, c->d_eext, c->d_changeable, c->d_W32, c->d_W64, c->d_ace_slots, c->d_ace_nin,
                   c->d_ace_a48, c->d_ace_dA, c->d_ace_e12, c->d_ace_de3, c->d_ace_e3, c->d_scan_tmp, c->d_red,
                   c->d_sel_model, c->d_sel_master, c->d_sel_m1, c->d_sel_m2, c->d_sel_grad, c->d_sel_partial,
-                  c->d_sel_rho, c->d_sel_feat, c->d_sel_score, c->d_sel_z, c->d_sel_h1, c->d_sel_h2, c->d_sc};
+                  c->d_sel_rho, c->d_sel_feat, c->d_sel_score, c->d_sel_z, c->d_sel_h1, c->d_sel_h2,
+                  c->d_th_lamc, c->d_th_dlam, c->d_th_w, c->d_th_df, c->d_th_ep, c->d_th_de, c->d_th_qk, c->d_th_qe,
+                  c->d_th_cellof, c->d_th_atoms, c->d_th_ccount, c->d_th_cstart, c->d_sc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_sc) cudaFreeHost(c->h_sc);
@@ -689,6 +750,12 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
   const ap_config& g = c->cfg;
   ap_status st = prep_detector(c);
   if (st) return st;
+  const bool thermo = g.thermostat_on != 0;
+  if (thermo) {
+    if (c->n_sys != 1) return fail(c, AP_ERR_ARG, "the local thermostat needs a single system");
+    st = ensure_th(c);
+    if (st) return st;
+  }
   if (!c->md_ready) {
     launch_wrap_positions(c, d_x, s);
     st = build_checked(c, d_x, nullptr, s);
@@ -730,7 +797,18 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
       }
       {
         PhaseTimer t(c, s, AP_PHASE_CLASSIFY);
-        if (lam_step) classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s);
+        if (lam_step) {
+          if (thermo)
+            CK(cudaMemcpyAsync(c->d_th_lamc, c->d_lam_int, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+          classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s);
+        }
+      }
+      if (lam_step && thermo) {
+        PhaseTimer t(c, s, AP_PHASE_THERMOSTAT);
+        th_difference(c, d_x, s);
+      }
+      {
+        PhaseTimer t(c, s, AP_PHASE_CLASSIFY);
         launch_build_ace(c, d_x, c->d_precise, &c->d_sc->n_precise, s);
       }
     } else {
@@ -749,8 +827,19 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
     {
       PhaseTimer t(c, s, AP_PHASE_OTHER);
       launch_ace_finalize(c, d_f, s);
+    }
+    if (lam_step && thermo) {   // Delta E from the interatomic forces, before the external force
+      PhaseTimer t(c, s, AP_PHASE_THERMOSTAT);
+      th_energy(c, d_f, d_v, d_mass, d_fixed, s);
+    }
+    {
+      PhaseTimer t(c, s, AP_PHASE_OTHER);
       if (g.indenter_on) launch_indenter(c, d_x, d_f, c->step * g.dt, s);
       launch_vv_second(c, d_v, d_f, d_mass, d_fixed, s);
+    }
+    if (lam_step && thermo) {   // corrections of v(t + dt)
+      PhaseTimer t(c, s, AP_PHASE_THERMOSTAT);
+      launch_th_correct(c, c->d_th_qe, &c->d_sc->n_th_e, d_x, d_fixed, d_mass, d_v, s);
     }
   }
   {
@@ -777,6 +866,9 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
     std::memcpy(&d2, &c->h_sc->max_disp2_bits, sizeof(float));
     h_stats->max_disp = std::sqrt((double)d2);
     h_stats->error_bits = c->h_sc->err;
+    h_stats->th_corrected = (int64_t)c->h_sc->th_n;
+    h_stats->th_refused = (int64_t)c->h_sc->th_bad;
+    h_stats->th_energy = c->h_sc->th_e;
   }
   return check_err_bits(c);
 }

@@ -58,6 +58,7 @@ enum : int {
   kErrSkin = 1 << AP_ERR_SKIN,
   kErrArg = 1 << AP_ERR_ARG,
   kErrTimeout = 1 << AP_ERR_TIMEOUT,
+  kErrRadicand = 1 << AP_ERR_RADICAND,
 };
 
 // ------------------------------------------------------------------ device buffers
@@ -83,6 +84,11 @@ struct DevScalars {
   double e_ind;
   unsigned long long ace_pairs;   // neighbour pairs within the ACE cutoff processed (cumulative)
   unsigned long long ace_atoms;   // precise atoms processed by the ACE kernel (cumulative)
+  int n_th_k;                     // local thermostat: |{Delta lambda != 0}| of the last update
+  int n_th_e;                     // local thermostat: |{Delta E != 0}| of the last update
+  unsigned long long th_n;        // corrections applied (cumulative)
+  unsigned long long th_bad;      // corrections refused for a negative radicand (cumulative)
+  double th_e;                    // sum of the corrected Delta E (cumulative, eV)
 };
 
 // ------------------------------------------------------------------ ACE tables
@@ -233,6 +239,21 @@ struct ap_ctx {
   bool sel_ready = false;
   int64_t sel_t = 0;               // Adam steps taken
 
+  // local thermostat scratch (allocated when thermostat_on)
+  double* d_th_lamc = nullptr;   // [n] lambda^c (the values before the update)
+  double* d_th_dlam = nullptr;   // [n] Delta lambda = lambda^c - lambda^d
+  double* d_th_w = nullptr;      // [n] ACE weights of the difference force (-Delta lambda)
+  double* d_th_df = nullptr;     // [n][3] F^c - F^d
+  double* d_th_ep = nullptr;     // [n] E^p of the atoms with Delta lambda != 0
+  double* d_th_de = nullptr;     // [n] Delta E
+  int* d_th_qk = nullptr;        // [n] atoms with Delta lambda != 0
+  int* d_th_qe = nullptr;        // [n] atoms with Delta E != 0
+  int* d_th_cellof = nullptr;    // [n]
+  int* d_th_atoms = nullptr;     // [n]
+  int* d_th_ccount = nullptr;    // [cells]
+  int* d_th_cstart = nullptr;    // [cells + 1]
+  int64_t th_cap = 0, th_cells_cap = 0;
+
   ap::DevScalars* d_sc = nullptr;
   ap::DevScalars* h_sc = nullptr;  // pinned mirror
 
@@ -280,7 +301,10 @@ void launch_eam(ap_ctx* c, const double* d_lam, double* d_e_fast, double* d_f, b
 // k_ace.cu
 void upload_ace_tables(ap_ctx* c);
 bool ace_nu3_matches(const AceTables& t);
-void launch_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_prec, bool forces, cudaStream_t s);
+// d_wgt: explicit ACE weights w_i (NULL: w_i = 1 - lambda_i); d_count: device queue
+// length (NULL: the context's precise count).
+void launch_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_prec, bool forces, cudaStream_t s,
+                const double* d_wgt = nullptr, const int* d_count = nullptr);
 void launch_ace_finalize(ap_ctx* c, double* d_f, cudaStream_t s);
 
 // k_selector.cu
@@ -294,6 +318,14 @@ void launch_sel_backward(ap_ctx* c, int64_t b, const float* d_feat, const int* d
 void launch_sel_adam(ap_ctx* c, bool update, float lr, float beta1, float beta2, float eps, float inv_bc1,
                      float inv_bc2, cudaStream_t s);
 size_t sel_partial_floats(ap_ctx* c);
+
+// k_thermostat.cu
+int th_cell_count(const ap_ctx* c);
+void launch_th_delta(ap_ctx* c, const double* d_lam_c, const double* d_lam_d, cudaStream_t s);
+void launch_th_energy(ap_ctx* c, const double* d_f, const double* d_v, const double* d_mass, const uint8_t* d_fixed,
+                      cudaStream_t s);
+void launch_th_correct(ap_ctx* c, const int* d_q, const int* d_m, const double* d_x, const uint8_t* d_fixed,
+                       const double* d_mass, double* d_v, cudaStream_t s);
 
 // k_md.cu
 void launch_vv_first(ap_ctx* c, double* d_x, double* d_v, const double* d_f, const double* d_mass,

@@ -228,25 +228,46 @@ __device__ inline void add_force(float4* facc32, double* facc64, int j, R sx, R 
   }
 }
 
+// Block l of the force contraction for one neighbour: with S_m = sum_k u_k,lm g_k and
+// S'_m = sum_k u_k,lm g'_k, accumulates pr += sum_m S'_m Z_m and the tangential part
+// sum_m S_m (grad Z_m - l Z_m u) as (ptx, pty, ptz) += sum_m S_m grad Z_m and
+// pz_l += l sum_m S_m Z_m (the caller subtracts pz_l u once).
 template <typename R, int L>
 __device__ inline void force_block(const R* __restrict__ U, R ux, R uy, R uz, const R g[8], const R dg[8], R& pr,
-                                   R& ptx, R& pty, R& ptz) {
+                                   R& ptx, R& pty, R& ptz, R& pzl) {
   R Y[2 * L + 1], gx[2 * L + 1], gy[2 * L + 1], gz[2 * L + 1];
   sh_block<R, L>(ux, uy, uz, Y, gx, gy, gz);
+  R q = R(0);
 #pragma unroll
   for (int m = 0; m < 2 * L + 1; ++m) {
     const int lm = L * L + m;
     auto ua = ld4<R>(&U[lm * 8]);
     auto ub = ld4<R>(&U[lm * 8 + 4]);
-    R S = (ua.x * g[0] + ua.y * g[1]) + (ua.z * g[2] + ua.w * g[3]) + ((ub.x * g[4] + ub.y * g[5]) + (ub.z * g[6] + ub.w * g[7]));
-    R Sp = (ua.x * dg[0] + ua.y * dg[1]) + (ua.z * dg[2] + ua.w * dg[3]) +
-           ((ub.x * dg[4] + ub.y * dg[5]) + (ub.z * dg[6] + ub.w * dg[7]));
-    pr += Sp * Y[m];
-    R lz = R(L) * Y[m];
-    ptx += S * (gx[m] - lz * ux);
-    pty += S * (gy[m] - lz * uy);
-    ptz += S * (gz[m] - lz * uz);
+    R S = ua.x * g[0];
+    S = fma(ua.y, g[1], S);
+    S = fma(ua.z, g[2], S);
+    S = fma(ua.w, g[3], S);
+    S = fma(ub.x, g[4], S);
+    S = fma(ub.y, g[5], S);
+    S = fma(ub.z, g[6], S);
+    S = fma(ub.w, g[7], S);
+    R Sp = ua.x * dg[0];
+    Sp = fma(ua.y, dg[1], Sp);
+    Sp = fma(ua.z, dg[2], Sp);
+    Sp = fma(ua.w, dg[3], Sp);
+    Sp = fma(ub.x, dg[4], Sp);
+    Sp = fma(ub.y, dg[5], Sp);
+    Sp = fma(ub.z, dg[6], Sp);
+    Sp = fma(ub.w, dg[7], Sp);
+    pr = fma(Sp, Y[m], pr);
+    if (L > 0) {
+      q = fma(S, Y[m], q);
+      ptx = fma(S, gx[m], ptx);
+      pty = fma(S, gy[m], pty);
+      ptz = fma(S, gz[m], ptz);
+    }
   }
+  if (L > 0) pzl = fma(R(L), q, pzl);
 }
 
 template <typename T>
@@ -262,8 +283,14 @@ __device__ inline int unpack_j(float v) { return __float_as_int(v); }
 __device__ inline int unpack_j(double v) { return (int)__double_as_longlong(v); }
 
 constexpr int kListCap = 192;   // neighbours inside ace_rc kept per precise atom (FCC bulk: 134)
+#ifndef AP_ACE3_WARPS
+#define AP_ACE3_WARPS 6
+#endif
+#ifndef AP_ACE3_MINB
+#define AP_ACE3_MINB 4
+#endif
 template <typename R>
-constexpr int kWarps3 = sizeof(R) == 4 ? 8 : 4;   // warps per CTA of the adjoint kernel
+constexpr int kWarps3 = sizeof(R) == 4 ? AP_ACE3_WARPS : 4;   // warps per CTA of the adjoint kernel
 
 #include "ace_nu3.inc"
 
@@ -272,7 +299,7 @@ constexpr int kWarps3 = sizeof(R) == 4 ? 8 : 4;   // warps per CTA of the adjoin
 template <typename R>
 struct AceArgs {
   const int* queue;
-  const DevScalars* sc;
+  const int* count;        // queue length (device)
   DevScalars* stats;
   int* counter;
   int* counter2;
@@ -284,6 +311,7 @@ struct AceArgs {
   const int* cnt;
   int cap;
   const double* lam;
+  const double* wgt;       // explicit weights w_i (NULL: w_i = 1 - lambda_i)
   const R* W;
   const R* M2;
   const R* C1;
@@ -334,7 +362,7 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
   }
   if (threadIdx.x < 8) C1[threadIdx.x] = a.C1[threadIdx.x];
   __syncthreads();
-  const int m = a.sc->n_precise;
+  const int m = *a.count;
   const int kq = lane & 7, grp = lane >> 3;
   const unsigned lt_mask = (1u << lane) - 1u;
   while (true) {
@@ -463,7 +491,7 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
 // follows from Euler's identity for a homogeneous cubic, E3 = (1/3) sum A dE3/dA.
 template <typename R>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 128 : 64) k_ace_nu3(AceArgs<R> a, const Nu3Coef<R> P) {
-  const int m = a.sc->n_precise;
+  const int m = *a.count;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
     R A[48], dA[48];
     const R* src = a.a48 + (size_t)q * 48;
@@ -503,7 +531,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 128 : 64) k_ace_nu3(AceArgs<R
 // Y, grad Y per in-range neighbour (from the kept row positions), contract with u
 // and scatter -w_i p_ij to neighbour j, +w_i sum_j p_ij to i.
 template <typename R, bool FORCES>
-__global__ void __launch_bounds__(kWarps3<R> * 32) k_ace_adjoint(AceArgs<R> a) {
+__global__ void __launch_bounds__(kWarps3<R> * 32, sizeof(R) == 4 ? AP_ACE3_MINB : 1) k_ace_adjoint(AceArgs<R> a) {
   // Shared memory: W [320] | per warp: dA [200] | U [200]
   extern __shared__ __align__(128) unsigned char smem_raw[];
   R* Ws = reinterpret_cast<R*>(smem_raw);
@@ -512,7 +540,7 @@ __global__ void __launch_bounds__(kWarps3<R> * 32) k_ace_adjoint(AceArgs<R> a) {
   R* U = dA + 200;
   for (int t = threadIdx.x; t < 320; t += blockDim.x) Ws[t] = a.W[t];
   __syncthreads();
-  const int m = a.sc->n_precise;
+  const int m = *a.count;
   while (true) {
     int q = 0;
     if (lane == 0) q = atomicAdd(a.counter2, 1);
@@ -537,7 +565,7 @@ __global__ void __launch_bounds__(kWarps3<R> * 32) k_ace_adjoint(AceArgs<R> a) {
     const auto si = a.sh[i];
     const size_t row = (size_t)q * a.cap;
     const int nin = a.nin[q];
-    const R wgt = (R)(1.0 - (a.lam ? a.lam[i] : 0.0));
+    const R wgt = (R)(a.wgt ? a.wgt[i] : 1.0 - (a.lam ? a.lam[i] : 0.0));
     R pix = R(0), piy = R(0), piz = R(0);
     for (int base = 0; base < nin; base += 32) {
       const int slot = base + lane;
@@ -551,12 +579,15 @@ __global__ void __launch_bounds__(kWarps3<R> * 32) k_ace_adjoint(AceArgs<R> a) {
       R ux = d[0] * ir, uy = d[1] * ir, uz = d[2] * ir;
       R g[8], dg[8];
       radial<R, true>(r2 * ir, a.inv_rc, a.mode, g, dg);
-      R pr = R(0), ptx = R(0), pty = R(0), ptz = R(0);
-      force_block<R, 0>(U, ux, uy, uz, g, dg, pr, ptx, pty, ptz);
-      force_block<R, 1>(U, ux, uy, uz, g, dg, pr, ptx, pty, ptz);
-      force_block<R, 2>(U, ux, uy, uz, g, dg, pr, ptx, pty, ptz);
-      force_block<R, 3>(U, ux, uy, uz, g, dg, pr, ptx, pty, ptz);
-      force_block<R, 4>(U, ux, uy, uz, g, dg, pr, ptx, pty, ptz);
+      R pr = R(0), ptx = R(0), pty = R(0), ptz = R(0), pzl = R(0);
+      force_block<R, 0>(U, ux, uy, uz, g, dg, pr, ptx, pty, ptz, pzl);
+      force_block<R, 1>(U, ux, uy, uz, g, dg, pr, ptx, pty, ptz, pzl);
+      force_block<R, 2>(U, ux, uy, uz, g, dg, pr, ptx, pty, ptz, pzl);
+      force_block<R, 3>(U, ux, uy, uz, g, dg, pr, ptx, pty, ptz, pzl);
+      force_block<R, 4>(U, ux, uy, uz, g, dg, pr, ptx, pty, ptz, pzl);
+      ptx = fma(-pzl, ux, ptx);
+      pty = fma(-pzl, uy, pty);
+      ptz = fma(-pzl, uz, ptz);
       R px = pr * ux + ptx * ir, py = pr * uy + pty * ir, pz = pr * uz + ptz * ir;
       pix += px;
       piy += py;
@@ -605,10 +636,11 @@ int resident_blocks(K kern, int threads, size_t smem) {
 }
 
 template <typename R>
-void run_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_prec, bool forces, cudaStream_t s) {
+void run_ace(ap_ctx* c, const double* d_lam, const double* d_wgt, const int* d_queue, const int* d_count,
+             double* d_e_prec, bool forces, cudaStream_t s) {
   AceArgs<R> a;
   a.queue = d_queue;
-  a.sc = c->d_sc;
+  a.count = d_count ? d_count : &c->d_sc->n_precise;
   a.stats = c->d_sc;
   a.counter = &c->d_sc->work_counter;
   a.counter2 = &c->d_sc->work_counter2;
@@ -630,6 +662,7 @@ void run_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_pre
   a.cnt = c->d_cnt_ace;
   a.cap = c->cap_ace;
   a.lam = d_lam;
+  a.wgt = d_wgt;
   a.M2 = a.W + 320;   // the parameter block is [W (320) | M2 (320) | C1 (8)]
   a.C1 = a.W + 640;
   a.rc2 = (R)(c->cfg.ace_rc * c->cfg.ace_rc);
@@ -689,11 +722,12 @@ void upload_ace_tables(ap_ctx* c) {
   cudaMemcpy(c->d_W64, p64.data(), sizeof(double) * p64.size(), cudaMemcpyHostToDevice);
 }
 
-void launch_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_prec, bool forces, cudaStream_t s) {
+void launch_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_prec, bool forces, cudaStream_t s,
+                const double* d_wgt, const int* d_count) {
   if (c->cfg.precision == AP_PREC_FP64)
-    run_ace<double>(c, d_lam, d_queue, d_e_prec, forces, s);
+    run_ace<double>(c, d_lam, d_wgt, d_queue, d_count, d_e_prec, forces, s);
   else
-    run_ace<float>(c, d_lam, d_queue, d_e_prec, forces, s);
+    run_ace<float>(c, d_lam, d_wgt, d_queue, d_count, d_e_prec, forces, s);
 }
 
 void launch_ace_finalize(ap_ctx* c, double* d_f, cudaStream_t s) {
