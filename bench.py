@@ -35,10 +35,22 @@ import ap_inputs as I  # noqa: E402
 
 MD_PER_STEP = 10
 METRIC = "atom-steps/s adaptive vs full-ACE on 1 GB300 at <=10 meV/A force error"
-# Algorithmic FLOPs of the fused ACE kernel: per neighbour pair within r_c and per
-# precise atom (contractions, basis functions and their gradients; FMA = 2).
-ACE_FLOP_PER_PAIR = 1855
-ACE_FLOP_PER_ATOM = 32000
+# Algorithmic FLOPs of the ACE force stage k_ace_adjoint (the dominant kernel), per
+# neighbour pair within r_c and per precise atom (FMA = 2): per pair the radial
+# functions and derivatives (~100), the solid harmonics and gradients for l <= 4
+# (~400), the two 8-term contractions and the accumulations for 25 (l, m) (~1040)
+# and the scatter (~40); per atom u = W^T dE/dA / N0 (~3300).
+ADJ_FLOP_PER_PAIR = 1580
+ADJ_FLOP_PER_ATOM = 3300
+# The whole ACE evaluation (k_ace_basis + k_ace_nu3 + k_ace_adjoint): per pair add the
+# basis stage (g, Y and the G = g^T Y contraction, ~520); per atom add A = W G, the
+# nu = 1, 2 energy and gradient (~7000) and the nu = 3 monomials (~11400).
+ACE_FLOP_PER_PAIR = ADJ_FLOP_PER_PAIR + 520
+ACE_FLOP_PER_ATOM = ADJ_FLOP_PER_ATOM + 7000 + 11400
+# DRAM bytes (read + write) of one k_ace_adjoint launch on this workload: the ncu
+# capture of the 500k-atom case (60,000 precise atoms: 128.6 MB read + 4.0 MB
+# written) scaled by the precise atoms to 240,000 (profiles/k_ace_adjoint_slab50_mixed.md).
+ADJ_TRAFFIC_BYTES = 132.6e6 * 240000 / 60000
 # FP32 SIMT peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -55,6 +67,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip full-ACE/full-EAM, error and CPU baseline legs")
     p.add_argument("--skin", type=float, default=1.0, help="neighbour-list skin (A); lists are rebuilt every "
                    "lambda update, so skin/2 bounds the displacement over 10 MD steps")
+    p.add_argument("--thermostat", action="store_true", help="local thermostat (Appendix C) in the timed run")
     p.add_argument("--detector", default="csp", choices=["csp", "selector"],
                    help="detector behind lambda_0 in the timed run (centro-symmetry or the stored selector)")
     return p.parse_args()
@@ -173,10 +186,10 @@ def run_ours(args, ws, rank, local):
 
     sel = np.load(os.path.join(ROOT, "paper_2411_03002_gb300", "selector_cu.npz"))
 
-    def new_ctx(h, p=prec, detector=ap.DETECT_CSP):
+    def new_ctx(h, p=prec, detector=ap.DETECT_CSP, thermostat=False):
         c = ap.Context(ap.make_config(eam, acep, h, precision=p, indenter=w.indenter, lambda_every=MD_PER_STEP,
                                       dt=w.dt, skin=args.skin, detector=detector, sel_p_lo=float(sel["p_lo"]),
-                                      sel_p_hi=float(sel["p_hi"])))
+                                      sel_p_hi=float(sel["p_hi"]), thermostat=thermostat or args.thermostat))
         if detector == ap.DETECT_SELECTOR:
             c.sel_set_model(sel["params"], sel["mu"], sel["inv_sigma"])
         return c
@@ -219,10 +232,12 @@ def run_ours(args, ws, rank, local):
     atom_steps = w.n * MD_PER_STEP * args.steps * ws
     value = atom_steps / (ms / 1e3)
     ace_ms, ace_calls = prof["phases"]["ace"]
+    adj_ms, adj_calls = prof["phases"]["ace_adjoint"]          # a sub-phase of "ace"
     flops = ACE_FLOP_PER_PAIR * prof["ace_pairs"] + ACE_FLOP_PER_ATOM * prof["ace_atoms"]
-    achieved = flops / (ace_ms / 1e3) / 1e12 if ace_ms > 0 else 0.0
-    phase_share = {k: round(m / max(1e-9, sum(p[0] for p in prof["phases"].values())), 4)
-                   for k, (m, c) in prof["phases"].items()}
+    adj_flops = ADJ_FLOP_PER_PAIR * prof["ace_pairs"] + ADJ_FLOP_PER_ATOM * prof["ace_atoms"]
+    achieved = adj_flops / (adj_ms / 1e3) / 1e12 if adj_ms > 0 else 0.0
+    top = {k: v for k, v in prof["phases"].items() if k != "ace_adjoint"}
+    phase_share = {k: round(m / max(1e-9, sum(p[0] for p in top.values())), 4) for k, (m, c) in top.items()}
 
     # end-to-end through the public call with host buffers (pinned), copies inside the timed region
     xh, vh, fh = x.cpu().pin_memory(), v.cpu().pin_memory(), f.cpu().pin_memory()
@@ -303,8 +318,9 @@ def run_ours(args, ws, rank, local):
         del es, fs_, fa_, fe_, fh_
         torch.cuda.empty_cache()
         # full-ACE, full-EAM and selector-driven adaptive MD on the same GPU, same workload, same code path
-        for mode in ("full-ace", "full-eam", "selector"):
+        for mode in ("full-ace", "full-eam", "selector", "thermostat"):
             c2 = (new_ctx(hyb, detector=ap.DETECT_SELECTOR) if mode == "selector"
+                  else new_ctx(hyb, thermostat=True) if mode == "thermostat"
                   else new_ctx(hyb_for(mode, w.hyb)))
             x2, v2, f2, m2, fx2, l2 = tensors()
             c2.build_neighbors(x2, w.box)
@@ -321,6 +337,10 @@ def run_ours(args, ws, rank, local):
             rate = w.n * MD_PER_STEP * k2 / (a.elapsed_time(b) / 1e3)
             if mode == "selector":
                 extras["selector"]["atom_steps_s"] = rate
+            elif mode == "thermostat":
+                st2 = c2.step(x2, v2, f2, m2, fx2, l2, 0)
+                extras["thermostat"] = {"atom_steps_s": rate, "corrections": st2.th_corrected,
+                                        "refused": st2.th_refused, "corrected_energy_eV": st2.th_energy}
             else:
                 extras[mode.replace("-", "_") + "_atom_steps_s"] = rate
             c2.close()
@@ -340,7 +360,8 @@ def run_ours(args, ws, rank, local):
             "vs_baseline": None, "dtype": "f32" if prec == ap.PREC_MIXED else "f64", "data": "synthetic",
             "config": {"workload": f"nanoindentation-shaped FCC slab {args.ncell}^3 cells ({w.n} atoms), Hyb2 "
                                    f"(r_lambda 8/20 A), {args.mode}, {args.precision} precision"
-                                   + (", selector detector" if args.detector == "selector" else ""),
+                                   + (", selector detector" if args.detector == "selector" else "")
+                                   + (", local thermostat" if args.thermostat else ""),
                        "atoms": w.n, "md_steps_per_step": MD_PER_STEP, "lambda_every": MD_PER_STEP,
                        "precision": "FP32 potentials, FP64 integration and energy sums" if prec == ap.PREC_MIXED
                        else "FP64", "l2": "inputs larger than L2 (no flush)",
@@ -349,12 +370,14 @@ def run_ours(args, ws, rank, local):
             "e2e": {"value": atom_steps / (ms_e2e / 1e3), "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": prof["kernels"],
-            "roofline": {"bound": "alu", "kernel": "k_ace (fused ACE energy/adjoint/force)",
+            "roofline": {"bound": "alu", "kernel": "k_ace_adjoint (ACE force stage)",
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ADJ_TRAFFIC_BYTES,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived, not measured)",
-                         "ace_ms_per_launch": ace_ms / max(1, ace_calls), "ace_pairs": prof["ace_pairs"],
-                         "ace_atoms": prof["ace_atoms"]},
+                         "ms_per_launch": adj_ms / max(1, adj_calls), "pairs": prof["ace_pairs"],
+                         "atoms": prof["ace_atoms"],
+                         "ace_all_kernels": {"tflops": flops / (ace_ms / 1e3) / 1e12 if ace_ms > 0 else 0.0,
+                                             "ms_per_step": ace_ms / max(1, ace_calls)}},
             "phase_share": phase_share,
             "clocks": ck,
             "cpu_baseline": cpu,

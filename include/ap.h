@@ -362,7 +362,8 @@ ap_status ap_eval_eam_static(const ap_config* h_cfg, int64_t n, const double* d_
 #define AP_PHASE_ACE 3         /* fused ACE energy/adjoint/force kernel           */
 #define AP_PHASE_OTHER 4       /* integrator, finalize, indenter, reductions      */
 #define AP_PHASE_THERMOSTAT 5  /* local thermostat: difference forces, Delta E, corrections */
-#define AP_NUM_PHASES 6
+#define AP_PHASE_ACE_ADJOINT 6 /* k_ace_adjoint alone (the force stage; also counted in ACE) */
+#define AP_NUM_PHASES 7
 
 /* Turn per-phase event timing in ap_step on (1) or off (0) and clear the totals.
  * No paper counterpart: instrumentation of this implementation. */

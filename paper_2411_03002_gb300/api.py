@@ -249,7 +249,7 @@ class Context:
         return StepStats(st.step, st.n_precise, st.n_detected, st.rebuilds, st.e_pot, st.e_kin, st.max_disp,
                          st.error_bits, st.th_corrected, st.th_refused, st.th_energy)
 
-    PHASES = ("neighbors", "classify", "eam", "ace", "other", "thermostat")
+    PHASES = ("neighbors", "classify", "eam", "ace", "other", "thermostat", "ace_adjoint")
 
     def profile_enable(self, on: bool = True):
         self._ck(self.lib.ap_profile_enable(self.h, 1 if on else 0))

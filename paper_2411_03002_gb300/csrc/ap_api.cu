@@ -353,40 +353,46 @@ void queue_from_lambda(ap_ctx* c, cudaStream_t s) {
   k_compact_q<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_flag, c->d_scan, c->d_precise, &c->d_sc->n_precise);
 }
 
+}  // namespace
+
+namespace ap {
+int prof_mark(ap_ctx* c, cudaStream_t s) {
+  if (!c->prof_on) return -1;
+  if (c->ev_used == (int)c->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->ev_pool.push_back(e);
+  }
+  const int k = c->ev_used++;
+  cudaEventRecord(c->ev_pool[k], s);
+  return k;
+}
+
+void prof_add(ap_ctx* c, int phase, int start, int end) {
+  if (start >= 0 && end >= 0) c->ev_pairs_phase.push_back({phase, start, end});
+}
+}  // namespace ap
+
+namespace {
+
 // Event pair around one phase of ap_step (only when profiling is on).
 struct PhaseTimer {
   ap_ctx* c;
   cudaStream_t s;
   int phase;
-  int start = -1;
-  static int next_event(ap_ctx* c) {
-    if (c->ev_used == (int)c->ev_pool.size()) {
-      cudaEvent_t e;
-      cudaEventCreate(&e);
-      c->ev_pool.push_back(e);
-    }
-    return c->ev_used++;
-  }
-  PhaseTimer(ap_ctx* c_, cudaStream_t s_, int phase_) : c(c_), s(s_), phase(phase_) {
-    if (!c->prof_on) return;
-    start = next_event(c);
-    cudaEventRecord(c->ev_pool[start], s);
-  }
+  int start;
+  PhaseTimer(ap_ctx* c_, cudaStream_t s_, int phase_) : c(c_), s(s_), phase(phase_) { start = prof_mark(c, s); }
   ~PhaseTimer() {
-    if (start < 0) return;
-    int e = next_event(c);
-    cudaEventRecord(c->ev_pool[e], s);
-    c->ev_pairs_phase.push_back({phase, start});
+    if (start >= 0) prof_add(c, phase, start, prof_mark(c, s));
   }
 };
 
-// After a synchronisation: fold the recorded event pairs into the totals.
 void collect_profile(ap_ctx* c) {
   for (auto& pr : c->ev_pairs_phase) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->ev_pool[pr.second], c->ev_pool[pr.second + 1]) == cudaSuccess) {
-      c->prof_ms[pr.first] += ms;
-      c->prof_calls[pr.first] += 1;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[pr.start], c->ev_pool[pr.end]) == cudaSuccess) {
+      c->prof_ms[pr.phase] += ms;
+      c->prof_calls[pr.phase] += 1;
     }
   }
   c->ev_pairs_phase.clear();

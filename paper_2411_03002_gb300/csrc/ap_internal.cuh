@@ -265,10 +265,13 @@ struct ap_ctx {
   // profiling (ap_profile_enable / ap_profile_read)
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;   // reusable events
-  std::vector<std::pair<int, int>> ev_pairs_phase;  // (phase, index of start event)
+  struct EvSpan {
+    int phase, start, end;
+  };
+  std::vector<EvSpan> ev_pairs_phase;   // (phase, start event, end event)
   int ev_used = 0;
-  double prof_ms[AP_NUM_PHASES] = {0, 0, 0, 0, 0};
-  int64_t prof_calls[AP_NUM_PHASES] = {0, 0, 0, 0, 0};
+  double prof_ms[AP_NUM_PHASES] = {};
+  int64_t prof_calls[AP_NUM_PHASES] = {};
   int64_t kernels = 0;                // kernels launched by ap_step since the last enable
 };
 
@@ -287,6 +290,10 @@ void launch_build_ace(ap_ctx* c, const double* d_x, const int* d_queue, const in
 void launch_export_rows(ap_ctx* c, int which, int rows, int cap_out, int* d_cnt, int* d_idx, int* d_shift,
                         cudaStream_t s);
 void launch_wrap_positions(ap_ctx* c, double* d_x, cudaStream_t s);
+
+// ap_api.cu: profiling marks (event index, or -1 when profiling is off) and spans
+int prof_mark(ap_ctx* c, cudaStream_t s);
+void prof_add(ap_ctx* c, int phase, int start, int end);
 
 // k_classify.cu
 void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s);

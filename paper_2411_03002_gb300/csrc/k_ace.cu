@@ -696,7 +696,9 @@ void run_ace(ap_ctx* c, const double* d_lam, const double* d_wgt, const int* d_q
   k_ace_basis<R><<<c->num_sms * b1[pi], kWarps<R> * 32, s1, s>>>(a);
   const int t2 = sizeof(R) == 4 ? 128 : 64;
   k_ace_nu3<R><<<c->num_sms * (sizeof(R) == 4 ? 8 : 16), t2, 0, s>>>(a, P);
+  const int t0 = prof_mark(c, s);
   k3<<<c->num_sms * b3[pi][forces], kWarps3<R> * 32, s3, s>>>(a);
+  prof_add(c, AP_PHASE_ACE_ADJOINT, t0, prof_mark(c, s));
   c->kernels += 3;
 }
 
