@@ -93,11 +93,14 @@ EAM_NOMINAL = EAMParams(beta=3.0, alpha=1.6, A=0.42398, D=0.23925, rp=2.81322)
 
 @dataclasses.dataclass
 class ACEParams:
-    """Linear single-species ACE: radial mixing W[l][n][k] and coefficients c[v]."""
+    """Single-species ACE: radial mixing W[l][n][k] and coefficients c[v] of phi^(1);
+    with c2, the Finnis-Sinclair form E = phi^(1) + F(phi^(2)) (phi^(2) = sum c2_v B_v)."""
     W: np.ndarray            # (5, 8, 8) float64, indexed [l][n][k]
     c: np.ndarray            # (512,) float64; the first n_basis entries are used
     rc: float = 7.0
     n0: float = 10.0         # A-basis normalisation N0
+    c2: Optional[np.ndarray] = None   # (512,) coefficients of phi^(2), or None (linear ACE)
+    fs_eps: float = 0.1      # regularisation of the square-root embedding
 
 
 @dataclasses.dataclass
@@ -154,6 +157,16 @@ def ace_params(seed_config: int = 0, k: int = 2, c_std: float = 0.01) -> ACEPara
     W = np.eye(8)[None, :, :] + 0.1 * g.standard_normal((5, 8, 8))
     c = c_std * g.standard_normal(512)
     return ACEParams(W=W, c=c)
+
+
+def ace_params_fs(seed_config: int = 0, k: int = 2, c2_scale: float = -0.1, fs_eps: float = 0.01) -> ACEParams:
+    """ace_params plus seeded phi^(2) coefficients c2 = c2_scale N(0, 1) (512 draws).  With
+    this seed phi^(2) keeps one sign over FCC-like cells: c2_scale = -0.1 puts it near
+    +0.05 (the square-root branch), +0.1 near -0.05 (the odd extension), -0.001 near
+    +5e-4 (the transition, |phi| ~ 5 eps^2)."""
+    p = ace_params(seed_config, k)
+    g = rng_for(seed_config, k + 40)
+    return dataclasses.replace(p, c2=c2_scale * g.standard_normal(512), fs_eps=fs_eps)
 
 
 ANCHOR_FILE = __import__("os").path.join(__import__("os").path.dirname(__file__), "ace_anchor.npz")

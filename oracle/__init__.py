@@ -352,6 +352,54 @@ class ACE:
         return e, f
 
 
+def fs_embed(phi, eps: float):
+    """Embedding of the Finnis-Sinclair ACE form (Eq. energy_ace: E = phi^(1) + sqrt(phi^(2))),
+    regularised so that it is defined and C1 for every real phi:
+    F(phi) = sign(phi) (sqrt(|phi| + eps^2) - eps),  F'(phi) = 1 / (2 sqrt(|phi| + eps^2)).
+    For phi >> eps^2, F = sqrt(phi) - eps + O(eps^2/sqrt(phi)).  Returns (F, F')."""
+    phi = _f64(phi)
+    s = np.sqrt(np.abs(phi) + eps * eps)
+    return np.sign(phi) * (s - eps), 0.5 / s
+
+
+class ACEFS:
+    """ACE with the Finnis-Sinclair form E_i = phi_i^(1) + F(phi_i^(2)), phi^(p) = sum_v
+    c^(p)_v B_iv.  Forces at fixed weights: -grad sum_i w_i E_i = -grad sum_i w_i phi_i^(1)
+    - grad sum_i (w_i F'(phi_i^(2))) phi_i^(2), i.e. two linear ACE evaluations."""
+
+    def __init__(self, params, fcut_mode: int = 0):
+        import dataclasses as _dc
+        self.eps = float(params.fs_eps)
+        self.rc = float(params.rc)
+        self.a1 = ACE(_dc.replace(params, c2=None), fcut_mode)
+        self.a2 = ACE(_dc.replace(params, c=params.c2, c2=None), fcut_mode)
+
+    def phis(self, x, box, nl=None):
+        if nl is None:
+            nl = neighbors(x, box, self.rc)
+        p1, _ = self.a1.eval(x, box, nl=nl)
+        p2, _ = self.a2.eval(x, box, nl=nl)
+        return p1, p2
+
+    def eval(self, x, box, weights=None, nl: Optional[NeighborList] = None):
+        """Site energies (0 where weight == 0) and F = -grad sum_i w_i E_i."""
+        x = _f64(x)
+        if nl is None:
+            nl = neighbors(x, box, self.rc)
+        p1, p2 = self.phis(x, box, nl)
+        fv, dfv = fs_embed(p2, self.eps)
+        w = np.ones(x.shape[0]) if weights is None else _f64(weights)
+        _, f1 = self.a1.eval(x, box, weights=w, nl=nl)
+        _, f2 = self.a2.eval(x, box, weights=w * dfv, nl=nl)
+        e = np.where(w != 0.0, p1 + fv, 0.0)
+        return e, f1 + f2
+
+
+def ace_for(params, fcut_mode: int = 0):
+    """The oracle ACE for a parameter set: linear, or Finnis-Sinclair when params.c2 is set."""
+    return ACEFS(params, fcut_mode) if getattr(params, "c2", None) is not None else ACE(params, fcut_mode)
+
+
 def hybrid(x, box, lam, eam_p, ace: ACE):
     """Eq. energy_hyb and Eq. F_i_d: E_i = lam E^f + (1-lam) E^p and
     F = -grad sum_k [lam_k E_k^f + (1-lam_k) E_k^p] at fixed lam.
