@@ -130,6 +130,15 @@ typedef struct {
    * disjoint.  A negative radicand skips that correction and makes ap_step return
    * AP_ERR_RADICAND.  One system only (not with ap_build_neighbors_batch). */
   int32_t thermostat_on;
+  /* Finnis-Sinclair ACE form (Eq. energy_ace, nonlinear part): with ace_fs_on = 1,
+   * E_i^(p) = phi_i^(1) + F(phi_i^(2)), phi^(1) = sum c_v B_iv (ace_c) and
+   * phi^(2) = sum c2_v B_iv (ace_c2, the same basis and ace_nc), and the embedding
+   * F(phi) = sign(phi) (sqrt(|phi| + eps^2) - eps), eps = ace_fs_eps > 0: the paper's
+   * sqrt(phi) up to the constant -eps and O(eps^2/sqrt(phi)), defined and C1 for every
+   * real phi.  0 = linear ACE (E = phi^(1)). */
+  int32_t ace_fs_on;
+  double ace_fs_eps;
+  double ace_c2[512];
 } ap_config;
 
 typedef struct ap_ctx ap_ctx;

@@ -62,6 +62,13 @@ def make_config(eam, ace, hyb, precision: int = N.PREC_MIXED, skin: float = 1.0,
     c.ace_nc = nc
     c.ace_rc = float(ace.rc)
     c.ace_n0 = float(ace.n0)
+    c2 = getattr(ace, "c2", None)
+    if c2 is not None:   # Finnis-Sinclair form E = phi1 + F(phi2)
+        c2 = np.ascontiguousarray(c2, dtype=np.float64).reshape(-1)
+        c.ace_fs_on = 1
+        c.ace_fs_eps = float(ace.fs_eps)
+        for i in range(min(512, c2.size)):
+            c.ace_c2[i] = c2[i]
     c.csp_lo, c.csp_hi = float(hyb.csp_lo), float(hyb.csp_hi)
     c.r_lo, c.r_hi = float(hyb.r_lo), float(hyb.r_hi)
     c.dlam_min = float(hyb.dlam_min)

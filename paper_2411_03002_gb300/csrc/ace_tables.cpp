@@ -123,69 +123,102 @@ void build_ace_tables(const ap_config& cfg, AceTables& t) {
   // nu = 3: flattened Gaunt product terms coef * A[a1] A[a2] A[a3] (coef = c_v G),
   //         interleaved across functions so that neighbouring terms touch
   //         different A entries.
-  t.c1.assign(8, 0.0);
-  t.m2.assign(5 * 64, 0.0);
-  std::vector<std::vector<std::pair<int, double>>> per_fn;
+  // The nu = 3 Gaunt product terms of every function (structure only).
+  struct Term {
+    int idx;     // a1 | a2 << 8 | a3 << 16 over the 200 A entries
+    int fn;      // the B-function v
+    double g;    // real Gaunt coefficient
+  };
+  std::vector<std::vector<Term>> per_fn;
   for (int v = 0; v < t.nb; ++v) {
     const int* d = &t.desc[7 * v];
-    double cv = (v < cfg.ace_nc) ? cfg.ace_c[v] : 0.0;
-    if (d[0] == 1) {
-      t.c1[d[1]] = cv;
-    } else if (d[0] == 2) {
-      int l = d[4], n1 = d[1], n2 = d[2];
-      if (n1 == n2) {
-        t.m2[l * 64 + n1 * 8 + n1] = 2.0 * cv;
-      } else {
-        t.m2[l * 64 + n1 * 8 + n2] = cv;
-        t.m2[l * 64 + n2 * 8 + n1] = cv;
-      }
-    } else {
-      int l1 = d[4], l2 = d[5], l3 = d[6];
-      std::vector<std::pair<int, double>> terms;
-      for (int m1 = -l1; m1 <= l1; ++m1)
-        for (int m2 = -l2; m2 <= l2; ++m2)
-          for (int m3 = -l3; m3 <= l3; ++m3) {
-            double g = G(l1, m1, l2, m2, l3, m3);
-            if (std::fabs(g) < 1e-14) continue;
-            terms.push_back({aidx(d[1], l1, m1) | (aidx(d[2], l2, m2) << 8) | (aidx(d[3], l3, m3) << 16), cv * g});
-          }
-      per_fn.push_back(terms);
-    }
+    if (d[0] != 3) continue;
+    int l1 = d[4], l2 = d[5], l3 = d[6];
+    std::vector<Term> terms;
+    for (int m1 = -l1; m1 <= l1; ++m1)
+      for (int m2 = -l2; m2 <= l2; ++m2)
+        for (int m3 = -l3; m3 <= l3; ++m3) {
+          double g = G(l1, m1, l2, m2, l3, m3);
+          if (std::fabs(g) < 1e-14) continue;
+          terms.push_back({aidx(d[1], l1, m1) | (aidx(d[2], l2, m2) << 8) | (aidx(d[3], l3, m3) << 16), v, g});
+        }
+    per_fn.push_back(terms);
   }
-  t.term_idx.clear();
-  t.term_coef.clear();
+  // flattened, interleaved across functions
+  std::vector<Term> flat;
   for (size_t k = 0;; ++k) {
     bool any = false;
     for (auto& fn : per_fn)
       if (k < fn.size()) {
-        t.term_idx.push_back(fn[k].first);
-        t.term_coef.push_back(fn[k].second);
+        flat.push_back(fn[k]);
         any = true;
       }
     if (!any) break;
   }
-  t.n_terms = (int)t.term_idx.size();
+  t.n_terms = (int)flat.size();
+  t.term_idx.clear();
+  for (const Term& u : flat) t.term_idx.push_back(u.idx);
 
   auto c48 = [](int a) { return (a / 25) * 16 + (a % 25); };   // n <= 2, lm < 16
-
   // nu = 3 as merged monomials: every term coef*A1*A2*A3 with its three indices in
   // the 48-entry numbering, sorted (a <= b <= c), and the coefficients of equal
   // monomials summed (E3 is a sum of monomials, so merging is exact algebra).
   // Ordered by the packed key c | b << 6 | a << 12, i.e. by (a, b, c); the structure
   // does not depend on the coefficients (terms with c_v = 0 stay, coefficient 0).
-  std::map<uint32_t, double> mono;
-  for (int k = 0; k < t.n_terms; ++k) {
-    int pk = t.term_idx[k];
+  std::vector<uint32_t> key_of(flat.size());
+  std::map<uint32_t, int> slot;
+  for (size_t k = 0; k < flat.size(); ++k) {
+    int pk = flat[k].idx;
     int v[3] = {c48(pk & 255), c48((pk >> 8) & 255), c48((pk >> 16) & 255)};
     std::sort(v, v + 3);
-    mono[(uint32_t)v[2] | ((uint32_t)v[1] << 6) | ((uint32_t)v[0] << 12)] += t.term_coef[k];
+    key_of[k] = (uint32_t)v[2] | ((uint32_t)v[1] << 6) | ((uint32_t)v[0] << 12);
+    slot[key_of[k]] = 0;
   }
   t.nu3_key.clear();
-  t.nu3_coef.clear();
-  for (auto& kv : mono) {
+  for (auto& kv : slot) {
+    kv.second = (int)t.nu3_key.size();
     t.nu3_key.push_back(kv.first);
-    t.nu3_coef.push_back(kv.second);
   }
+
+  // Coefficient-dependent tables of one coefficient vector c:
+  // nu = 1: E1 = sum_n c1[n] A_n00.
+  // nu = 2: E2 = 1/2 sum_lm A_lm^T M_l A_lm with the symmetric 8x8 matrices
+  //         M_l[n1][n2] = c(n1,n2,l) (n1 != n2), M_l[n][n] = 2 c(n,n,l), so that
+  //         dE2/dA_{n,lm} = sum_n2 M_l[n][n2] A_{n2,lm}.
+  // nu = 3: term coefficients c_v G and the merged monomial coefficients.
+  auto coef_tables = [&](const double* c, int nc, std::vector<double>& c1, std::vector<double>& m2,
+                         std::vector<double>& term_coef, std::vector<double>& nu3) {
+    c1.assign(8, 0.0);
+    m2.assign(5 * 64, 0.0);
+    for (int v = 0; v < t.nb; ++v) {
+      const int* d = &t.desc[7 * v];
+      const double cv = (v < nc) ? c[v] : 0.0;
+      if (d[0] == 1) {
+        c1[d[1]] = cv;
+      } else if (d[0] == 2) {
+        int l = d[4], n1 = d[1], n2 = d[2];
+        if (n1 == n2) {
+          m2[l * 64 + n1 * 8 + n1] = 2.0 * cv;
+        } else {
+          m2[l * 64 + n1 * 8 + n2] = cv;
+          m2[l * 64 + n2 * 8 + n1] = cv;
+        }
+      }
+    }
+    term_coef.assign(flat.size(), 0.0);
+    nu3.assign(t.nu3_key.size(), 0.0);
+    for (size_t k = 0; k < flat.size(); ++k) {
+      const double cv = (flat[k].fn < nc) ? c[flat[k].fn] : 0.0;
+      term_coef[k] = cv * flat[k].g;
+      nu3[slot[key_of[k]]] += term_coef[k];
+    }
+  };
+  coef_tables(cfg.ace_c, cfg.ace_nc, t.c1, t.m2, t.term_coef, t.nu3_coef);
+  std::vector<double> unused;
+  if (cfg.ace_fs_on)
+    coef_tables(cfg.ace_c2, cfg.ace_nc, t.c1b, t.m2b, unused, t.nu3_coef2);
+  else
+    coef_tables(nullptr, 0, t.c1b, t.m2b, unused, t.nu3_coef2);
 }
 
 }  // namespace ap

@@ -59,6 +59,8 @@ ap_status validate(const ap_config& g, std::string& why) {
   if (g.detector == AP_DETECT_SELECTOR && !(g.sel_p_lo >= 0 && g.sel_p_hi > g.sel_p_lo))
     return bad("need 0 <= sel_p_lo < sel_p_hi");
   if (g.thermostat_on != 0 && g.thermostat_on != 1) return bad("thermostat_on must be 0 or 1");
+  if (g.ace_fs_on != 0 && g.ace_fs_on != 1) return bad("ace_fs_on must be 0 or 1");
+  if (g.ace_fs_on && !(g.ace_fs_eps > 0)) return bad("ace_fs_eps must be positive");
   return AP_OK;
 }
 
@@ -189,9 +191,13 @@ ap_status ensure_capacity(ap_ctx* c, int64_t n) {
     CK(dalloc(c->d_ace_nin, m));
     CK(dalloc(c->d_ace_e12, m));
     CK(dalloc(c->d_ace_e3, m));
-    void** bufs[3] = {&c->d_ace_a48, &c->d_ace_dA, &c->d_ace_de3};
-    const size_t per[3] = {48, 200, 48};
-    for (int k = 0; k < 3; ++k) {
+    void** bufs[4] = {&c->d_ace_a48, &c->d_ace_dA, &c->d_ace_de3, &c->d_ace_dAb};
+    const size_t per[4] = {48, 200, 48, c->cfg.ace_fs_on ? (size_t)200 : (size_t)1};
+    if (c->cfg.ace_fs_on) {
+      CK(dalloc(c->d_ace_e12b, m));
+      CK(dalloc(c->d_ace_fs, 2 * m));
+    }
+    for (int k = 0; k < 4; ++k) {
       if (*bufs[k]) cudaFree(*bufs[k]);
       *bufs[k] = nullptr;
       CK(cudaMalloc(bufs[k], rb * per[k] * (size_t)m));
@@ -539,7 +545,8 @@ void ap_destroy(ap_ctx* c) {
                   c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected,
                   c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_efast, c->d_eprec,
                   c->d_eatom, c->d_eext, c->d_changeable, c->d_W32, c->d_W64, c->d_ace_slots, c->d_ace_nin,
-                  c->d_ace_a48, c->d_ace_dA, c->d_ace_e12, c->d_ace_de3, c->d_ace_e3, c->d_scan_tmp, c->d_red,
+                  c->d_ace_a48, c->d_ace_dA, c->d_ace_e12, c->d_ace_de3, c->d_ace_e3, c->d_ace_dAb, c->d_ace_e12b,
+                  c->d_ace_fs, c->d_scan_tmp, c->d_red,
                   c->d_sel_model, c->d_sel_master, c->d_sel_m1, c->d_sel_m2, c->d_sel_grad, c->d_sel_partial,
                   c->d_sel_rho, c->d_sel_feat, c->d_sel_score, c->d_sel_z, c->d_sel_h1, c->d_sel_h2,
                   c->d_th_lamc, c->d_th_dlam, c->d_th_w, c->d_th_df, c->d_th_ep, c->d_th_de, c->d_th_qk, c->d_th_qe,

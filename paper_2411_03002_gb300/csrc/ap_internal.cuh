@@ -108,6 +108,8 @@ struct AceTables {
   // lane-per-atom kernel's straight-line code (ace_nu3.inc) is generated from nu3_key.
   std::vector<uint32_t> nu3_key;
   std::vector<double> nu3_coef;
+  // second coefficient set phi^(2) of the Finnis-Sinclair form (zeros unless ace_fs_on)
+  std::vector<double> c1b, m2b, nu3_coef2;
 };
 void build_ace_tables(const ap_config& cfg, AceTables& t);
 
@@ -214,6 +216,9 @@ struct ap_ctx {
   double* d_ace_e12 = nullptr;      // [n]
   void* d_ace_de3 = nullptr;        // [n][48]
   double* d_ace_e3 = nullptr;       // [n]
+  void* d_ace_dAb = nullptr;        // [n][200] (Finnis-Sinclair form)
+  double* d_ace_e12b = nullptr;     // [n]
+  double* d_ace_fs = nullptr;       // [n][2]
 
   // scan scratch
   int* d_scan_tmp = nullptr;

@@ -315,8 +315,12 @@ struct AceArgs {
   const R* W;
   const R* M2;
   const R* C1;
+  const R* M2b;      // phi^(2) tables of the Finnis-Sinclair form
+  const R* C1b;
   R rc2, inv_rc, inv_n0;
   int mode;
+  int fs_on;
+  double fs_eps;
   double* e_prec;
   float4* facc32;
   double* facc64;
@@ -325,8 +329,11 @@ struct AceArgs {
   R* a48;            // [q][48] A entries with n <= 2, l <= 3 (input of nu = 3)
   R* dA;             // [q][200] dE/dA of nu = 1, 2
   double* e12;       // [q] E of nu = 1, 2
-  R* de3;            // [q][48] dE3/dA
-  double* e3;        // [q] E3
+  R* de3;            // [q][48] dE3/dA (Finnis-Sinclair form: of phi^(1) + F' phi^(2))
+  double* e3;        // [q] E3 (of phi^(1))
+  R* dAb;            // [q][200] dphi^(2)_12/dA                 (Finnis-Sinclair form only)
+  double* e12b;      // [q] phi^(2)_12                          (Finnis-Sinclair form only)
+  double* fs;        // [q][2] F(phi^(2)), F'(phi^(2))          (Finnis-Sinclair form only)
 };
 
 // nu = 3 coefficients, passed by value (kernel parameter space), in the order of kNu3Key.
@@ -344,13 +351,15 @@ struct Nu3Coef {
 //   nu = 1, 2: E12 and dE12/dA (symmetric 8x8 matrix-vector products per (l, m)).
 template <typename R>
 __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB : 1) k_ace_basis(AceArgs<R> a) {
-  // Shared memory: W [320] | M2 [320] | C1 [8] | per warp: list [kListCap][4] | tile [kRows][kCols]
-  // (A and the G scratch alias the tile once the contraction is done).
+  // Shared memory: W [320] | M2 [320] | C1 [8] | M2b [320] | C1b [8] | per warp: list
+  // [kListCap][4] | tile [kRows][kCols] (A and the G scratch alias the tile after stage A).
   extern __shared__ __align__(128) unsigned char smem_raw[];
   R* Ws = reinterpret_cast<R*>(smem_raw);
   R* M2 = Ws + 320;
   R* C1 = M2 + 320;
-  R* wbase = C1 + 8;
+  R* M2b = C1 + 8;
+  R* C1b = M2b + 320;
+  R* wbase = C1b + 8;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   R* list = wbase + warp * (4 * kListCap + kRows * kCols);
   R* tile = list + 4 * kListCap;
@@ -359,8 +368,12 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
   for (int t = threadIdx.x; t < 320; t += blockDim.x) {
     Ws[t] = a.W[t];
     M2[t] = a.M2[t];
+    M2b[t] = a.M2b[t];
   }
-  if (threadIdx.x < 8) C1[threadIdx.x] = a.C1[threadIdx.x];
+  if (threadIdx.x < 8) {
+    C1[threadIdx.x] = a.C1[threadIdx.x];
+    C1b[threadIdx.x] = a.C1b[threadIdx.x];
+  }
   __syncthreads();
   const int m = *a.count;
   const int kq = lane & 7, grp = lane >> 3;
@@ -475,6 +488,21 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
       e += A[o] * (R(0.5) * s + lin);
       a.dA[(size_t)q * 200 + o] = s + lin;
     }
+    if (a.fs_on) {   // the same products with the phi^(2) coefficients
+      R eb = R(0);
+      for (int o = lane; o < 200; o += 32) {
+        const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
+        const R* mrow = &M2b[l * 64 + n * 8];
+        R sb = R(0);
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) sb += mrow[n2] * A[n2 * 25 + lm];
+        const R lin = lm == 0 ? C1b[n] : R(0);
+        eb += A[o] * (R(0.5) * sb + lin);
+        a.dAb[(size_t)q * 200 + o] = sb + lin;
+      }
+      const double Eb = warp_sum<double>((double)eb);
+      if (lane == 0) a.e12b[q] = Eb;
+    }
     const double E = warp_sum<double>((double)e);
     if (lane == 0) {
       a.e12[q] = E;
@@ -489,8 +517,12 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
 // entries and their gradient in registers, as straight-line code over the merged
 // monomials (ace_nu3.inc); coefficients are read from the parameter space.  E3
 // follows from Euler's identity for a homogeneous cubic, E3 = (1/3) sum A dE3/dA.
-template <typename R>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? 128 : 64) k_ace_nu3(AceArgs<R> a, const Nu3Coef<R> P) {
+// Finnis-Sinclair form (FS): a first pass gives the nu = 3 part of phi^(2), hence
+// phi^(2), F and F'; the gradient pass then uses the coefficients c1 + F' c2, and
+// E3 of phi^(1) is E3(c1 + F' c2) - F' E3(c2).
+template <typename R, bool FS>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 128 : 64) k_ace_nu3(AceArgs<R> a, const Nu3Coef<R> P,
+                                                                       const Nu3Coef<R> Q) {
   const int m = *a.count;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
     R A[48], dA[48];
@@ -500,19 +532,43 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 128 : 64) k_ace_nu3(AceArgs<R
       A[v] = src[v];
       dA[v] = R(0);
     }
+    R fp = R(0);
+    double e3b = 0.0, Fv = 0.0;
+    if constexpr (FS) {
+      R eb = R(0);
 #define NU3_GROUP_BEGIN(x, y) \
   {                           \
     const R p_ = A[x] * A[y]; \
     R s_ = R(0);
-#define NU3_TERM(t, z)        \
-  s_ = fma(P.c[t], A[z], s_); \
-  dA[z] = fma(P.c[t], p_, dA[z]);
-#define NU3_GROUP_END(x, y)         \
-  dA[x] = fma(s_, A[y], dA[x]);     \
-  dA[y] = fma(s_, A[x], dA[y]);     \
+#define NU3_TERM(t, z) s_ = fma(Q.c[t], A[z], s_);
+#define NU3_GROUP_END(x, y) \
+  eb = fma(p_, s_, eb);     \
+  }
+      AP_NU3_BODY
+#undef NU3_GROUP_BEGIN
+#undef NU3_TERM
+#undef NU3_GROUP_END
+      e3b = (double)eb;
+      const double phi2 = a.e12b[q] + e3b;
+      const double sq = sqrt(fabs(phi2) + a.fs_eps * a.fs_eps);
+      Fv = phi2 > 0.0 ? sq - a.fs_eps : (phi2 < 0.0 ? a.fs_eps - sq : 0.0);
+      fp = (R)(0.5 / sq);
+    }
+#define NU3_GROUP_BEGIN(x, y) \
+  {                           \
+    const R p_ = A[x] * A[y]; \
+    R s_ = R(0);
+#define NU3_COEF(t) (FS ? fma(fp, Q.c[t], P.c[t]) : P.c[t])
+#define NU3_TERM(t, z)             \
+  s_ = fma(NU3_COEF(t), A[z], s_); \
+  dA[z] = fma(NU3_COEF(t), p_, dA[z]);
+#define NU3_GROUP_END(x, y)     \
+  dA[x] = fma(s_, A[y], dA[x]); \
+  dA[y] = fma(s_, A[x], dA[y]); \
   }
     AP_NU3_BODY
 #undef NU3_GROUP_BEGIN
+#undef NU3_COEF
 #undef NU3_TERM
 #undef NU3_GROUP_END
     R e = R(0);
@@ -522,7 +578,11 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 128 : 64) k_ace_nu3(AceArgs<R
       e = fma(A[v], dA[v], e);
       dst[v] = dA[v];
     }
-    a.e3[q] = (double)e * (1.0 / 3.0);
+    a.e3[q] = (double)e * (1.0 / 3.0) - (FS ? (double)fp * e3b : 0.0);
+    if (FS) {
+      a.fs[2 * (size_t)q] = Fv;
+      a.fs[2 * (size_t)q + 1] = (double)fp;
+    }
   }
 }
 
@@ -530,7 +590,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 128 : 64) k_ace_nu3(AceArgs<R
 // u_klm = (1/N0) sum_n W[l][n][k] dE/dA_nlm and the forces: lanes recompute g, g',
 // Y, grad Y per in-range neighbour (from the kept row positions), contract with u
 // and scatter -w_i p_ij to neighbour j, +w_i sum_j p_ij to i.
-template <typename R, bool FORCES>
+template <typename R, bool FORCES, bool FS>
 __global__ void __launch_bounds__(kWarps3<R> * 32, sizeof(R) == 4 ? AP_ACE3_MINB : 1) k_ace_adjoint(AceArgs<R> a) {
   // Shared memory: W [320] | per warp: dA [200] | U [200]
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -547,9 +607,14 @@ __global__ void __launch_bounds__(kWarps3<R> * 32, sizeof(R) == 4 ? AP_ACE3_MINB
     q = __shfl_sync(0xffffffffu, q, 0);
     if (q >= m) break;
     const int i = a.queue[q];
-    if (lane == 0) a.e_prec[i] = a.e12[q] + a.e3[q];
+    if (lane == 0) a.e_prec[i] = a.e12[q] + a.e3[q] + (FS ? a.fs[2 * (size_t)q] : 0.0);
     if (!FORCES) continue;
-    for (int o = lane; o < 200; o += 32) dA[o] = a.dA[(size_t)q * 200 + o];
+    if (FS) {
+      const R fp = (R)a.fs[2 * (size_t)q + 1];
+      for (int o = lane; o < 200; o += 32) dA[o] = fma(fp, a.dAb[(size_t)q * 200 + o], a.dA[(size_t)q * 200 + o]);
+    } else {
+      for (int o = lane; o < 200; o += 32) dA[o] = a.dA[(size_t)q * 200 + o];
+    }
     __syncwarp();
     for (int v = lane; v < 48; v += 32) dA[(v >> 4) * 25 + (v & 15)] += a.de3[(size_t)q * 48 + v];
     __syncwarp();
@@ -619,7 +684,7 @@ __global__ void k_ace_finalize64(int n, const double* __restrict__ acc, double* 
 
 template <typename R>
 size_t basis_smem() {
-  return sizeof(R) * (320 + 320 + 8) + sizeof(R) * kWarps<R> * (4 * kListCap + kRows * kCols);
+  return sizeof(R) * (320 + 320 + 8 + 320 + 8) + sizeof(R) * kWarps<R> * (4 * kListCap + kRows * kCols);
 }
 
 template <typename R>
@@ -663,8 +728,15 @@ void run_ace(ap_ctx* c, const double* d_lam, const double* d_wgt, const int* d_q
   a.cap = c->cap_ace;
   a.lam = d_lam;
   a.wgt = d_wgt;
-  a.M2 = a.W + 320;   // the parameter block is [W (320) | M2 (320) | C1 (8)]
+  a.M2 = a.W + 320;   // the parameter block is [W (320) | M2 (320) | C1 (8) | M2b (320) | C1b (8)]
   a.C1 = a.W + 640;
+  a.M2b = a.W + 648;
+  a.C1b = a.W + 968;
+  a.fs_on = c->cfg.ace_fs_on;
+  a.fs_eps = c->cfg.ace_fs_eps;
+  a.dAb = reinterpret_cast<R*>(c->d_ace_dAb);
+  a.e12b = c->d_ace_e12b;
+  a.fs = c->d_ace_fs;
   a.rc2 = (R)(c->cfg.ace_rc * c->cfg.ace_rc);
   a.inv_rc = (R)(1.0 / c->cfg.ace_rc);
   a.inv_n0 = (R)(1.0 / c->cfg.ace_n0);
@@ -677,15 +749,20 @@ void run_ace(ap_ctx* c, const double* d_lam, const double* d_wgt, const int* d_q
   a.e12 = c->d_ace_e12;
   a.de3 = reinterpret_cast<R*>(c->d_ace_de3);
   a.e3 = c->d_ace_e3;
-  static Nu3Coef<R> P;
-  for (int t = 0; t < AP_NU3_N; ++t) P.c[t] = (R)c->ace.nu3_coef[t];
+  static Nu3Coef<R> P, Q;
+  for (int t = 0; t < AP_NU3_N; ++t) {
+    P.c[t] = (R)c->ace.nu3_coef[t];
+    Q.c[t] = (R)c->ace.nu3_coef2[t];
+  }
+  const bool fs = c->cfg.ace_fs_on != 0;
 
   const int pi = sizeof(R) == 4 ? 0 : 1;
-  static int b1[2] = {0, 0}, b3[2][2] = {{0, 0}, {0, 0}};
+  static int b1[2] = {0, 0}, b3[2][2][2] = {};
   const size_t s1 = basis_smem<R>(), s3 = adjoint_smem<R>();
   if (!b1[pi]) b1[pi] = resident_blocks(k_ace_basis<R>, kWarps<R> * 32, s1);
-  auto k3 = forces ? k_ace_adjoint<R, true> : k_ace_adjoint<R, false>;
-  if (!b3[pi][forces]) b3[pi][forces] = resident_blocks(k3, kWarps3<R> * 32, s3);
+  auto k3 = forces ? (fs ? k_ace_adjoint<R, true, true> : k_ace_adjoint<R, true, false>)
+                   : (fs ? k_ace_adjoint<R, false, true> : k_ace_adjoint<R, false, false>);
+  if (!b3[pi][forces][fs]) b3[pi][forces][fs] = resident_blocks(k3, kWarps3<R> * 32, s3);
   if (forces) {
     if constexpr (sizeof(R) == 4)
       cudaMemsetAsync(c->d_facc32, 0, sizeof(float4) * (size_t)c->n, s);
@@ -695,9 +772,12 @@ void run_ace(ap_ctx* c, const double* d_lam, const double* d_wgt, const int* d_q
   cudaMemsetAsync(a.counter, 0, 2 * sizeof(int), s);   // work_counter and work_counter2
   k_ace_basis<R><<<c->num_sms * b1[pi], kWarps<R> * 32, s1, s>>>(a);
   const int t2 = sizeof(R) == 4 ? 128 : 64;
-  k_ace_nu3<R><<<c->num_sms * (sizeof(R) == 4 ? 8 : 16), t2, 0, s>>>(a, P);
+  if (fs)
+    k_ace_nu3<R, true><<<c->num_sms * (sizeof(R) == 4 ? 8 : 16), t2, 0, s>>>(a, P, Q);
+  else
+    k_ace_nu3<R, false><<<c->num_sms * (sizeof(R) == 4 ? 8 : 16), t2, 0, s>>>(a, P, Q);
   const int t0 = prof_mark(c, s);
-  k3<<<c->num_sms * b3[pi][forces], kWarps3<R> * 32, s3, s>>>(a);
+  k3<<<c->num_sms * b3[pi][forces][fs], kWarps3<R> * 32, s3, s>>>(a);
   prof_add(c, AP_PHASE_ACE_ADJOINT, t0, prof_mark(c, s));
   c->kernels += 3;
 }
@@ -717,6 +797,8 @@ void upload_ace_tables(ap_ctx* c) {
   std::vector<double> p64(c->cfg.ace_W, c->cfg.ace_W + 320);
   p64.insert(p64.end(), t.m2.begin(), t.m2.end());
   p64.insert(p64.end(), t.c1.begin(), t.c1.end());
+  p64.insert(p64.end(), t.m2b.begin(), t.m2b.end());
+  p64.insert(p64.end(), t.c1b.begin(), t.c1b.end());
   std::vector<float> p32(p64.begin(), p64.end());
   cudaMalloc(&c->d_W32, sizeof(float) * p32.size());
   cudaMalloc(&c->d_W64, sizeof(double) * p64.size());
