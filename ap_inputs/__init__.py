@@ -92,6 +92,58 @@ EAM_NOMINAL = EAMParams(beta=3.0, alpha=1.6, A=0.42398, D=0.23925, rp=2.81322)
 
 
 @dataclasses.dataclass
+class MishinParams:
+    """Mishin EAM2 copper (the paper's Appendix E functional forms).  Field order is
+    the oracle's and the library's parameter order."""
+    E1: float
+    E2: float
+    delta: float
+    F0: float
+    xi0: float
+    xi2: float
+    h: float
+    q1: float
+    q2: float
+    q3: float
+    q4: float
+    Q1: float
+    Q2: float
+    S1: float
+    S2: float
+    S3: float
+    a: float
+    a1: float
+    a2: float
+    b1: float
+    b2: float
+    r01: float
+    r02: float
+    r03: float
+    r04: float
+    rs1: float
+    rs2: float
+    rs3: float
+    rc: float
+
+    def as_array(self) -> np.ndarray:
+        return np.array([getattr(self, f.name) for f in dataclasses.fields(self)])
+
+
+# The two parameter sets printed in the paper's table of the optimised EAM (Appendix E):
+# the original EAM2 values and the values fitted at 300 K to the ACE potential.
+MISHIN_ORIGINAL = MishinParams(
+    E1=2.01458e+02, E2=6.59288e-03, delta=8.62250e-03, F0=0.0, xi0=-2.30000, xi2=1.40000, h=5.00370e-01,
+    q1=-1.30000, q2=-9.00000e-01, q3=1.80000, q4=3.00000, Q1=4.00000e-01, Q2=3.00000e-01, S1=4.0, S2=40.0,
+    S3=1150.0, a=3.80362, a1=2.97758, a2=1.54927, b1=1.73940e-01, b2=5.35661e+02, r01=8.35910e-01,
+    r02=4.46867, r03=-2.19885, r04=-2.61984e+02, rs1=2.24, rs2=1.80, rs3=1.20, rc=5.50679)
+MISHIN_FIT_300K = MishinParams(
+    E1=2.01486e+02, E2=6.44057e-03, delta=2.18016e-02, F0=-1.50036e-01, xi0=-2.30089, xi2=1.39912, h=5.00370e-01,
+    q1=-1.29894, q2=-8.99672e-01, q3=1.79940, q4=2.99944, Q1=3.99178e-01, Q2=3.00455e-01, S1=4.0, S2=40.0,
+    S3=1150.0, a=3.80541, a1=2.96972, a2=1.55510, b1=1.66589e-01, b2=5.35661e+02, r01=8.36347e-01,
+    r02=4.46690, r03=-2.19834, r04=-2.61984e+02, rs1=2.24, rs2=1.80, rs3=1.20, rc=5.50679)
+
+
+@dataclasses.dataclass
 class ACEParams:
     """Single-species ACE: radial mixing W[l][n][k] and coefficients c[v] of phi^(1);
     with c2, the Finnis-Sinclair form E = phi^(1) + F(phi^(2)) (phi^(2) = sum c2_v B_v)."""

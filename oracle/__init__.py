@@ -61,6 +61,18 @@ class _EAM(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("beta", "alpha", "A", "D", "rp", "r0", "rc", "h")]
 
 
+_MISHIN_FIELDS = ("E1", "E2", "delta", "F0", "xi0", "xi2", "h", "q1", "q2", "q3", "q4", "Q1", "Q2", "S1", "S2",
+                  "S3", "a", "a1", "a2", "b1", "b2", "r01", "r02", "r03", "r04", "rs1", "rs2", "rs3", "rc")
+
+
+class _Mishin(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in _MISHIN_FIELDS]
+
+
+def _mishin(p) -> _Mishin:
+    return _Mishin(*[float(getattr(p, k)) for k in _MISHIN_FIELDS])
+
+
 _lib = None
 
 
@@ -82,6 +94,9 @@ def lib():
         _lib.orc_lambda_min.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int, P]
         _lib.orc_eam.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int, P, P, P, P, P, P]
         _lib.orc_eam_pair.argtypes = [P, ctypes.c_int, P, P, P, P, P]
+        _lib.orc_eam_mishin.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int, P, P, P, P, P, P]
+        _lib.orc_mishin_pair.argtypes = [P, ctypes.c_double, P, P, P, P]
+        _lib.orc_mishin_embed.argtypes = [P, ctypes.c_double, P, P]
         _lib.orc_ace_create.restype = P
         _lib.orc_ace_create.argtypes = [P, P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
         _lib.orc_ace_destroy.argtypes = [P]
@@ -279,6 +294,42 @@ def eam(x, box, p, weights=None, nl: Optional[NeighborList] = None):
     return e, f, rho, dxi
 
 
+def eam_mishin(x, box, p, weights=None, nl: Optional[NeighborList] = None):
+    """Mishin EAM2 site energies and F = -grad sum_i w_i E_i^f (Appendix E forms).
+    p: ap_inputs.MishinParams.  Returns (E, F, rho, xi'(rho))."""
+    x = _f64(x)
+    n = x.shape[0]
+    if nl is None:
+        nl = neighbors(x, box, p.rc)
+    e, f, rho, dxi = np.zeros(n), np.zeros((n, 3)), np.zeros(n), np.zeros(n)
+    w = None if weights is None else _f64(weights)
+    pp = _mishin(p)
+    lib().orc_eam_mishin(n, _p(x), ctypes.byref(_box(box)), _p(nl.cnt), _p(nl.j), _p(nl.s), nl.cap, ctypes.byref(pp),
+                         _p(w), _p(e), _p(f), _p(rho), _p(dxi))
+    return e, f, rho, dxi
+
+
+def mishin_terms(p, r: float):
+    """(Phi, Phi', zeta, zeta') of the Mishin EAM2 at distance r."""
+    out = [ctypes.c_double() for _ in range(4)]
+    lib().orc_mishin_pair(ctypes.byref(_mishin(p)), float(r), *[ctypes.byref(o) for o in out])
+    return tuple(o.value for o in out)
+
+
+def mishin_embed(p, x: float):
+    """(xi, xi') of the Mishin EAM2 at density x (including the fitted offset F0)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().orc_mishin_embed(ctypes.byref(_mishin(p)), float(x), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def eam_any(x, box, p, weights=None, nl: Optional[NeighborList] = None):
+    """EAM with either parameter type (analytic synthetic or Mishin EAM2)."""
+    if hasattr(p, "E1"):
+        return eam_mishin(x, box, p, weights, nl)
+    return eam(x, box, p, weights, nl)
+
+
 def eam_pair(p, r):
     """zeta(r), zeta'(r), Phi(r), Phi'(r) of the analytic EAM at the distances r."""
     r = _f64(r).reshape(-1)
@@ -405,7 +456,7 @@ def hybrid(x, box, lam, eam_p, ace: ACE):
     F = -grad sum_k [lam_k E_k^f + (1-lam_k) E_k^p] at fixed lam.
     Returns (E_site, F, E_fast, E_prec); E_prec is 0 where lam == 1."""
     lam = _f64(lam)
-    ef, ff, _, _ = eam(x, box, eam_p, weights=lam)
+    ef, ff, _, _ = eam_any(x, box, eam_p, weights=lam)
     w = 1.0 - lam
     ep, fp = ace.eval(x, box, weights=w)
     e = lam * ef + w * ep

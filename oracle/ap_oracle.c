@@ -353,6 +353,125 @@ static void eam_xi(const orc_eam_params* p, double rho, double* xi, double* dxi)
   *dxi = -p->A / (2.0 * s);
 }
 
+/* ------------------------------------------------------------------ Mishin EAM2 (Appendix E)
+ * Pair:      Phi(r) = (E1 M(r, r01, a1) + E2 M(r, r02, a2) + delta) psi((r - rc)/h)
+ *                     - sum_n Theta(rs_n - r) S_n (rs_n - r)^4,
+ *            M(r, r0, a) = exp(-2a(r - r0)) - 2 exp(-a(r - r0)), psi(x) = x^4/(1+x^4) for x < 0.
+ * Embedding: xi(x) = xi0 + xi2/2 (x-1)^2 + sum_{n=1..4} q_n (x-1)^(n+2)                 (x <= 1)
+ *            xi(x) = (xi0 + xi2/2 (x-1)^2 + q1 (x-1)^3 + Q1 (x-1)^4) / (1 + Q2 (x-1)^3)  (x > 1)
+ *            plus the fitted offset F0.
+ * Density:   zeta(r) = (a exp(-b1 (r - r03)^2) + exp(-b2 (r - r04))) psi((r - rc)/h); the second
+ *            exponent is evaluated only when it is above -700 (for the published r04, b2 it
+ *            underflows to 0 at every r > 0). */
+typedef struct {
+  double E1, E2, delta, F0, xi0, xi2, h, q1, q2, q3, q4, Q1, Q2, S1, S2, S3, a, a1, a2, b1, b2, r01, r02, r03, r04,
+      rs1, rs2, rs3, rc;
+} orc_mishin;
+
+static void morse(double r, double r0, double al, double* m, double* dm) {
+  double e1 = exp(-al * (r - r0));
+  *m = e1 * e1 - 2.0 * e1;
+  *dm = -2.0 * al * e1 * e1 + 2.0 * al * e1;
+}
+
+void orc_mishin_pair(const orc_mishin* p, double r, double* phi, double* dphi, double* z, double* dz) {
+  double u = (r - p->rc) / p->h;
+  double ps = psi(u), dps = dpsi(u) / p->h;
+  double m1, dm1, m2, dm2;
+  morse(r, p->r01, p->a1, &m1, &dm1);
+  morse(r, p->r02, p->a2, &m2, &dm2);
+  double core = p->E1 * m1 + p->E2 * m2 + p->delta;
+  double dcore = p->E1 * dm1 + p->E2 * dm2;
+  double ph = core * ps, dph = dcore * ps + core * dps;
+  const double rs[3] = {p->rs1, p->rs2, p->rs3}, S[3] = {p->S1, p->S2, p->S3};
+  for (int k = 0; k < 3; ++k)
+    if (rs[k] - r >= 0.0) {
+      double t = rs[k] - r;
+      ph -= S[k] * t * t * t * t;
+      dph += 4.0 * S[k] * t * t * t;
+    }
+  double g = exp(-p->b1 * (r - p->r03) * (r - p->r03));
+  double dg = -2.0 * p->b1 * (r - p->r03) * g;
+  double arg = -p->b2 * (r - p->r04);
+  double e2 = arg > -700.0 ? exp(arg) : 0.0;
+  double rho0 = p->a * g + e2, drho0 = p->a * dg - p->b2 * e2;
+  *phi = ph;
+  *dphi = dph;
+  *z = rho0 * ps;
+  *dz = drho0 * ps + rho0 * dps;
+}
+
+void orc_mishin_embed(const orc_mishin* p, double x, double* xi, double* dxi) {
+  double y = x - 1.0, y2 = y * y, y3 = y2 * y;
+  if (x <= 1.0) {
+    double y4 = y3 * y, y5 = y4 * y, y6 = y5 * y;
+    *xi = p->xi0 + 0.5 * p->xi2 * y2 + p->q1 * y3 + p->q2 * y4 + p->q3 * y5 + p->q4 * y6;
+    *dxi = p->xi2 * y + 3.0 * p->q1 * y2 + 4.0 * p->q2 * y3 + 5.0 * p->q3 * y4 + 6.0 * p->q4 * y5;
+  } else {
+    double num = p->xi0 + 0.5 * p->xi2 * y2 + p->q1 * y3 + p->Q1 * y3 * y;
+    double dnum = p->xi2 * y + 3.0 * p->q1 * y2 + 4.0 * p->Q1 * y3;
+    double den = 1.0 + p->Q2 * y3, dden = 3.0 * p->Q2 * y2;
+    *xi = num / den;
+    *dxi = (dnum * den - num * dden) / (den * den);
+  }
+  *xi += p->F0;
+}
+
+/* EAM site energies and weighted forces with the Mishin functions; same contract as orc_eam. */
+void orc_eam_mishin(int n, const double* x, const orc_box* b, const int* cnt, const int* jl, const int* sl, int cap,
+                    const orc_mishin* p, const double* wt, double* e_site, double* f, double* rho_out,
+                    double* dxi_out) {
+  double* dxi = (double*)malloc(sizeof(double) * (size_t)n);
+  double* gp = (double*)calloc((size_t)n * cap * 3, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int i = 0; i < n; ++i) {
+    double r_sum = 0.0, phi_sum = 0.0;
+    for (int q = 0; q < cnt[i]; ++q) {
+      int j = jl[(size_t)i * cap + q];
+      double d[3];
+      displacement(b, &x[3 * i], &x[3 * j], &sl[((size_t)i * cap + q) * 3], d);
+      double r = sqrt(norm2(d));
+      if (r >= p->rc) continue;
+      double ph, dph, z, dz;
+      orc_mishin_pair(p, r, &ph, &dph, &z, &dz);
+      r_sum += z;
+      phi_sum += ph;
+    }
+    double xi, dx;
+    orc_mishin_embed(p, r_sum, &xi, &dx);
+    if (rho_out) rho_out[i] = r_sum;
+    dxi[i] = dx;
+    e_site[i] = xi + 0.5 * phi_sum;
+    for (int q = 0; q < cnt[i]; ++q) {
+      int j = jl[(size_t)i * cap + q];
+      double d[3];
+      displacement(b, &x[3 * i], &x[3 * j], &sl[((size_t)i * cap + q) * 3], d);
+      double r = sqrt(norm2(d));
+      if (r >= p->rc) continue;
+      double ph, dph, z, dz;
+      orc_mishin_pair(p, r, &ph, &dph, &z, &dz);
+      double g = dx * dz + 0.5 * dph;
+      for (int k = 0; k < 3; ++k) gp[((size_t)i * cap + q) * 3 + k] = g * d[k] / r;
+    }
+  }
+  for (int k = 0; k < 3 * n; ++k) f[k] = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double w = wt ? wt[i] : 1.0;
+    if (w == 0.0) continue;
+    for (int q = 0; q < cnt[i]; ++q) {
+      int j = jl[(size_t)i * cap + q];
+      for (int k = 0; k < 3; ++k) {
+        double g = gp[((size_t)i * cap + q) * 3 + k];
+        f[3 * j + k] -= w * g;
+        f[3 * i + k] += w * g;
+      }
+    }
+  }
+  if (dxi_out) memcpy(dxi_out, dxi, sizeof(double) * (size_t)n);
+  free(dxi);
+  free(gp);
+}
+
 /* zeta, zeta', Phi, Phi' at m distances (the selector features use the pair terms). */
 void orc_eam_pair(const orc_eam_params* p, int m, const double* r, double* z, double* dz, double* ph, double* dph) {
   for (int k = 0; k < m; ++k) {
