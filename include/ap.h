@@ -59,6 +59,9 @@ typedef int32_t ap_status;
 #define AP_SEL_NHID 64       /* hidden width of the selector MLP                        */
 #define AP_SEL_NPARAMS 5825  /* 24*64 + 64 + 64*64 + 64 + 64 + 1                        */
 
+#define AP_EAM_ANALYTIC 0   /* eam_type: the analytic synthetic EAM (eam_beta .. eam_h)     */
+#define AP_EAM_MISHIN 1     /* eam_type: Mishin EAM2 copper (Appendix E), eam_mishin[]      */
+
 #define AP_FCUT_PRINTED 0   /* f_cut(x) = 1 - 1.875x + 1.25x^3 - 0.375x^5 as printed    */
 #define AP_FCUT_C2 1        /* C2-symmetric reading 0.5*p(2x-1)                         */
 
@@ -139,6 +142,21 @@ typedef struct {
   int32_t ace_fs_on;
   double ace_fs_eps;
   double ace_c2[512];
+  /* Fast potential.  AP_EAM_ANALYTIC: the analytic forms above.  AP_EAM_MISHIN: the
+   * EAM2 forms of Appendix E with
+   *   Phi(r)  = (E1 M(r; r01, a1) + E2 M(r; r02, a2) + delta) psi((r - rc)/h)
+   *             - sum_{n=1..3} [r <= rs_n] S_n (rs_n - r)^4,
+   *             M(r; r0, a) = exp(-2a(r - r0)) - 2 exp(-a(r - r0)),
+   *   zeta(r) = (a exp(-b1 (r - r03)^2) + exp(-b2 (r - r04))) psi((r - rc)/h),
+   *   xi(x)   = F0 + xi0 + xi2/2 y^2 + q1 y^3 + q2 y^4 + q3 y^5 + q4 y^6   (x <= 1),
+   *           = F0 + (xi0 + xi2/2 y^2 + q1 y^3 + Q1 y^4)/(1 + Q2 y^3)    (x > 1),  y = x - 1,
+   * and eam_mishin holding E1, E2, delta, F0, xi0, xi2, h, q1, q2, q3, q4, Q1, Q2,
+   * S1, S2, S3, a, a1, a2, b1, b2, r01, r02, r03, r04, rs1, rs2, rs3, rc in that order
+   * (eV, Angstrom).  The EAM neighbour rows still use eam_rc + skin, so eam_rc must be
+   * >= the Mishin rc; eam_beta .. eam_h other than eam_rc are then unused.  The
+   * selector detector and ap_eval_eam_static accept AP_EAM_ANALYTIC only. */
+  int32_t eam_type;
+  double eam_mishin[29];
 } ap_config;
 
 typedef struct ap_ctx ap_ctx;
@@ -317,7 +335,9 @@ ap_status ap_sel_get_model(ap_ctx* ctx, float* h_params, float* h_mu, float* h_i
 /* Raw features d_feat [n][24] FP32 of every atom at positions d_x.  Requires
  * ap_build_neighbors on the same n and positions.  Computes the CSP sample of
  * every changeable atom (d_changeable as in ap_classify) on the way, which
- * replaces the one ap_get_lambda_state returns. */
+ * replaces the one ap_get_lambda_state returns.  Errors: AP_ERR_STATE without
+ * neighbours, AP_ERR_ARG with eam_type other than AP_EAM_ANALYTIC (the features
+ * are the analytic EAM's pair terms). */
 ap_status ap_sel_features(ap_ctx* ctx, int64_t n, const double* d_x, const uint8_t* d_changeable, float* d_feat,
                           void* stream);
 
@@ -358,7 +378,8 @@ ap_status ap_sel_get_grad(ap_ctx* ctx, float* h_grad, float* h_loss);
  * race: serialise them.  The first call on each device looks up the array's
  * device address (with that device current); make that first call before any
  * stream capture.  Errors: AP_ERR_ARG for n > 32768, n < 0, null pointers or a
- * bad box/config; AP_ERR_CUDA if the address lookup or a launch fails. */
+ * bad box/config (including eam_type other than AP_EAM_ANALYTIC); AP_ERR_CUDA if
+ * the address lookup or a launch fails. */
 ap_status ap_eval_eam_static(const ap_config* h_cfg, int64_t n, const double* d_x, const ap_box* h_box,
                              const double* d_lam, double* d_e_fast, double* d_f, void* stream);
 

@@ -7,12 +7,12 @@ from .api import (Context, StepStats, ace_basis_desc, ace_gaunt, ace_nbasis, ap_
                   ap_classify, ap_create, ap_eval_ace, ap_eval_eam, ap_sel_features, ap_sel_get_grad,
                   ap_sel_get_model, ap_sel_predict, ap_sel_set_model, ap_sel_train_step, ap_step, make_box,
                   make_config)
-from ._native import (ApConfig, ApError, DETECT_CSP, DETECT_SELECTOR, PREC_FP64, PREC_MIXED, SEL_NFEAT,
-                      SEL_NPARAMS)
+from ._native import (ApConfig, ApError, DETECT_CSP, DETECT_SELECTOR, EAM_ANALYTIC, EAM_MISHIN, PREC_FP64,
+                      PREC_MIXED, SEL_NFEAT, SEL_NPARAMS)
 from . import autograd
 
 __all__ = ["Context", "StepStats", "ApConfig", "ApError", "PREC_FP64", "PREC_MIXED", "DETECT_CSP",
-           "DETECT_SELECTOR", "SEL_NFEAT", "SEL_NPARAMS", "make_box", "make_config", "ace_nbasis",
+           "DETECT_SELECTOR", "EAM_ANALYTIC", "EAM_MISHIN", "SEL_NFEAT", "SEL_NPARAMS", "make_box", "make_config", "ace_nbasis",
            "ace_basis_desc", "ace_gaunt", "ap_create", "ap_build_neighbors", "ap_classify", "ap_eval_eam",
            "ap_eval_ace", "ap_blend_forces", "ap_step", "ap_sel_set_model", "ap_sel_get_model", "ap_sel_features",
            "ap_sel_predict", "ap_sel_train_step", "ap_sel_get_grad", "autograd"]

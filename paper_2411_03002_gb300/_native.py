@@ -18,6 +18,8 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 DETECT_CSP = 0
 DETECT_SELECTOR = 1
+EAM_ANALYTIC = 0
+EAM_MISHIN = 1
 SEL_NFEAT = 24
 SEL_NPARAMS = 5825
 F32 = ctypes.c_float
@@ -35,7 +37,8 @@ class ApConfig(ctypes.Structure):
                    ("cap_ace", I32), ("precision", I32), ("dt", F64), ("lambda_every", I32), ("indenter_on", I32),
                    ("ind_c0", F64 * 3), ("ind_v", F64 * 3), ("ind_R", F64), ("ind_k", F64),
                    ("rebuild_every", I32), ("detector", I32), ("sel_p_lo", F64), ("sel_p_hi", F64),
-                   ("thermostat_on", I32), ("ace_fs_on", I32), ("ace_fs_eps", F64), ("ace_c2", F64 * 512)])
+                   ("thermostat_on", I32), ("ace_fs_on", I32), ("ace_fs_eps", F64), ("ace_c2", F64 * 512),
+                   ("eam_type", I32), ("eam_mishin", F64 * 29)])
 
 
 class ApStepStats(ctypes.Structure):

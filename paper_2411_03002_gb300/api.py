@@ -46,10 +46,20 @@ def make_config(eam, ace, hyb, precision: int = N.PREC_MIXED, skin: float = 1.0,
     """Fill an ap_config from parameter objects with the attribute names of
     the EAM (beta, alpha, A, D, rp, r0, rc, h), ACE (W, c, rc, n0) and switching
     (csp_lo, csp_hi, r_lo, r_hi, dlam_min, n_csp_avg, n_lam_avg, fcut_mode,
-    sample_every) parameter sets."""
+    sample_every) parameter sets.  An EAM object with the 29 Mishin EAM2
+    parameters (E1 .. rc, Appendix E; ap_inputs.MishinParams) selects that potential."""
     c = ApConfig()
-    for k in ("beta", "alpha", "A", "D", "rp", "r0", "rc", "h"):
-        setattr(c, "eam_" + k, float(getattr(eam, k)))
+    if hasattr(eam, "E1"):
+        m = np.asarray(eam.as_array(), dtype=np.float64)
+        if m.size != 29:
+            raise ValueError("Mishin EAM2 needs 29 parameters")
+        c.eam_type = N.EAM_MISHIN
+        for i in range(29):
+            c.eam_mishin[i] = m[i]
+        c.eam_rc, c.eam_h = float(eam.rc), float(eam.h)
+    else:
+        for k in ("beta", "alpha", "A", "D", "rp", "r0", "rc", "h"):
+            setattr(c, "eam_" + k, float(getattr(eam, k)))
     W = np.ascontiguousarray(ace.W, dtype=np.float64).reshape(-1)
     if W.size != 320:
         raise ValueError("ACE W must have 5*8*8 entries")

@@ -43,7 +43,15 @@ ap_status validate(const ap_config& g, std::string& why) {
     why = m;
     return AP_ERR_ARG;
   };
-  if (!(g.eam_rc > 0 && g.eam_h > 0 && g.eam_r0 > 0)) return bad("EAM cutoff, h and r0 must be positive");
+  if (g.eam_type != AP_EAM_ANALYTIC && g.eam_type != AP_EAM_MISHIN) return bad("unknown eam_type");
+  if (g.eam_type == AP_EAM_ANALYTIC && !(g.eam_rc > 0 && g.eam_h > 0 && g.eam_r0 > 0))
+    return bad("EAM cutoff, h and r0 must be positive");
+  if (g.eam_type == AP_EAM_MISHIN) {
+    const double h = g.eam_mishin[6], rc = g.eam_mishin[28];
+    if (!(h > 0 && rc > 0)) return bad("Mishin h and rc must be positive");
+    if (!(g.eam_rc >= rc)) return bad("eam_rc must be >= the Mishin rc (it sets the EAM rows)");
+    if (g.detector == AP_DETECT_SELECTOR) return bad("the selector detector needs eam_type AP_EAM_ANALYTIC");
+  }
   if (!(g.ace_rc > 0 && g.ace_n0 > 0)) return bad("ACE cutoff and N0 must be positive");
   if (!(g.skin >= 0)) return bad("skin must be >= 0");
   if (!(g.csp_hi > g.csp_lo)) return bad("csp_hi must exceed csp_lo");
@@ -935,6 +943,7 @@ ap_status ap_sel_features(ap_ctx* c, int64_t n, const double* d_x, const uint8_t
                           void* stream) {
   if (!c) return AP_ERR_ARG;
   if (!c->built || n != c->n) return fail(c, AP_ERR_STATE, "ap_sel_features needs ap_build_neighbors on the same atoms");
+  if (c->cfg.eam_type != AP_EAM_ANALYTIC) return fail(c, AP_ERR_ARG, "selector features need eam_type AP_EAM_ANALYTIC");
   if (n == 0) return AP_OK;
   if (!d_x || !d_feat) return fail(c, AP_ERR_ARG, "null argument");
   ap_status st = ensure_sel_feat(c, n);

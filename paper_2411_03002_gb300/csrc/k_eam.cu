@@ -6,8 +6,8 @@
 //            g_ij = (lambda_i xi'_i + lambda_j xi'_j) zeta'(r_ij) + (lambda_i + lambda_j)/2 Phi'(r_ij),
 //            which is -grad_i sum_k lambda_k E_k^(f) gathered without atomics;
 //            E_i^(f) = xi_i + 1/2 sum_j Phi(r_ij)  (the Phi sum reduced in FP64).
-// Analytic forms: zeta(r) = exp(-beta (r/r0 - 1)) psi, Phi(r) = D (e^{-2a(r-rp)} -
-// 2 e^{-a(r-rp)}) psi, xi(rho) = -A sqrt(rho), psi = u^4/(1+u^4), u = (r - rc)/h < 0.
+// The potential P is a functor (eam_frame.cuh): the analytic synthetic EAM or the
+// Mishin EAM2 of Appendix E, selected by ap_config.eam_type.
 //
 // Pair displacements come from cell-relative shadows: d = k h + s_j - s_i with k
 // the pair's cell offset, either stored per entry (small periodic boxes) or
@@ -19,12 +19,12 @@ namespace ap {
 
 namespace {
 
-template <typename R, int G, bool STORED>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? AP_EAM_MINB : 1) k_eam_density(int n, const SysInfo* __restrict__ sys,
+template <typename R, int G, bool STORED, typename P>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam_density(int n, const SysInfo* __restrict__ sys,
                                                      const int* __restrict__ atom_sys,
                                                      const typename Shadow<R>::T* __restrict__ sh,
                                                      const int* __restrict__ nbr, const int* __restrict__ off,
-                                                     const int* __restrict__ cnt, int cap, EamP<R> p,
+                                                     const int* __restrict__ cnt, int cap, P p,
                                                      const double* __restrict__ lam,
                                                      typename Q2<R>::T* __restrict__ q, double* __restrict__ xi_out) {
   const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -44,33 +44,25 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? AP_EAM_MINB : 1) k_eam_d
     fr.disp(sj, off, row + t, d);
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     if (r2 < p.rc2) {
-      const R r = r2 * rsqrt_(r2);
-      const R u = (r - p.rc) * p.inv_h;
-      const R u2 = u * u;
-      const R u4 = u2 * u2;
-      rho += rexp(p.beta - p.beta_r0 * r) * (u4 * rcp_(R(1) + u4));
+      rho += p.zeta(r2 * rsqrt_(r2));
     }
   }
   rho = group_sum<R, G>(rho);
   if (active && sub == 0) {
     const R li = lam ? (R)lam[i] : R(1);
-    R xi = R(0), dxi = R(0);
-    if (rho > R(0)) {
-      const R s = sqrt(rho);
-      xi = -p.A * s;
-      dxi = R(-0.5) * p.A * rcp_(s);
-    }
+    R xi, dxi;
+    p.embed(rho, xi, dxi);
     q[i] = Q2<R>::make(li * dxi, li);
     xi_out[i] = (double)xi;
   }
 }
 
-template <typename R, int G, bool STORED>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? AP_EAM_MINB : 1) k_eam_force(int n, const SysInfo* __restrict__ sys,
+template <typename R, int G, bool STORED, typename P>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam_force(int n, const SysInfo* __restrict__ sys,
                                                    const int* __restrict__ atom_sys,
                                                    const typename Shadow<R>::T* __restrict__ sh,
                                                    const int* __restrict__ nbr, const int* __restrict__ off,
-                                                   const int* __restrict__ cnt, int cap, EamP<R> p,
+                                                   const int* __restrict__ cnt, int cap, P p,
                                                    const typename Q2<R>::T* __restrict__ q,
                                                    const double* __restrict__ xi, double* __restrict__ e_fast,
                                                    double* __restrict__ f, int accumulate) {
@@ -95,20 +87,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? AP_EAM_MINB : 1) k_eam_f
     if (r2 < p.rc2) {
       const R inv_r = rsqrt_(r2);
       const R r = r2 * inv_r;
-      const R u = (r - p.rc) * p.inv_h;
-      const R u2 = u * u;
-      const R u4 = u2 * u2;
-      const R inv = rcp_(R(1) + u4);
-      const R ps = u4 * inv;
-      const R dps = R(4) * u2 * u * inv * inv * p.inv_h;
-      const R ez = rexp(p.beta - p.beta_r0 * r);
-      const R dzeta = ez * (dps - p.beta_r0 * ps);
-      const R e1 = rexp(-p.alpha * (r - p.rp));
-      const R e2 = e1 * e1;
-      const R m = p.D * (e2 - R(2) * e1);
-      const R dm = R(2) * p.alpha * p.D * (e1 - e2);
-      const R dphi = dm * ps + m * dps;
-      phi += m * ps;
+      R dzeta, ph, dphi;
+      p.pair(r, dzeta, ph, dphi);
+      phi += ph;
       const R g = (qi.x + qj.x) * dzeta + R(0.5) * (qi.y + qj.y) * dphi;
       const R s = g * inv_r;
       fx += s * d[0];
@@ -134,38 +115,48 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? AP_EAM_MINB : 1) k_eam_f
   }
 }
 
-template <typename R, bool STORED>
-void run_eam(ap_ctx* c, const typename Shadow<R>::T* sh, const double* d_lam, double* d_e_fast, double* d_f,
-             bool accumulate, cudaStream_t s) {
+template <typename R, bool STORED, typename P>
+void run_eam(ap_ctx* c, const P& p, const typename Shadow<R>::T* sh, const double* d_lam, double* d_e_fast,
+             double* d_f, bool accumulate, cudaStream_t s) {
   constexpr int G = AP_EAM_LANES;
   const int threads = 256;
   int blocks = (int)((c->n * G + threads - 1) / threads);
-  EamP<R> p = make_params<R>(c->cfg);
   auto* q = reinterpret_cast<typename Q2<R>::T*>(c->d_q);
   const int* off = STORED ? c->d_off_eam : nullptr;
-  k_eam_density<R, G, STORED><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam,
+  k_eam_density<R, G, STORED, P><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam,
                                                          off, c->d_cnt_eam, c->cap_eam, p, d_lam, q, c->d_xi);
-  k_eam_force<R, G, STORED><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam, off,
+  k_eam_force<R, G, STORED, P><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam, off,
                                                        c->d_cnt_eam, c->cap_eam, p, q, c->d_xi, d_e_fast, d_f,
                                                        accumulate ? 1 : 0);
   c->kernels += 2;
+}
+
+template <typename R>
+void run_eam_pot(ap_ctx* c, const typename Shadow<R>::T* sh, const double* d_lam, double* d_e_fast, double* d_f,
+                 bool accumulate, cudaStream_t s) {
+  if (c->cfg.eam_type == AP_EAM_MISHIN) {
+    const PotMishin<R> p = make_mishin<R>(c->cfg);
+    if (c->stored_off)
+      run_eam<R, true>(c, p, sh, d_lam, d_e_fast, d_f, accumulate, s);
+    else
+      run_eam<R, false>(c, p, sh, d_lam, d_e_fast, d_f, accumulate, s);
+  } else {
+    const PotSynth<R> p = make_synth<R>(c->cfg);
+    if (c->stored_off)
+      run_eam<R, true>(c, p, sh, d_lam, d_e_fast, d_f, accumulate, s);
+    else
+      run_eam<R, false>(c, p, sh, d_lam, d_e_fast, d_f, accumulate, s);
+  }
 }
 
 }  // namespace
 
 void launch_eam(ap_ctx* c, const double* d_lam, double* d_e_fast, double* d_f, bool accumulate, cudaStream_t s) {
   if (c->n <= 0) return;
-  if (c->cfg.precision == AP_PREC_FP64) {
-    if (c->stored_off)
-      run_eam<double, true>(c, c->d_sh64, d_lam, d_e_fast, d_f, accumulate, s);
-    else
-      run_eam<double, false>(c, c->d_sh64, d_lam, d_e_fast, d_f, accumulate, s);
-  } else {
-    if (c->stored_off)
-      run_eam<float, true>(c, c->d_sh32, d_lam, d_e_fast, d_f, accumulate, s);
-    else
-      run_eam<float, false>(c, c->d_sh32, d_lam, d_e_fast, d_f, accumulate, s);
-  }
+  if (c->cfg.precision == AP_PREC_FP64)
+    run_eam_pot<double>(c, c->d_sh64, d_lam, d_e_fast, d_f, accumulate, s);
+  else
+    run_eam_pot<float>(c, c->d_sh32, d_lam, d_e_fast, d_f, accumulate, s);
 }
 
 }  // namespace ap

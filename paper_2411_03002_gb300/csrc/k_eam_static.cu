@@ -151,6 +151,7 @@ extern "C" ap_status ap_eval_eam_static(const ap_config* h_cfg, int64_t n, const
   if (n == 0) return AP_OK;
   if (!d_x || !d_e_fast || !d_f) return AP_ERR_ARG;
   const ap_config& c = *h_cfg;
+  if (c.eam_type != AP_EAM_ANALYTIC) return AP_ERR_ARG;
   if (!(c.eam_rc > 0 && c.eam_h > 0 && c.eam_r0 > 0)) return AP_ERR_ARG;
   StaticBox b;
   for (int d = 0; d < 3; ++d) {

@@ -33,11 +33,14 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_struct_layouts_match_header(tmp_path):
+    """sizeof of the three structs and offsetof of every ap_config and ap_step_stats
+    field agree between the header and the ctypes binding."""
+    fields = [("ap_config", N.ApConfig, f[0]) for f in N.ApConfig._fields_]
+    fields += [("ap_step_stats", N.ApStepStats, f[0]) for f in N.ApStepStats._fields_]
+    body = 'printf("%zu %zu %zu\\n", sizeof(ap_config), sizeof(ap_box), sizeof(ap_step_stats));'
+    body += "".join(f'printf("%zu\\n", offsetof({t}, {k}));' for t, _, k in fields)
     prog = tmp_path / "sz.c"
-    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ap.h"\nint main(){'
-                    'printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ap_config), sizeof(ap_box), sizeof(ap_step_stats),'
-                    ' offsetof(ap_config, ace_nc), offsetof(ap_config, dt), offsetof(ap_config, ind_k),'
-                    ' offsetof(ap_config, detector), offsetof(ap_config, sel_p_hi));return 0;}')
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ap.h"\nint main(){' + body + "return 0;}")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
@@ -45,11 +48,8 @@ def test_struct_layouts_match_header(tmp_path):
     assert sz[0] == ctypes.sizeof(N.ApConfig)
     assert sz[1] == ctypes.sizeof(N.ApBox)
     assert sz[2] == ctypes.sizeof(N.ApStepStats)
-    assert sz[3] == N.ApConfig.ace_nc.offset
-    assert sz[4] == N.ApConfig.dt.offset
-    assert sz[5] == N.ApConfig.ind_k.offset
-    assert sz[6] == N.ApConfig.detector.offset
-    assert sz[7] == N.ApConfig.sel_p_hi.offset
+    for (t, cls, k), off in zip(fields, sz[3:]):
+        assert getattr(cls, k).offset == off, (t, k)
 
 
 def test_basis_enumeration_matches_oracle():
