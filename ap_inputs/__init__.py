@@ -16,6 +16,8 @@ Workloads (all copper-like FCC, a = 3.615 A):
         0, 1 and U(0,1); plus a batch of 64 cells of 4*n1*n2*n3 atoms.
   * c5  100x100x100 slab (4,000,000 atoms), bottom 3 (200) layers fixed, a
         spherical indenter (R = 50 A, k = 10 eV/A^3, 20 m/s) above the top surface.
+  * c6  indented-slab snapshot of the c5 geometry (crater, graded disorder, vacancies,
+        thermal noise) for the switching-zone parameter study.
 """
 from __future__ import annotations
 
@@ -342,6 +344,36 @@ def config_c5(ncell: int = 100, hyb: HybridParams = HYB2, T: float = 300.0, nxy:
     ind = Indenter(center0=np.array([nx * A_CU / 2, ny * A_CU / 2, ztop + R]),
                    velocity=np.array([0.0, 0.0, -2.0e-4]), radius=R, k=10.0)
     return Workload(f"c5_indent{ncell}", x, box, mass, fixed, v=v, indenter=ind, hyb=hyb)
+
+
+def config_c6(nxy: int = 100, nz: int = 100, depth: float = 8.0) -> Workload:
+    """Indented-slab snapshot for the switching-zone parameter study (a stand-in for the
+    paper's nanoindentation snapshot with dislocations): the c5 slab geometry with
+    - the atoms inside the R = 50 A indenter sphere, its tip `depth` below the surface, removed;
+    - a graded disordered zone under the contact: extra Gaussian displacement of width
+      0.3 exp(-d / 12 A) for atoms within d < 40 A of the contact point;
+    - 0.2 % of the atoms within 45 A of the contact point removed (vacancies);
+    - thermal Gaussian displacement of width 0.06 A on every mobile atom.
+    Bottom three (200) layers fixed; no velocities (a single-step study).  4,000,000
+    lattice sites at nxy = nz = 100."""
+    g = rng_for(6, 0)
+    x = fcc_lattice(nxy, nxy, nz)
+    box = _slab_box(nxy, nxy, nz)
+    ztop = (nz - 0.5) * A_CU
+    R = 50.0
+    contact = np.array([nxy * A_CU / 2, nxy * A_CU / 2, ztop - depth])
+    centre = contact + np.array([0.0, 0.0, R])
+    keep = np.linalg.norm(x - centre, axis=1) >= R
+    d = np.linalg.norm(x - contact, axis=1)
+    keep &= ~((d < 45.0) & (g.uniform(size=x.shape[0]) < 0.002))
+    x, d = x[keep], d[keep]
+    fixed = (x[:, 2] < 1.25 * A_CU).astype(np.uint8)
+    mobile = fixed == 0
+    sig = np.where(mobile, 0.06, 0.0)
+    sig = np.where(mobile & (d < 40.0), np.hypot(sig, 0.3 * np.exp(-d / 12.0)), sig)
+    x = x + sig[:, None] * g.standard_normal(x.shape)
+    n = x.shape[0]
+    return Workload(f"c6_snapshot{nxy}x{nz}", x, box, np.full(n, MASS_CU), fixed, hyb=HYB1)
 
 
 # ----------------------------------------------------------------------------- selector data (c4)
