@@ -17,10 +17,9 @@
 //   k_ace_nu3      one lane per precise atom: the nu = 3 energy and gradient with A
 //                  and dE/dA in registers, straight-line code over the merged
 //                  monomials generated from the basis (ace_nu3.inc);
-//   k_ace_adjoint  persistent warps over the stream of in-range pairs of their atoms:
-//                  u = W^T dE/dA / N0 per atom; lanes recompute g, g', Y, grad Y per
-//                  pair, contract with its atom's u, and scatter -w_i p_ij to
-//                  neighbour j and +w_i sum p to i.
+//   k_ace_adjoint  one warp per precise atom: u = W^T dE/dA / N0; lanes recompute g,
+//                  g', Y, grad Y per in-range neighbour, contract with u, and scatter
+//                  -w_i p_ij to neighbour j and +w_i sum p to i.
 #include <complex>
 #include <algorithm>
 #include <cstring>
@@ -587,106 +586,56 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 128 : 64) k_ace_nu3(AceArgs<R
   }
 }
 
-// Kernel 3 (persistent warps): E_i = E12 + E3 -> e_prec, then the forces.  Each warp
-// keeps a ring of up to kRing precise atoms in shared memory, each with
-// u_klm = (1/N0) sum_n W[l][n][k] dE/dA_nlm, its weight and its range in the warp's
-// stream of in-range pairs (the atoms' compacted rows, one after the other).  The
-// 32 lanes take 32 consecutive pairs of that stream, so a window runs on into the
-// next atom instead of idling at the end of a row: each lane recomputes g, g', Y,
-// grad Y for its pair, contracts with its atom's u and scatters -w_i p_ij to j; the
-// lanes of each atom in the window then reduce +w_i sum_j p_ij for atom i.
-constexpr int kRing = 4;
-
-template <typename R, bool FS>
-__device__ inline void adjoint_load_u(const AceArgs<R>& a, int q, const R* __restrict__ Ws, R* __restrict__ dA,
-                                      R* __restrict__ U, int lane) {
-  if (FS) {
-    const R fp = (R)a.fs[2 * (size_t)q + 1];
-    for (int o = lane; o < 200; o += 32) dA[o] = fma(fp, a.dAb[(size_t)q * 200 + o], a.dA[(size_t)q * 200 + o]);
-  } else {
-    for (int o = lane; o < 200; o += 32) dA[o] = a.dA[(size_t)q * 200 + o];
-  }
-  __syncwarp();
-  for (int v = lane; v < 48; v += 32) dA[(v >> 4) * 25 + (v & 15)] += a.de3[(size_t)q * 48 + v];
-  __syncwarp();
-  for (int o = lane; o < 200; o += 32) {
-    const int lm = o >> 3, k = o & 7, l = l_of(lm);
-    R s = R(0);
-#pragma unroll
-    for (int n = 0; n < 8; ++n) s += Ws[(l * 8 + n) * 8 + k] * dA[n * 25 + lm];
-    U[o] = s * a.inv_n0;
-  }
-  __syncwarp();
-}
-
+// Kernel 3, one warp per precise atom (persistent): E_i = E12 + E3 -> e_prec, then
+// u_klm = (1/N0) sum_n W[l][n][k] dE/dA_nlm and the forces: lanes recompute g, g',
+// Y, grad Y per in-range neighbour (from the kept row positions), contract with u
+// and scatter -w_i p_ij to neighbour j, +w_i sum_j p_ij to i.
 template <typename R, bool FORCES, bool FS>
 __global__ void __launch_bounds__(kWarps3<R> * 32, sizeof(R) == 4 ? AP_ACE3_MINB : 1) k_ace_adjoint(AceArgs<R> a) {
-  // Shared memory: W [320] | per warp: dA [200] | U [kRing][200]
+  // Shared memory: W [320] | per warp: dA [200] | U [200]
   extern __shared__ __align__(128) unsigned char smem_raw[];
   R* Ws = reinterpret_cast<R*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  R* dA = Ws + 320 + warp * (200 + kRing * 200);
-  R* Uring = dA + 200;
-  __shared__ int s_i[kWarps3<R>][kRing], s_q[kWarps3<R>][kRing], s_beg[kWarps3<R>][kRing], s_end[kWarps3<R>][kRing];
-  __shared__ R s_w[kWarps3<R>][kRing];
+  R* dA = Ws + 320 + warp * 400;
+  R* U = dA + 200;
   for (int t = threadIdx.x; t < 320; t += blockDim.x) Ws[t] = a.W[t];
   __syncthreads();
   const int m = *a.count;
-  if (!FORCES) {
-    while (true) {
-      int q = 0;
-      if (lane == 0) q = atomicAdd(a.counter2, 1);
-      q = __shfl_sync(0xffffffffu, q, 0);
-      if (q >= m) break;
-      if (lane == 0) {
-        const int i = a.queue[q];
-        a.e_prec[i] = a.e12[q] + a.e3[q] + (FS ? a.fs[2 * (size_t)q] : 0.0);
-      }
-    }
-    return;
-  }
-  int head = 0, tail = 0, pos = 0;   // ring atoms [head, tail); stream position of the window
-  bool more = true;
   while (true) {
-    // refill until the loaded pairs cover the window (or the ring is full / no atoms left)
-    while (more && tail - head < kRing && (tail == head || s_end[warp][(tail - 1) % kRing] < pos + 32)) {
-      int q = 0;
-      if (lane == 0) q = atomicAdd(a.counter2, 1);
-      q = __shfl_sync(0xffffffffu, q, 0);
-      if (q >= m) {
-        more = false;
-        break;
-      }
-      const int i = a.queue[q];
-      if (lane == 0) a.e_prec[i] = a.e12[q] + a.e3[q] + (FS ? a.fs[2 * (size_t)q] : 0.0);
-      const int rs = tail % kRing;
-      adjoint_load_u<R, FS>(a, q, Ws, dA, Uring + rs * 200, lane);
-      const int beg = tail == head ? pos : s_end[warp][(tail - 1) % kRing];
-      if (lane == 0) {
-        s_i[warp][rs] = i;
-        s_q[warp][rs] = q;
-        s_beg[warp][rs] = beg;
-        s_end[warp][rs] = beg + a.nin[q];
-        s_w[warp][rs] = (R)(a.wgt ? a.wgt[i] : 1.0 - (a.lam ? a.lam[i] : 0.0));
-      }
-      __syncwarp();
-      ++tail;
+    int q = 0;
+    if (lane == 0) q = atomicAdd(a.counter2, 1);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= m) break;
+    const int i = a.queue[q];
+    if (lane == 0) a.e_prec[i] = a.e12[q] + a.e3[q] + (FS ? a.fs[2 * (size_t)q] : 0.0);
+    if (!FORCES) continue;
+    if (FS) {
+      const R fp = (R)a.fs[2 * (size_t)q + 1];
+      for (int o = lane; o < 200; o += 32) dA[o] = fma(fp, a.dAb[(size_t)q * 200 + o], a.dA[(size_t)q * 200 + o]);
+    } else {
+      for (int o = lane; o < 200; o += 32) dA[o] = a.dA[(size_t)q * 200 + o];
     }
-    if (head == tail) break;
-    const int stream_end = s_end[warp][(tail - 1) % kRing];
-    const int p = pos + lane;
-    int at = head;   // this lane's ring atom: the first whose range ends after p
-    while (at < tail - 1 && s_end[warp][at % kRing] <= p) ++at;
-    const int rs = at % kRing;
-    R px = R(0), py = R(0), pz = R(0);
-    if (p < stream_end) {
-      const int i = s_i[warp][rs], q = s_q[warp][rs];
-      const R wgt = s_w[warp][rs];
-      const R* U = Uring + rs * 200;
-      const SysInfo& S = a.sys[a.atom_sys ? a.atom_sys[i] : 0];
-      const auto si = a.sh[i];
-      const size_t row = (size_t)q * a.cap;
-      const int ent = a.slots[(size_t)q * kListCap + (p - s_beg[warp][rs])];
+    __syncwarp();
+    for (int v = lane; v < 48; v += 32) dA[(v >> 4) * 25 + (v & 15)] += a.de3[(size_t)q * 48 + v];
+    __syncwarp();
+    for (int o = lane; o < 200; o += 32) {
+      const int lm = o >> 3, k = o & 7, l = l_of(lm);
+      R s = R(0);
+#pragma unroll
+      for (int n = 0; n < 8; ++n) s += Ws[(l * 8 + n) * 8 + k] * dA[n * 25 + lm];
+      U[o] = s * a.inv_n0;
+    }
+    __syncwarp();
+    const SysInfo& S = a.sys[a.atom_sys ? a.atom_sys[i] : 0];
+    const auto si = a.sh[i];
+    const size_t row = (size_t)q * a.cap;
+    const int nin = a.nin[q];
+    const R wgt = (R)(a.wgt ? a.wgt[i] : 1.0 - (a.lam ? a.lam[i] : 0.0));
+    R pix = R(0), piy = R(0), piz = R(0);
+    for (int base = 0; base < nin; base += 32) {
+      const int slot = base + lane;
+      if (slot >= nin) continue;
+      const int ent = a.slots[(size_t)q * kListCap + slot];
       const int j = a.nbr[row + ent];
       R d[3];
       pair_disp<R>(S, si, a.sh[j], a.off, row + ent, d);
@@ -704,27 +653,16 @@ __global__ void __launch_bounds__(kWarps3<R> * 32, sizeof(R) == 4 ? AP_ACE3_MINB
       ptx = fma(-pzl, ux, ptx);
       pty = fma(-pzl, uy, pty);
       ptz = fma(-pzl, uz, ptz);
-      px = pr * ux + ptx * ir;
-      py = pr * uy + pty * ir;
-      pz = pr * uz + ptz * ir;
+      R px = pr * ux + ptx * ir, py = pr * uy + pty * ir, pz = pr * uz + ptz * ir;
+      pix += px;
+      piy += py;
+      piz += pz;
       add_force<R>(a.facc32, a.facc64, j, -wgt * px, -wgt * py, -wgt * pz);
     }
-    // +w_i sum_j p_ij for each ring atom with pairs in this window (warp-uniform loop)
-    const int wend = min(pos + 32, stream_end);
-    for (int b = head; b < tail; ++b) {
-      const int bs = b % kRing;
-      if (s_end[warp][bs] <= pos || s_beg[warp][bs] >= wend) continue;
-      const bool mine = at == b && p < stream_end;
-      const R sx = warp_sum<R>(mine ? px : R(0));
-      const R sy = warp_sum<R>(mine ? py : R(0));
-      const R sz = warp_sum<R>(mine ? pz : R(0));
-      if (lane == 0) {
-        const R w = s_w[warp][bs];
-        add_force<R>(a.facc32, a.facc64, s_i[warp][bs], w * sx, w * sy, w * sz);
-      }
-    }
-    pos = wend;
-    while (head < tail && s_end[warp][head % kRing] <= pos) ++head;
+    pix = warp_sum<R>(pix);
+    piy = warp_sum<R>(piy);
+    piz = warp_sum<R>(piz);
+    if (lane == 0) add_force<R>(a.facc32, a.facc64, i, wgt * pix, wgt * piy, wgt * piz);
     __syncwarp();
   }
 }
@@ -751,7 +689,7 @@ size_t basis_smem() {
 
 template <typename R>
 size_t adjoint_smem() {
-  return sizeof(R) * (320 + kWarps3<R> * (200 + kRing * 200));
+  return sizeof(R) * (320 + kWarps3<R> * 400);
 }
 
 template <typename K>
