@@ -12,12 +12,6 @@
 // Pair displacements come from cell-relative shadows: d = k h + s_j - s_i with k
 // the pair's cell offset, either stored per entry (small periodic boxes) or
 // unwrapped from the packed cell codes (branch-free, per-atom constants hoisted).
-//
-// Row staging (STAGE): a CTA first copies the valid entries of its 64 atoms' rows
-// into shared memory (every warp 8 rows, all loads independent and in flight), so
-// the per-pair chain is shared row entry -> neighbour gather instead of global row
-// entry -> neighbour gather.  Row stride in shared memory = cap rounded up to 32,
-// plus 4 words: the 8 atoms x 4 lanes of a warp then read 32 distinct banks.
 #include "ap_internal.cuh"
 #include "eam_frame.cuh"
 
@@ -25,33 +19,7 @@ namespace ap {
 
 namespace {
 
-constexpr int kTileAtoms = 256 / AP_EAM_LANES;   // atoms per 256-thread CTA
-
-__host__ __device__ inline int stage_stride(int cap) { return ((cap + 31) & ~31) + 4; }
-
-// Copy the valid entries of rows tile0 .. tile0+kTileAtoms-1 into srow (stride words).
-__device__ inline void stage_rows(int n, int tile0, const int* __restrict__ nbr, const int* __restrict__ cnt,
-                                  int cap, int stride, int* __restrict__ srow) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 0; k < kTileAtoms / 8; ++k) {
-    const int r = warp + 8 * k;
-    const int ia = tile0 + r;
-    const int c = ia < n ? cnt[ia] : 0;
-    const int* src = nbr + (size_t)ia * cap;
-    int* dst = srow + r * stride;
-    int v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = lane + 32 * u < c ? src[lane + 32 * u] : 0;
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (lane + 32 * u < c) dst[lane + 32 * u] = v[u];
-    for (int t = lane + 128; t < c; t += 32) dst[t] = src[t];
-  }
-  __syncthreads();
-}
-
-template <typename R, int G, bool STORED, typename P, bool STAGE>
+template <typename R, int G, bool STORED, typename P>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam_density(int n, const SysInfo* __restrict__ sys,
                                                      const int* __restrict__ atom_sys,
                                                      const typename Shadow<R>::T* __restrict__ sh,
@@ -59,12 +27,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
                                                      const int* __restrict__ cnt, int cap, P p,
                                                      const double* __restrict__ lam,
                                                      typename Q2<R>::T* __restrict__ q, double* __restrict__ xi_out) {
-  extern __shared__ int srow[];
-  const int stride = stage_stride(cap);
-  if constexpr (STAGE) stage_rows(n, blockIdx.x * kTileAtoms, nbr, cnt, cap, stride, srow);
   const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int sub = threadIdx.x & (G - 1);
-  const int* myrow = srow + (threadIdx.x / G) * stride;
   const bool active = gid < n;
   const int i = active ? gid : n - 1;
   const auto si = sh[i];
@@ -74,7 +38,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   R rho = R(0);
 #pragma unroll 4
   for (int t = sub; t < c; t += G) {
-    const int j = STAGE ? myrow[t] : nbr[row + t];
+    const int j = nbr[row + t];
     const auto sj = sh[j];
     R d[3];
     fr.disp(sj, off, row + t, d);
@@ -93,7 +57,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   }
 }
 
-template <typename R, int G, bool STORED, typename P, bool STAGE>
+template <typename R, int G, bool STORED, typename P>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam_force(int n, const SysInfo* __restrict__ sys,
                                                    const int* __restrict__ atom_sys,
                                                    const typename Shadow<R>::T* __restrict__ sh,
@@ -102,12 +66,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
                                                    const typename Q2<R>::T* __restrict__ q,
                                                    const double* __restrict__ xi, double* __restrict__ e_fast,
                                                    double* __restrict__ f, int accumulate) {
-  extern __shared__ int srow[];
-  const int stride = stage_stride(cap);
-  if constexpr (STAGE) stage_rows(n, blockIdx.x * kTileAtoms, nbr, cnt, cap, stride, srow);
   const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int sub = threadIdx.x & (G - 1);
-  const int* myrow = srow + (threadIdx.x / G) * stride;
   const bool active = gid < n;
   const int i = active ? gid : n - 1;
   const auto si = sh[i];
@@ -118,7 +78,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   R fx = R(0), fy = R(0), fz = R(0), phi = R(0);
 #pragma unroll 4
   for (int t = sub; t < c; t += G) {
-    const int j = STAGE ? myrow[t] : nbr[row + t];
+    const int j = nbr[row + t];
     const auto sj = sh[j];
     const auto qj = q[j];
     R d[3];
@@ -155,8 +115,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   }
 }
 
-constexpr size_t kStageMaxBytes = 64 * 1024;   // rows staged up to cap = 220 entries
-
 template <typename R, bool STORED, typename P>
 void run_eam(ap_ctx* c, const P& p, const typename Shadow<R>::T* sh, const double* d_lam, double* d_e_fast,
              double* d_f, bool accumulate, cudaStream_t s) {
@@ -165,28 +123,11 @@ void run_eam(ap_ctx* c, const P& p, const typename Shadow<R>::T* sh, const doubl
   int blocks = (int)((c->n * G + threads - 1) / threads);
   auto* q = reinterpret_cast<typename Q2<R>::T*>(c->d_q);
   const int* off = STORED ? c->d_off_eam : nullptr;
-  const size_t smem = sizeof(int) * kTileAtoms * (size_t)stage_stride(c->cap_eam);
-  if (smem <= kStageMaxBytes) {
-    static bool attr = false;   // per instantiation
-    if (!attr) {
-      cudaFuncSetAttribute(k_eam_density<R, G, STORED, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kStageMaxBytes);
-      cudaFuncSetAttribute(k_eam_force<R, G, STORED, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kStageMaxBytes);
-      attr = true;
-    }
-    k_eam_density<R, G, STORED, P, true><<<blocks, threads, smem, s>>>(
-        (int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam, off, c->d_cnt_eam, c->cap_eam, p, d_lam, q, c->d_xi);
-    k_eam_force<R, G, STORED, P, true><<<blocks, threads, smem, s>>>(
-        (int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam, off, c->d_cnt_eam, c->cap_eam, p, q, c->d_xi,
-        d_e_fast, d_f, accumulate ? 1 : 0);
-  } else {
-    k_eam_density<R, G, STORED, P, false><<<blocks, threads, 0, s>>>(
-        (int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam, off, c->d_cnt_eam, c->cap_eam, p, d_lam, q, c->d_xi);
-    k_eam_force<R, G, STORED, P, false><<<blocks, threads, 0, s>>>(
-        (int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam, off, c->d_cnt_eam, c->cap_eam, p, q, c->d_xi,
-        d_e_fast, d_f, accumulate ? 1 : 0);
-  }
+  k_eam_density<R, G, STORED, P><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam,
+                                                         off, c->d_cnt_eam, c->cap_eam, p, d_lam, q, c->d_xi);
+  k_eam_force<R, G, STORED, P><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam, off,
+                                                       c->d_cnt_eam, c->cap_eam, p, q, c->d_xi, d_e_fast, d_f,
+                                                       accumulate ? 1 : 0);
   c->kernels += 2;
 }
 
