@@ -358,14 +358,21 @@ __global__ void k_compact(int n, const int* __restrict__ flag, const int* __rest
 // within r_hi; for every image j with r_ij < r_hi it lowers lambda_min,j to
 // 1 - (1 - lambda_0,i) f_cut((r_ij - r_lo)/(r_hi - r_lo)) by a 64-bit atomicMin on
 // the bit pattern (order-free and exact for non-negative doubles).
-__global__ void __launch_bounds__(256) k_spread(const int* __restrict__ det, const int* __restrict__ n_det,
-                                                const double* __restrict__ x, const uint8_t* __restrict__ ch,
-                                                const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
-                                                const float4* __restrict__ s32, const int4* __restrict__ cunw,
-                                                const int* __restrict__ cstart, const int* __restrict__ catoms,
-                                                const double* __restrict__ lam0, double r_lo, double r_hi, int mode,
-                                                int sx, int sy, int sz, double* __restrict__ lam_min) {
-  const int lane = threadIdx.x & 31;
+// The warp takes the stencil cells 32 at a time; the cells that can reach r_hi form,
+// through a warp scan of their atom counts, one stream of candidate atoms that the
+// lanes share out (lane k takes candidates k, k + 32, ...; its cell is found by a
+// binary search over the 32 prefix sums), so lanes stay busy whatever the cells hold.
+constexpr int kSpreadWarps = 8;
+
+__global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
+    const int* __restrict__ det, const int* __restrict__ n_det, const double* __restrict__ x,
+    const uint8_t* __restrict__ ch, const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
+    const float4* __restrict__ s32, const int4* __restrict__ cunw, const int* __restrict__ cstart,
+    const int* __restrict__ catoms, const double* __restrict__ lam0, double r_lo, double r_hi, int mode, int sx,
+    int sy, int sz, double* __restrict__ lam_min) {
+  // per warp: inclusive prefix of candidate counts, first catoms slot, stencil offset
+  __shared__ int s_pre[kSpreadWarps][32], s_beg[kSpreadWarps][32], s_t[kSpreadWarps][32], s_img[kSpreadWarps][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const int m = *n_det;
   const double rh2 = __dmul_rn(r_hi, r_hi);
@@ -382,38 +389,69 @@ __global__ void __launch_bounds__(256) k_spread(const int* __restrict__ det, con
     const double one_minus = __dsub_rn(1.0, lam0[i]);
     const float one_minus_f = (float)one_minus;
     const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
-    for (int t = lane; t < ncell; t += 32) {
-      int dx = t % wx - sx;
-      int dy = (t / wx) % wy - sy;
-      int dz = t / (wx * wy) - sz;
-      int tc[3] = {cw[0] + dx, cw[1] + dy, cw[2] + dz};
-      int img[3] = {0, 0, 0};
-      bool skip = false;
-      for (int a = 0; a < 3; ++a) {
-        if (S.periodic[a]) {
-          img[a] = floor_div(tc[a], S.nc[a]);
-          tc[a] -= img[a] * S.nc[a];
-        } else if (tc[a] < 0 || tc[a] >= S.nc[a]) {
-          skip = true;
+    for (int t0 = 0; t0 < ncell; t0 += 32) {
+      // this lane's cell of the chunk: kept if it exists and can reach r_hi
+      const int t = t0 + lane;
+      int cnt = 0, beg = 0, imgp = 0;
+      if (t < ncell) {
+        const int dx = t % wx - sx, dy = (t / wx) % wy - sy, dz = t / (wx * wy) - sz;
+        int tc[3] = {cw[0] + dx, cw[1] + dy, cw[2] + dz};
+        int img[3] = {0, 0, 0};
+        bool skip = false;
+        for (int a = 0; a < 3; ++a) {
+          if (S.periodic[a]) {
+            img[a] = floor_div(tc[a], S.nc[a]);
+            tc[a] -= img[a] * S.nc[a];
+          } else if (tc[a] < 0 || tc[a] >= S.nc[a]) {
+            skip = true;
+          }
+        }
+        if (!skip) {
+          const float gx = fmaxf(0.f, fmaxf((float)dx * S.hf[0] - si.x, si.x - (float)(dx + 1) * S.hf[0]));
+          const float gy = fmaxf(0.f, fmaxf((float)dy * S.hf[1] - si.y, si.y - (float)(dy + 1) * S.hf[1]));
+          const float gz = fmaxf(0.f, fmaxf((float)dz * S.hf[2] - si.z, si.z - (float)(dz + 1) * S.hf[2]));
+          if (gx * gx + gy * gy + gz * gz <= rhf2 + kBand) {
+            const int cid = S.cell_base + (tc[2] * S.nc[1] + tc[1]) * S.nc[0] + tc[0];
+            beg = cstart[cid];
+            cnt = cstart[cid + 1] - beg;
+            // periodic image of the cell, 8 bits per component biased by 128
+            imgp = pack_off(img[0], img[1], img[2]);
+          }
         }
       }
-      if (skip) continue;
-      float gx = fmaxf(0.f, fmaxf((float)dx * S.hf[0] - si.x, si.x - (float)(dx + 1) * S.hf[0]));
-      float gy = fmaxf(0.f, fmaxf((float)dy * S.hf[1] - si.y, si.y - (float)(dy + 1) * S.hf[1]));
-      float gz = fmaxf(0.f, fmaxf((float)dz * S.hf[2] - si.z, si.z - (float)(dz + 1) * S.hf[2]));
-      if (gx * gx + gy * gy + gz * gz > rhf2 + kBand) continue;
-      int cid = S.cell_base + (tc[2] * S.nc[1] + tc[1]) * S.nc[0] + tc[0];
-      int b = cstart[cid], e = cstart[cid + 1];
-      const float ox = (float)dx * S.hf[0] - si.x;
-      const float oy = (float)dy * S.hf[1] - si.y;
-      const float oz = (float)dz * S.hf[2] - si.z;
-      for (int a = b; a < e; ++a) {
-        int j = catoms[a];
+      int pre = cnt;   // inclusive warp scan of the counts
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+      }
+      const int total = __shfl_sync(0xffffffffu, pre, 31);
+      s_pre[wib][lane] = pre;
+      s_beg[wib][lane] = beg;
+      s_t[wib][lane] = t;
+      s_img[wib][lane] = imgp;
+      __syncwarp();
+      for (int k = lane; k < total; k += 32) {
+        // cell of candidate k: the first c with s_pre[c] > k
+        int lo = 0, hi = 31;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (s_pre[wib][mid] > k) hi = mid;
+          else lo = mid + 1;
+        }
+        const int c = lo;
+        const int a = s_beg[wib][c] + k - (c ? s_pre[wib][c - 1] : 0);
+        const int tt = s_t[wib][c], ip = s_img[wib][c];
+        const int dx = tt % wx - sx, dy = (tt / wx) % wy - sy, dz = tt / (wx * wy) - sz;
+        const int j = catoms[a];
         if (j == i && dx == 0 && dy == 0 && dz == 0) continue;
         if (ch && !ch[j]) continue;
-        float4 sj = s32[j];
-        float ddx = ox + sj.x, ddy = oy + sj.y, ddz = oz + sj.z;
-        float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
+        const float ox = (float)dx * S.hf[0] - si.x;
+        const float oy = (float)dy * S.hf[1] - si.y;
+        const float oz = (float)dz * S.hf[2] - si.z;
+        const float4 sj = s32[j];
+        const float ddx = ox + sj.x, ddy = oy + sj.y, ddz = oz + sj.z;
+        const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
         if (r2f > rhf2 + kBand) continue;
         // FP32 estimate of the candidate value (error < 1e-5): if even its lower
         // bound cannot go below the current lambda_min,j (which only decreases),
@@ -422,24 +460,26 @@ __global__ void __launch_bounds__(256) k_spread(const int* __restrict__ det, con
           const float vf = 1.f - one_minus_f * fcut_f((sqrtf(r2f) - r_lo_f) * inv_w_f, mode);
           if ((double)vf - 1e-4 >= __ldcg(&lam_min[j])) continue;
         }
-        int4 cj = cunw[j];
+        const int img[3] = {off_x(ip), off_y(ip), off_z(ip)};
+        const int4 cj = cunw[j];
         double d[3];
         // image relative to the input positions: S = img + nwrap_i - nwrap_j
-        int cu_i[3] = {ci.x, ci.y, ci.z}, cu_j[3] = {cj.x, cj.y, cj.z};
-        int cwi[3] = {cw[0], cw[1], cw[2]}, cwj[3] = {cell_x(cj.w), cell_y(cj.w), cell_z(cj.w)};
+        const int cu_i[3] = {ci.x, ci.y, ci.z}, cu_j[3] = {cj.x, cj.y, cj.z};
+        const int cwj[3] = {cell_x(cj.w), cell_y(cj.w), cell_z(cj.w)};
         for (int q = 0; q < 3; ++q) {
           int sd = 0;
-          if (S.periodic[q]) sd = img[q] + (cu_i[q] - cwi[q]) / S.nc[q] - (cu_j[q] - cwj[q]) / S.nc[q];
-          double shifted = __dadd_rn(x[3 * j + q], __dmul_rn((double)sd, S.L[q]));
+          if (S.periodic[q]) sd = img[q] + (cu_i[q] - cw[q]) / S.nc[q] - (cu_j[q] - cwj[q]) / S.nc[q];
+          const double shifted = __dadd_rn(x[3 * j + q], __dmul_rn((double)sd, S.L[q]));
           d[q] = __dsub_rn(shifted, x[3 * i + q]);
         }
-        double r2 = norm2_exact(d);
+        const double r2 = norm2_exact(d);
         if (!(r2 < rh2)) continue;
-        double r = __dsqrt_rn(r2);
-        double f = fcut_exact(__ddiv_rn(__dsub_rn(r, r_lo), width), mode);
-        double v = __dsub_rn(1.0, __dmul_rn(one_minus, f));
+        const double r = __dsqrt_rn(r2);
+        const double f = fcut_exact(__ddiv_rn(__dsub_rn(r, r_lo), width), mode);
+        const double v = __dsub_rn(1.0, __dmul_rn(one_minus, f));
         atomicMin((unsigned long long*)&lam_min[j], (unsigned long long)__double_as_longlong(v));
       }
+      __syncwarp();
     }
   }
 }
@@ -497,7 +537,7 @@ void launch_lambda0(ap_ctx* c, const uint8_t* d_ch, const double* d_score, doubl
 
 void launch_spread(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s) {
   int grid = c->num_sms * 8;
-  k_spread<<<grid, 256, 0, s>>>(c->d_detected, &c->d_sc->n_detected, d_x, d_ch, c->d_sys, c->d_atom_sys, c->d_sh32,
+  k_spread<<<grid, kSpreadWarps * 32, 0, s>>>(c->d_detected, &c->d_sc->n_detected, d_x, d_ch, c->d_sys, c->d_atom_sys, c->d_sh32,
                                 c->d_cunw, c->d_cell_start, c->d_cell_atoms, c->d_lam0, c->cfg.r_lo, c->cfg.r_hi,
                                 c->cfg.fcut_mode, c->sten_spread[0], c->sten_spread[1], c->sten_spread[2],
                                 c->d_lam_min);
