@@ -53,7 +53,7 @@ __device__ inline double rsqrt_(double v) { return rsqrt(v); }
 #define AP_EAM_MINB 6   // FP32 only: <= 42 registers, 48 resident warps per SM
 #endif
 #ifndef AP_EAM_FAST_RCP
-#define AP_EAM_FAST_RCP 0
+#define AP_EAM_FAST_RCP 1
 #endif
 
 __device__ inline float rcp_(float v) {
