@@ -632,11 +632,21 @@ __global__ void __launch_bounds__(kWarps3<R> * 32, sizeof(R) == 4 ? AP_ACE3_MINB
     const int nin = a.nin[q];
     const R wgt = (R)(a.wgt ? a.wgt[i] : 1.0 - (a.lam ? a.lam[i] : 0.0));
     R pix = R(0), piy = R(0), piz = R(0);
+    // the row entry and neighbour index of the lane's next pair are loaded one
+    // iteration ahead, so only the neighbour-shadow load is exposed per pair
+    int ent_n = 0, j_n = 0;
+    if (lane < nin) {
+      ent_n = a.slots[(size_t)q * kListCap + lane];
+      j_n = a.nbr[row + ent_n];
+    }
     for (int base = 0; base < nin; base += 32) {
       const int slot = base + lane;
+      const int ent = ent_n, j = j_n;
+      if (slot + 32 < nin) {
+        ent_n = a.slots[(size_t)q * kListCap + slot + 32];
+        j_n = a.nbr[row + ent_n];
+      }
       if (slot >= nin) continue;
-      const int ent = a.slots[(size_t)q * kListCap + slot];
-      const int j = a.nbr[row + ent];
       R d[3];
       pair_disp<R>(S, si, a.sh[j], a.off, row + ent, d);
       R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
