@@ -80,10 +80,7 @@ ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box
   double htarget = rlist / kStencil;
   std::vector<SysInfo> sys(n_sys);
   int base = 0;
-  // Per-entry cell offsets are stored for every box: small periodic boxes need them
-  // (a pair can span more than half the cells), and elsewhere unpacking a stored
-  // offset costs fewer instructions per pair than unwrapping the cell codes.
-  bool stored = true;
+  bool stored = false;
   int spread[3] = {0, 0, 0};
   for (int s = 0; s < n_sys; ++s) {
     SysInfo& I = sys[s];
@@ -100,7 +97,7 @@ ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box
       I.h[d] = L / nc;
       I.hf[d] = (float)I.h[d];
       I.periodic[d] = boxes[s].periodic[d] ? 1 : 0;
-      (void)stored;
+      if (I.periodic[d] && nc < 2 * kStencil + 1) stored = true;
       int sp = (int)std::ceil(g.r_hi / I.h[d]);
       if (!I.periodic[d]) sp = std::min(sp, nc);
       spread[d] = std::max(spread[d], sp);
