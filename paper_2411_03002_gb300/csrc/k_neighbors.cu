@@ -345,8 +345,11 @@ __global__ void k_build_eam(int n, const double* __restrict__ x, const SysInfo* 
                             const int4* __restrict__ cunw, const int* __restrict__ cstart,
                             const int* __restrict__ catoms, float rcf2, double rc2, float band, int cap,
                             int* __restrict__ nbr, int* __restrict__ off, int* __restrict__ cnt, DevScalars* sc) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  // Threads take the atoms in cell order: the atoms of one cell walk the same stencil
+  // cells with the same atom counts, so a warp diverges only on the per-atom gap test.
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = catoms[t];
   const SysInfo& S = sys_of(sys, atom_sys, i);
   int c = build_row(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, band, cap, nbr + (size_t)i * cap,
                     off ? off + (size_t)i * cap : nullptr);
