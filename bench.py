@@ -80,6 +80,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, ws: int, device) -> float:
+    """The whole job's time for N independent replicas: the slowest rank's (ms)."""
+    if ws <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ws: int, ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * ws / (ms / 1e3)
+
+
 def hyb_for(mode: str, hyb: I.HybridParams) -> I.HybridParams:
     import dataclasses
     if mode == "full-ace":       # every changeable atom detected: lambda = 0
@@ -225,12 +240,9 @@ def run_ours(args, ws, rank, local):
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     prof = ctx.profile_read()
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws, dev)
     atom_steps = w.n * MD_PER_STEP * args.steps * ws
-    value = atom_steps / (ms / 1e3)
+    value = job_rate(w.n * MD_PER_STEP * args.steps, ws, ms)
     ace_ms, ace_calls = prof["phases"]["ace"]
     adj_ms, adj_calls = prof["phases"]["ace_adjoint"]          # a sub-phase of "ace"
     flops = ACE_FLOP_PER_PAIR * prof["ace_pairs"] + ACE_FLOP_PER_ATOM * prof["ace_atoms"]
@@ -256,11 +268,7 @@ def run_ours(args, ws, rank, local):
         lamh.copy_(lam, non_blocking=True)
     e3.record(stream)
     barrier()
-    ms_e2e = e2.elapsed_time(e3)
-    if ws > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3), ws, dev)
     h2d = 3 * w.n * 3 * 8
     d2h = 3 * w.n * 3 * 8 + w.n * 8
 
