@@ -376,9 +376,7 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
   }
   __syncthreads();
   const int m = *a.count;
-  // contraction lanes: k pair (2 kp, 2 kp + 1) x lm in {q, q + 7, q + 14, q + 21} (q < 7);
-  // the strided lm put the 7 row groups of one load on distinct banks
-  const int kp = lane & 3, qq = lane >> 2;
+  const int kq = lane & 7, grp = lane >> 3;
   const unsigned lt_mask = (1u << lane) - 1u;
   while (true) {
     int q = 0;
@@ -424,9 +422,9 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
     __syncwarp();
 
     // ---------------- stage A: G_klm = sum_j g_k Y_lm over the compacted neighbours
-    R acc[2][4];
+    R acc[7];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) acc[0][t] = acc[1][t] = R(0);
+    for (int t = 0; t < 7; ++t) acc[t] = R(0);
     for (int base = 0; base < nin; base += 32) {
       const int slot = base + lane;
       R g[8], Y[25];
@@ -448,46 +446,31 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
       for (int k = 0; k < 25; ++k) tile[(8 + k) * kCols + lane] = Y[k];
       __syncwarp();
       const int nv = min(32, nin - base);
-      if (qq < 7) {
-        for (int s4 = 0; s4 < (nv + 3) / 4; ++s4) {
-          const auto ga = ld4<R>(&tile[(2 * kp) * kCols + 4 * s4]);
-          const auto gb = ld4<R>(&tile[(2 * kp + 1) * kCols + 4 * s4]);
+      for (int s4 = 0; s4 < (nv + 3) / 4; ++s4) {
+        auto g4 = ld4<R>(&tile[kq * kCols + 4 * s4]);
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const int lm = qq + 7 * t;
-            if (lm < 25) {
-              const auto y4 = ld4<R>(&tile[(8 + lm) * kCols + 4 * s4]);
-              acc[0][t] += ga.x * y4.x + ga.y * y4.y + ga.z * y4.z + ga.w * y4.w;
-              acc[1][t] += gb.x * y4.x + gb.y * y4.y + gb.z * y4.z + gb.w * y4.w;
-            }
+        for (int t = 0; t < 7; ++t) {
+          const int lm = grp + 4 * t;
+          if (lm < 25) {
+            auto y4 = ld4<R>(&tile[(8 + lm) * kCols + 4 * s4]);
+            acc[t] += g4.x * y4.x + g4.y * y4.y + g4.z * y4.z + g4.w * y4.w;
           }
         }
       }
       __syncwarp();
     }
-    if (qq < 7) {
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int lm = qq + 7 * t;
-        if (lm < 25) {
-          Gs[(2 * kp) * 25 + lm] = acc[0][t];
-          Gs[(2 * kp + 1) * 25 + lm] = acc[1][t];
-        }
-      }
+    for (int t = 0; t < 7; ++t) {
+      const int lm = grp + 4 * t;
+      if (lm < 25) Gs[kq * 25 + lm] = acc[t];
     }
     __syncwarp();
     for (int o = lane; o < 200; o += 32) {
       const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
-      const auto w0 = ld4<R>(&Ws[(l * 8 + n) * 8]);
-      const auto w1 = ld4<R>(&Ws[(l * 8 + n) * 8 + 4]);
-      R s = w0.x * Gs[0 * 25 + lm];
-      s += w0.y * Gs[1 * 25 + lm];
-      s += w0.z * Gs[2 * 25 + lm];
-      s += w0.w * Gs[3 * 25 + lm];
-      s += w1.x * Gs[4 * 25 + lm];
-      s += w1.y * Gs[5 * 25 + lm];
-      s += w1.z * Gs[6 * 25 + lm];
-      s += w1.w * Gs[7 * 25 + lm];
+      const R* w = &Ws[(l * 8 + n) * 8];
+      R s = R(0);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s += w[k] * Gs[k * 25 + lm];
       A[o] = s * a.inv_n0;
     }
     __syncwarp();
@@ -497,16 +480,10 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
     R e = R(0);
     for (int o = lane; o < 200; o += 32) {
       const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
-      const auto m0 = ld4<R>(&M2[l * 64 + n * 8]);
-      const auto m1 = ld4<R>(&M2[l * 64 + n * 8 + 4]);
-      R s = m0.x * A[0 * 25 + lm];
-      s += m0.y * A[1 * 25 + lm];
-      s += m0.z * A[2 * 25 + lm];
-      s += m0.w * A[3 * 25 + lm];
-      s += m1.x * A[4 * 25 + lm];
-      s += m1.y * A[5 * 25 + lm];
-      s += m1.z * A[6 * 25 + lm];
-      s += m1.w * A[7 * 25 + lm];
+      const R* mrow = &M2[l * 64 + n * 8];
+      R s = R(0);
+#pragma unroll
+      for (int n2 = 0; n2 < 8; ++n2) s += mrow[n2] * A[n2 * 25 + lm];
       const R lin = lm == 0 ? C1[n] : R(0);
       e += A[o] * (R(0.5) * s + lin);
       a.dA[(size_t)q * 200 + o] = s + lin;
@@ -515,16 +492,10 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
       R eb = R(0);
       for (int o = lane; o < 200; o += 32) {
         const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
-        const auto m0 = ld4<R>(&M2b[l * 64 + n * 8]);
-        const auto m1 = ld4<R>(&M2b[l * 64 + n * 8 + 4]);
-        R sb = m0.x * A[0 * 25 + lm];
-        sb += m0.y * A[1 * 25 + lm];
-        sb += m0.z * A[2 * 25 + lm];
-        sb += m0.w * A[3 * 25 + lm];
-        sb += m1.x * A[4 * 25 + lm];
-        sb += m1.y * A[5 * 25 + lm];
-        sb += m1.z * A[6 * 25 + lm];
-        sb += m1.w * A[7 * 25 + lm];
+        const R* mrow = &M2b[l * 64 + n * 8];
+        R sb = R(0);
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) sb += mrow[n2] * A[n2 * 25 + lm];
         const R lin = lm == 0 ? C1b[n] : R(0);
         eb += A[o] * (R(0.5) * sb + lin);
         a.dAb[(size_t)q * 200 + o] = sb + lin;
