@@ -63,7 +63,8 @@ __device__ inline void exact_disp(const double* __restrict__ x, const SysInfo& S
   int cu_i[3] = {ci.x, ci.y, ci.z}, cu_j[3] = {cj.x, cj.y, cj.z};
   for (int a = 0; a < 3; ++a) {
     int sd = S.periodic[a] ? (k[a] - (cu_j[a] - cu_i[a])) / S.nc[a] : 0;
-    double shifted = __dadd_rn(x[3 * j + a], __dmul_rn((double)sd, S.L[a]));
+    // x_j + 0 L is x_j exactly: the FP64 multiply-add (slow on this GPU) only for images
+    double shifted = sd == 0 ? x[3 * j + a] : __dadd_rn(x[3 * j + a], __dmul_rn((double)sd, S.L[a]));
     d[a] = __dsub_rn(shifted, x[3 * i + a]);
   }
 }
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
         for (int q = 0; q < 3; ++q) {
           int sd = 0;
           if (S.periodic[q]) sd = img[q] + (cu_i[q] - cw[q]) / S.nc[q] - (cu_j[q] - cwj[q]) / S.nc[q];
-          const double shifted = __dadd_rn(x[3 * j + q], __dmul_rn((double)sd, S.L[q]));
+          const double shifted = sd == 0 ? x[3 * j + q] : __dadd_rn(x[3 * j + q], __dmul_rn((double)sd, S.L[q]));
           d[q] = __dsub_rn(shifted, x[3 * i + q]);
         }
         const double r2 = norm2_exact(d);

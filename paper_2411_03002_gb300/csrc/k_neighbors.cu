@@ -186,7 +186,7 @@ __device__ inline bool exact_within(const double* __restrict__ x, const SysInfo&
   for (int d = 0; d < 3; ++d) {
     int Sd = 0;
     if (S.periodic[d]) Sd = img[d] + (cui[d] - cwi[d]) / S.nc[d] - (cuj[d] - cwj[d]) / S.nc[d];
-    double shifted = __dadd_rn(x[3 * j + d], __dmul_rn((double)Sd, S.L[d]));
+    double shifted = Sd == 0 ? x[3 * j + d] : __dadd_rn(x[3 * j + d], __dmul_rn((double)Sd, S.L[d]));
     dd[d] = __dsub_rn(shifted, x[3 * i + d]);
   }
   r2 = __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])), __dmul_rn(dd[2], dd[2]));
