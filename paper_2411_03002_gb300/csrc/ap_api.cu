@@ -165,6 +165,7 @@ ap_status ensure_capacity(ap_ctx* c, int64_t n) {
   CK(dalloc(c->d_sh32, m));
   CK(dalloc(c->d_sh64, m));
   CK(dalloc(c->d_xbuild, 3 * m));
+  CK(dalloc(c->d_vscale, m));
   CK(dalloc(c->d_cnt_eam, m));
   CK(dalloc(c->d_cnt_ace, m));
   ap_status st = alloc_rows(c, true, true);
@@ -548,7 +549,7 @@ void ap_destroy(ap_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   void* ptrs[] = {c->d_sys, c->d_atom_sys, c->d_cell, c->d_cunw, c->d_cell_start, c->d_cell_count, c->d_cell_atoms,
-                  c->d_slot, c->d_sh32, c->d_sh64, c->d_xbuild, c->d_nbr_eam, c->d_off_eam, c->d_cnt_eam,
+                  c->d_slot, c->d_sh32, c->d_sh64, c->d_xbuild, c->d_vscale, c->d_nbr_eam, c->d_off_eam, c->d_cnt_eam,
                   c->d_nbr_ace, c->d_off_ace, c->d_cnt_ace, c->d_csp, c->d_csp_avg, c->d_lam0, c->d_lam_min,
                   c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected,
                   c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_efast, c->d_eprec,
@@ -800,6 +801,10 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
   st = clear_err(c, s);
   if (st) return st;
   const float skin_lim2 = (float)(0.25 * g.skin * g.skin);
+  if (nsteps > 0) {
+    PhaseTimer t(c, s, AP_PHASE_OTHER);
+    launch_vscale(c, d_mass, s);   // the half-kick factors of this call's masses
+  }
   for (int64_t k = 0; k < nsteps; ++k) {
     c->step++;
     {

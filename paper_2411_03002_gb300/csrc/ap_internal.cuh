@@ -170,6 +170,7 @@ struct ap_ctx {
   float4* d_sh32 = nullptr;      // FP32 cell-relative shadow
   double4_32a* d_sh64 = nullptr;     // FP64 cell-relative shadow
   double* d_xbuild = nullptr;    // [n][3] positions at the last build
+  double* d_vscale = nullptr;    // [n] 0.5 dt ACC / m_i of the current ap_step call
   int* d_nbr_eam = nullptr;      // [n][cap_eam]
   int* d_off_eam = nullptr;      // [n][cap_eam] (stored offsets only)
   int* d_cnt_eam = nullptr;      // [n]
@@ -340,6 +341,7 @@ void launch_th_correct(ap_ctx* c, const int* d_q, const int* d_m, const double* 
                        const double* d_mass, double* d_v, cudaStream_t s);
 
 // k_md.cu
+void launch_vscale(ap_ctx* c, const double* d_mass, cudaStream_t s);
 void launch_vv_first(ap_ctx* c, double* d_x, double* d_v, const double* d_f, const double* d_mass,
                      const uint8_t* d_fixed, cudaStream_t s);
 void launch_vv_second(ap_ctx* c, double* d_v, const double* d_f, const double* d_mass, const uint8_t* d_fixed,

@@ -12,8 +12,15 @@ constexpr double kAcc = 1.602176634e-19 / 1.66053906660e-27 * 1e-20 / 1e-10;
 constexpr int kRedBlocks = 512;
 constexpr int kRedThreads = 256;
 
+// Half-kick factor s_i = 0.5 dt ACC / m_i, once per ap_step call (FP64 division is
+// slow on this GPU; the kicks then need one FMA per component).
+__global__ void k_vscale(int n, const double* __restrict__ mass, double dt, double* __restrict__ vs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) vs[i] = 0.5 * dt * kAcc / mass[i];
+}
+
 __global__ void k_vv_first(int n, double* __restrict__ x, double* __restrict__ v, const double* __restrict__ f,
-                           const double* __restrict__ mass, const uint8_t* __restrict__ fixed, double dt,
+                           const double* __restrict__ vs, const uint8_t* __restrict__ fixed, double dt,
                            const double* __restrict__ xb, DevScalars* sc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   float d2 = 0.f;
@@ -21,20 +28,18 @@ __global__ void k_vv_first(int n, double* __restrict__ x, double* __restrict__ v
     if (fixed && fixed[i]) {
       v[3 * i + 0] = v[3 * i + 1] = v[3 * i + 2] = 0.0;
     } else {
-      double s = 0.5 * dt * kAcc / mass[i];
+      const double s = vs[i];
       bool bad = false;
-      double dd = 0.0;
       for (int a = 0; a < 3; ++a) {
         double vv = v[3 * i + a] + s * f[3 * i + a];
         double xx = x[3 * i + a] + dt * vv;
         v[3 * i + a] = vv;
         x[3 * i + a] = xx;
         bad |= !isfinite(xx);
-        double e = xx - xb[3 * i + a];
-        dd += e * e;
+        const float e = (float)(xx - xb[3 * i + a]);   // displacement since the build (skin check)
+        d2 += e * e;
       }
       if (bad) atomicOr(&sc->err, kErrNonfinite);
-      d2 = (float)dd;
     }
   }
 #pragma unroll
@@ -43,14 +48,14 @@ __global__ void k_vv_first(int n, double* __restrict__ x, double* __restrict__ v
 }
 
 __global__ void k_vv_second(int n, double* __restrict__ v, const double* __restrict__ f,
-                            const double* __restrict__ mass, const uint8_t* __restrict__ fixed, double dt) {
+                            const double* __restrict__ vs, const uint8_t* __restrict__ fixed) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (fixed && fixed[i]) {
     v[3 * i + 0] = v[3 * i + 1] = v[3 * i + 2] = 0.0;
     return;
   }
-  double s = 0.5 * dt * kAcc / mass[i];
+  const double s = vs[i];
   for (int a = 0; a < 3; ++a) v[3 * i + a] += s * f[3 * i + a];
 }
 
@@ -59,7 +64,12 @@ __global__ void k_indenter(int n, const double* __restrict__ x, double* __restri
                            double cx, double cy, double cz, double R, double k) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double dx = x[3 * i] - cx, dy = x[3 * i + 1] - cy, dz = x[3 * i + 2] - cz;
+  const double dz = x[3 * i + 2] - cz;
+  if (!(dz < R && dz > -R)) {   // r^2 < R^2 needs |dz| < R: most atoms stop here
+    if (e_ext) e_ext[i] = 0.0;
+    return;
+  }
+  double dx = x[3 * i] - cx, dy = x[3 * i + 1] - cy;
   double r2 = dx * dx + dy * dy + dz * dz;
   double e = 0.0;
   if (r2 < R * R && r2 > 0.0) {
@@ -130,16 +140,23 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
+void launch_vscale(ap_ctx* c, const double* d_mass, cudaStream_t s) {
+  k_vscale<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_mass, c->cfg.dt, c->d_vscale);
+  c->kernels += 1;
+}
+
 void launch_vv_first(ap_ctx* c, double* d_x, double* d_v, const double* d_f, const double* d_mass,
                      const uint8_t* d_fixed, cudaStream_t s) {
-  k_vv_first<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, d_v, d_f, d_mass, d_fixed, c->cfg.dt, c->d_xbuild,
+  (void)d_mass;   // the half-kick factors come from launch_vscale
+  k_vv_first<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, d_v, d_f, c->d_vscale, d_fixed, c->cfg.dt, c->d_xbuild,
                                              c->d_sc);
   c->kernels += 1;
 }
 
 void launch_vv_second(ap_ctx* c, double* d_v, const double* d_f, const double* d_mass, const uint8_t* d_fixed,
                       cudaStream_t s) {
-  k_vv_second<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_v, d_f, d_mass, d_fixed, c->cfg.dt);
+  (void)d_mass;
+  k_vv_second<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_v, d_f, c->d_vscale, d_fixed);
   c->kernels += 1;
 }
 

@@ -151,9 +151,10 @@ __global__ void k_shadow(int n, const double* __restrict__ x, const SysInfo* __r
   if (i >= n) return;
   const SysInfo& S = sys_of(sys, atom_sys, i);
   int4 c = cunw[i];
-  double s0 = (x[3 * i + 0] - S.lo[0]) - (double)c.x * S.h[0];
-  double s1 = (x[3 * i + 1] - S.lo[1]) - (double)c.y * S.h[1];
-  double s2 = (x[3 * i + 2] - S.lo[2]) - (double)c.z * S.h[2];
+  // (x - lo) - c h with one rounding for the product and the difference
+  double s0 = fma(-(double)c.x, S.h[0], x[3 * i + 0] - S.lo[0]);
+  double s1 = fma(-(double)c.y, S.h[1], x[3 * i + 1] - S.lo[1]);
+  double s2 = fma(-(double)c.z, S.h[2], x[3 * i + 2] - S.lo[2]);
   s32[i] = make_float4((float)s0, (float)s1, (float)s2, __int_as_float(c.w));
   if (s64) s64[i] = make_double4_32a(s0, s1, s2, (double)c.w);
 }
