@@ -681,6 +681,7 @@ __global__ void k_ace_finalize32(int n, const float4* __restrict__ acc, double* 
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 v = acc[i];
+  if (v.x == 0.f && v.y == 0.f && v.z == 0.f) return;   // no precise atom in reach (most atoms)
   f[3 * i + 0] += (double)v.x;
   f[3 * i + 1] += (double)v.y;
   f[3 * i + 2] += (double)v.z;

@@ -5,7 +5,7 @@
 //   force:   F_i = sum_j g_ij (x_j - x_i)/r_ij with
 //            g_ij = (lambda_i xi'_i + lambda_j xi'_j) zeta'(r_ij) + (lambda_i + lambda_j)/2 Phi'(r_ij),
 //            which is -grad_i sum_k lambda_k E_k^(f) gathered without atomics;
-//            E_i^(f) = xi_i + 1/2 sum_j Phi(r_ij)  (the Phi sum reduced in FP64).
+//            E_i^(f) = xi_i + 1/2 sum_j Phi(r_ij)  (E_i^(f) formed in FP64).
 // The potential P is a functor (eam_frame.cuh): the analytic synthetic EAM or the
 // Mishin EAM2 of Appendix E, selected by ap_config.eam_type.
 //
@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   fx = group_sum<R, G>(fx);
   fy = group_sum<R, G>(fy);
   fz = group_sum<R, G>(fz);
-  const double ph = group_sum<double, G>((double)phi);
+  // the G partial Phi sums are combined in the working precision, then widened once
+  const double ph = (double)group_sum<R, G>(phi);
   if (active && sub == 0) {
     if (accumulate) {
       f[3 * i + 0] += (double)fx;
