@@ -77,6 +77,7 @@ struct DevScalars {
   int n_precise;      // |P| (int32 copy used by kernels)
   int work_counter;   // persistent-kernel work counter
   int work_counter2;  // second persistent-kernel work counter (right after work_counter)
+  int n_csp_slow;     // atoms handed from the FP32 CSP kernel to the exact one
   unsigned int max_disp2_bits;  // float bits of the largest squared displacement
   long long n_precise64;
   double e_total;
@@ -181,6 +182,7 @@ struct ap_ctx {
 
   // lambda state (FP64)
   double* d_csp = nullptr;       // sample
+  int* d_csp_slow = nullptr;     // [n] atoms whose CSP needs the exact selection
   double* d_csp_avg = nullptr;
   double* d_lam0 = nullptr;
   double* d_lam_min = nullptr;

@@ -116,14 +116,18 @@ __device__ inline bool entry_less(const double* __restrict__ x, const SysInfo& S
 // ------------------------------------------------------------------ CSP
 // One thread per atom.  All selection arrays are indexed with compile-time
 // indices (fully unrolled insertion), so they live in registers.
-__global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x, const uint8_t* __restrict__ ch,
-                                             const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
-                                             const float4* __restrict__ s32, const int4* __restrict__ cunw,
-                                             const int* __restrict__ nbr, const int* __restrict__ off,
-                                             const int* __restrict__ cnt, int cap, float rsf2, double rs2,
-                                             double* __restrict__ csp) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// FAST: every atom, FP32 selections only; an atom whose selection the FP32 values
+// cannot decide (an r_search band hit, an ambiguous 12/13 or 6/7 boundary) is
+// appended to `slow`.  !FAST: the atoms of `slow`, with the exact FP64 selections.
+// CSP of atom i (128-thread blocks: the shared arrays are indexed by threadIdx.x).
+template <bool FAST>
+__device__ __forceinline__ void csp_atom(int i, const double* __restrict__ x, const uint8_t* __restrict__ ch,
+                                         const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
+                                         const float4* __restrict__ s32, const int4* __restrict__ cunw,
+                                         const int* __restrict__ nbr, const int* __restrict__ off,
+                                         const int* __restrict__ cnt, int cap, float rsf2, double rs2,
+                                         double* __restrict__ csp, int* __restrict__ slow, int* __restrict__ n_slow) {
+  static_assert(kNN <= 255, "neighbour slots are packed in 8 bits");
   if (ch && !ch[i]) {
     csp[i] = 0.0;
     return;
@@ -154,6 +158,10 @@ __global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (r2 > rsf2 + kBand) continue;
     if (r2 >= rsf2 - kBand) {
+      if constexpr (FAST) {
+        slow[atomicAdd(n_slow, 1)] = i;
+        return;
+      }
       double d[3];
       exact_disp(x, S, i, j, ci, cunw[j], k, d);
       if (!(norm2_exact(d) < rs2)) continue;
@@ -181,6 +189,10 @@ __global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x
   }
   // 2. exact (r2, j, s) selection when the 12/13 boundary lies within the guard band
   if (n_in > kNN && tr[kNN] - tr[kNN - 1] <= 2.f * kBand) {
+    if constexpr (FAST) {
+      slow[atomicAdd(n_slow, 1)] = i;
+      return;
+    }
     double br[kNN];
     int bq[kNN];
 #pragma unroll
@@ -212,34 +224,41 @@ __global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x
 #pragma unroll
     for (int a = 0; a < kNN; ++a) tq[a] = bq[a];
   }
-  // 3. FP32 vectors of the 12 and the 7 smallest pair values |r_a + r_b|^2
-  float vx[kNN], vy[kNN], vz[kNN];
+  // 3. FP32 vectors of the 12 and the 7 smallest pair values |r_a + r_b|^2.  The 12
+  // vectors and row positions live in shared memory, component-major (thread index
+  // fastest, conflict-free), not in registers.
+  __shared__ float s_v[3][kNN][128];
+  __shared__ int s_tq[kNN][128];
+  const int tx = threadIdx.x;
 #pragma unroll
   for (int a = 0; a < kNN; ++a) {
-    const int j = nbr[row + tq[a]];
+    const int q = tq[a];
+    s_tq[a][tx] = q;
+    const int j = nbr[row + q];
     const float4 sj = s32[j];
     int k[3];
-    entry_offset(off, row + tq[a], S, ci.w, __float_as_int(sj.w), k);
-    vx[a] = (float)k[0] * S.hf[0] + sj.x - si.x;
-    vy[a] = (float)k[1] * S.hf[1] + sj.y - si.y;
-    vz[a] = (float)k[2] * S.hf[2] + sj.z - si.z;
+    entry_offset(off, row + q, S, ci.w, __float_as_int(sj.w), k);
+    s_v[0][a][tx] = (float)k[0] * S.hf[0] + sj.x - si.x;
+    s_v[1][a][tx] = (float)k[1] * S.hf[1] + sj.y - si.y;
+    s_v[2][a][tx] = (float)k[2] * S.hf[2] + sj.z - si.z;
   }
   float pv[kHalf + 1];
-  int pc[kHalf + 1];   // row positions qa | qb << 16
+  int pc[kHalf + 1];   // neighbour slots a | b << 8
 #pragma unroll
   for (int a = 0; a <= kHalf; ++a) {
     pv[a] = INFINITY;
     pc[a] = 0;
   }
 #pragma unroll
-  for (int a = 0; a < kNN; ++a)
+  for (int a = 0; a < kNN; ++a) {
+    const float ax = s_v[0][a][tx], ay = s_v[1][a][tx], az = s_v[2][a][tx];
 #pragma unroll
     for (int b = a + 1; b < kNN; ++b) {
-      const float sx = vx[a] + vx[b], sy = vy[a] + vy[b], sz = vz[a] + vz[b];
+      const float sx = ax + s_v[0][b][tx], sy = ay + s_v[1][b][tx], sz = az + s_v[2][b][tx];
       const float v = sx * sx + sy * sy + sz * sz;
       if (v < pv[kHalf]) {
         pv[kHalf] = v;
-        pc[kHalf] = tq[a] | (tq[b] << 16);
+        pc[kHalf] = a | (b << 8);
 #pragma unroll
         for (int p = kHalf; p > 0; --p) {
           if (pv[p] < pv[p - 1]) {
@@ -253,6 +272,7 @@ __global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x
         }
       }
     }
+  }
   // 4. exact values of the six smallest pairs (all 66 in FP64 if the 6/7 boundary is ambiguous)
   double chosen[kHalf];
   if (pv[kHalf] - pv[kHalf - 1] > 2.f * kBand) {
@@ -260,19 +280,23 @@ __global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x
     for (int t = 0; t < kHalf; ++t) {
       double da[3], db[3];
       int ja, jb, sa[3], sb[3];
-      exact_entry(x, S, i, ci, nbr, off, cunw, row, pc[t] & 0xffff, da, ja, sa);
-      exact_entry(x, S, i, ci, nbr, off, cunw, row, pc[t] >> 16, db, jb, sb);
+      exact_entry(x, S, i, ci, nbr, off, cunw, row, s_tq[pc[t] & 0xff][tx], da, ja, sa);
+      exact_entry(x, S, i, ci, nbr, off, cunw, row, s_tq[pc[t] >> 8][tx], db, jb, sb);
       const double s3[3] = {__dadd_rn(da[0], db[0]), __dadd_rn(da[1], db[1]), __dadd_rn(da[2], db[2])};
       chosen[t] = norm2_exact(s3);
     }
   } else {
+    if constexpr (FAST) {
+      slow[atomicAdd(n_slow, 1)] = i;
+      return;
+    }
 #pragma unroll
     for (int t = 0; t < kHalf; ++t) chosen[t] = INFINITY;
     double ex[kNN][3];
 #pragma unroll
     for (int a = 0; a < kNN; ++a) {
       int j, s[3];
-      exact_entry(x, S, i, ci, nbr, off, cunw, row, tq[a], ex[a], j, s);
+      exact_entry(x, S, i, ci, nbr, off, cunw, row, s_tq[a][tx], ex[a], j, s);
     }
 #pragma unroll
     for (int a = 0; a < kNN; ++a)
@@ -308,6 +332,29 @@ __global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x
 #pragma unroll
   for (int a = 1; a < kHalf; ++a) sum = __dadd_rn(sum, chosen[a]);
   csp[i] = sum;
+}
+
+__global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x, const uint8_t* __restrict__ ch,
+                                                const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
+                                                const float4* __restrict__ s32, const int4* __restrict__ cunw,
+                                                const int* __restrict__ nbr, const int* __restrict__ off,
+                                                const int* __restrict__ cnt, int cap, float rsf2, double rs2,
+                                                double* __restrict__ csp, int* __restrict__ slow,
+                                                int* __restrict__ n_slow) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) csp_atom<true>(i, x, ch, sys, atom_sys, s32, cunw, nbr, off, cnt, cap, rsf2, rs2, csp, slow, n_slow);
+}
+
+__global__ void __launch_bounds__(128) k_csp_exact(const double* __restrict__ x, const uint8_t* __restrict__ ch,
+                                                   const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
+                                                   const float4* __restrict__ s32, const int4* __restrict__ cunw,
+                                                   const int* __restrict__ nbr, const int* __restrict__ off,
+                                                   const int* __restrict__ cnt, int cap, float rsf2, double rs2,
+                                                   double* __restrict__ csp, const int* __restrict__ slow,
+                                                   const int* __restrict__ n_slow) {
+  const int m = *n_slow;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x)
+    csp_atom<false>(slow[t], x, ch, sys, atom_sys, s32, cunw, nbr, off, cnt, cap, rsf2, rs2, csp, nullptr, nullptr);
 }
 
 // Canonical moving average over a ring buffer [ns][n]: oldest -> newest, then / ns.
@@ -516,10 +563,17 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s) {
   double r = c->cfg.eam_rc + c->cfg.skin;
   double rs2 = r * r;
+  const int* off = c->stored_off ? c->d_off_eam : nullptr;
+  int* n_slow = &c->d_sc->n_csp_slow;
+  cudaMemsetAsync(n_slow, 0, sizeof(int), s);
   k_csp<<<nblk(c->n, 128), 128, 0, s>>>((int)c->n, d_x, d_ch, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
-                                        c->d_nbr_eam, c->stored_off ? c->d_off_eam : nullptr, c->d_cnt_eam,
-                                        c->cap_eam, (float)rs2, rs2, c->d_csp);
-  c->kernels += 1;
+                                              c->d_nbr_eam, off, c->d_cnt_eam, c->cap_eam, (float)rs2, rs2, c->d_csp,
+                                              c->d_csp_slow, n_slow);
+  // the handed-over atoms (a small fraction), grid-stride over the device-side count
+  k_csp_exact<<<c->num_sms * 4, 128, 0, s>>>(d_x, d_ch, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw, c->d_nbr_eam,
+                                             off, c->d_cnt_eam, c->cap_eam, (float)rs2, rs2, c->d_csp,
+                                             c->d_csp_slow, n_slow);
+  c->kernels += 2;
 }
 
 // d_score: the detection score pushed into the history (CSP, or the selector's p),
