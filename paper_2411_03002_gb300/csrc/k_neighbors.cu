@@ -198,18 +198,11 @@ __device__ inline bool exact_within(const double* __restrict__ x, const SysInfo&
 // by the cell-box distance), iterate their cells' atoms in lock-step and append
 // accepted (j, offset) with ballot compaction.  Entry order: (cell round, atom
 // slot, lane) -- deterministic.  Returns the full count (may exceed cap).
-// One warp builds one row.  The stencil cells are taken 32 at a time; the cells
-// that can reach the cutoff form, through a warp scan of their atom counts, one
-// stream of candidate atoms that the lanes share out (lane k takes candidates
-// k, k + 32, ...; its cell is found by a binary search over the 32 prefix sums in
-// the warp's shared scratch sw[4][32]).  Accepted candidates are appended in stream
-// order with a ballot, so the row lists the stencil cells in order, each cell's atoms
-// in cell order.
 __device__ inline int build_row_warp(int i, const double* __restrict__ x, const SysInfo& S,
                                      const float4* __restrict__ s32, const int4* __restrict__ cunw,
                                      const int* __restrict__ cstart, const int* __restrict__ catoms, float rcf2,
                                      double rc2, float band, int cap, int* __restrict__ row,
-                                     int* __restrict__ offrow, int (*sw)[32]) {
+                                     int* __restrict__ offrow) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const float4 si = s32[i];
@@ -224,8 +217,7 @@ __device__ inline int build_row_warp(int i, const double* __restrict__ x, const 
     int tc[3] = {cw[0] + dx, cw[1] + dy, cw[2] + dz};
     int img[3] = {0, 0, 0};
     bool valid = t < W * W * W;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
+    for (int d = 0; d < 3 && valid; ++d) {
       if (S.periodic[d]) {
         img[d] = floor_div(tc[d], S.nc[d]);
         tc[d] -= img[d] * S.nc[d];
@@ -245,46 +237,24 @@ __device__ inline int build_row_warp(int i, const double* __restrict__ x, const 
       b = cstart[cid];
       len = cstart[cid + 1] - b;
     }
-    int pre = len;   // inclusive warp scan of the candidate counts
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, pre, o);
-      if (lane >= o) pre += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, pre, 31);
-    sw[0][lane] = pre;
-    sw[1][lane] = b;
-    sw[2][lane] = t;
-    sw[3][lane] = pack_off(img[0], img[1], img[2]);
-    __syncwarp();
-    for (int base = 0; base < total; base += 32) {   // warp-uniform
-      const int k = base + lane;
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    const float ox = (float)dx * S.hf[0] - si.x;
+    const float oy = (float)dy * S.hf[1] - si.y;
+    const float oz = (float)dz * S.hf[2] - si.z;
+    const bool self_cell = dx == 0 && dy == 0 && dz == 0;
+    for (int k = 0; k < maxlen; ++k) {
       bool take = false;
-      int j = 0, code = 0;
-      if (k < total) {
-        int lo = 0, hi = 31;   // cell of candidate k: the first c with sw[0][c] > k
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (sw[0][mid] > k) hi = mid;
-          else lo = mid + 1;
-        }
-        const int c = lo;
-        const int tt = sw[2][c];
-        const int ex = tt % W - kStencil, ey = (tt / W) % W - kStencil, ez = tt / (W * W) - kStencil;
-        j = catoms[sw[1][c] + k - (c ? sw[0][c - 1] : 0)];
-        code = pack_off(ex, ey, ez);
-        if (!(j == i && ex == 0 && ey == 0 && ez == 0)) {
+      int j = 0;
+      if (k < len) {
+        j = catoms[b + k];
+        if (!(j == i && self_cell)) {
           const float4 sj = s32[j];
-          const float ddx = (float)ex * S.hf[0] - si.x + sj.x;
-          const float ddy = (float)ey * S.hf[1] - si.y + sj.y;
-          const float ddz = (float)ez * S.hf[2] - si.z + sj.z;
+          const float ddx = ox + sj.x, ddy = oy + sj.y, ddz = oz + sj.z;
           const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
           if (r2f < rcf2 - band) {
             take = true;
           } else if (r2f <= rcf2 + band) {
-            const int ip = sw[3][c];
-            const int im[3] = {off_x(ip), off_y(ip), off_z(ip)};
-            take = exact_within(x, S, i, j, ci, cunw[j], im, rc2);
+            take = exact_within(x, S, i, j, ci, cunw[j], img, rc2);
           }
         }
       }
@@ -292,36 +262,102 @@ __device__ inline int build_row_warp(int i, const double* __restrict__ x, const 
       const int pos = cnt + __popc(m & lt);
       if (take && pos < cap) {
         row[pos] = j;
-        if (offrow) offrow[pos] = code;
+        if (offrow) offrow[pos] = pack_off(dx, dy, dz);
       }
       cnt += __popc(m);
     }
-    __syncwarp();
   }
   return cnt;
 }
 
-constexpr int kBuildWarps = 8;   // warps per 256-thread block of the row builds
+// One thread builds one row (EAM rows of all atoms): scan the 5x5x5 stencil around atom i and append accepted (j, offset) to a row.
+__device__ inline int build_row(int i, const double* __restrict__ x, const SysInfo& S, const float4* __restrict__ s32,
+                                const int4* __restrict__ cunw, const int* __restrict__ cstart,
+                                const int* __restrict__ catoms, float rcf2, double rc2, float band, int cap,
+                                int* __restrict__ row, int* __restrict__ offrow) {
+  const float4 si = s32[i];
+  const int4 ci = cunw[i];
+  const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
+  const float sv[3] = {si.x, si.y, si.z};
+  const float rmax2 = rcf2 + band;
+  int cnt = 0;
+  for (int dz = -kStencil; dz <= kStencil; ++dz) {
+    int tz = cw[2] + dz, iz = 0;
+    if (S.periodic[2]) {
+      iz = floor_div(tz, S.nc[2]);
+      tz -= iz * S.nc[2];
+    } else if (tz < 0 || tz >= S.nc[2]) {
+      continue;
+    }
+    float gz = fmaxf(0.f, fmaxf((float)dz * S.hf[2] - sv[2], sv[2] - (float)(dz + 1) * S.hf[2]));
+    for (int dy = -kStencil; dy <= kStencil; ++dy) {
+      int ty = cw[1] + dy, iy = 0;
+      if (S.periodic[1]) {
+        iy = floor_div(ty, S.nc[1]);
+        ty -= iy * S.nc[1];
+      } else if (ty < 0 || ty >= S.nc[1]) {
+        continue;
+      }
+      float gy = fmaxf(0.f, fmaxf((float)dy * S.hf[1] - sv[1], sv[1] - (float)(dy + 1) * S.hf[1]));
+      if (gz * gz + gy * gy > rmax2) continue;
+      for (int dx = -kStencil; dx <= kStencil; ++dx) {
+        int tx = cw[0] + dx, ix = 0;
+        if (S.periodic[0]) {
+          ix = floor_div(tx, S.nc[0]);
+          tx -= ix * S.nc[0];
+        } else if (tx < 0 || tx >= S.nc[0]) {
+          continue;
+        }
+        float gx = fmaxf(0.f, fmaxf((float)dx * S.hf[0] - sv[0], sv[0] - (float)(dx + 1) * S.hf[0]));
+        if (gz * gz + gy * gy + gx * gx > rmax2) continue;
+        int cid = S.cell_base + (tz * S.nc[1] + ty) * S.nc[0] + tx;
+        int b = cstart[cid], e = cstart[cid + 1];
+        const float ox = (float)dx * S.hf[0] - si.x;
+        const float oy = (float)dy * S.hf[1] - si.y;
+        const float oz = (float)dz * S.hf[2] - si.z;
+        for (int a = b; a < e; ++a) {
+          int j = catoms[a];
+          if (j == i && dx == 0 && dy == 0 && dz == 0) continue;
+          float4 sj = s32[j];
+          float ddx = ox + sj.x, ddy = oy + sj.y, ddz = oz + sj.z;
+          float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
+          if (r2f > rcf2 + band) continue;
+          bool take = r2f < rcf2 - band;
+          if (!take) {
+            int img[3] = {ix, iy, iz};
+            take = exact_within(x, S, i, j, ci, cunw[j], img, rc2);
+          }
+          if (take) {
+            if (cnt < cap) {
+              row[cnt] = j;
+              if (offrow) offrow[cnt] = pack_off(dx, dy, dz);
+            }
+            ++cnt;
+          }
+        }
+      }
+    }
+  }
+  return cnt;
+}
 
-// One warp per atom, the atoms taken in cell order.
-__global__ void __launch_bounds__(kBuildWarps * 32) k_build_eam(
-    int n, const double* __restrict__ x, const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
-    const float4* __restrict__ s32, const int4* __restrict__ cunw, const int* __restrict__ cstart,
-    const int* __restrict__ catoms, float rcf2, double rc2, float band, int cap, int* __restrict__ nbr,
-    int* __restrict__ off, int* __restrict__ cnt, DevScalars* sc) {
-  __shared__ int s_scan[kBuildWarps][4][32];
-  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (t >= n) return;   // warp-uniform
+__global__ void k_build_eam(int n, const double* __restrict__ x, const SysInfo* __restrict__ sys,
+                            const int* __restrict__ atom_sys, const float4* __restrict__ s32,
+                            const int4* __restrict__ cunw, const int* __restrict__ cstart,
+                            const int* __restrict__ catoms, float rcf2, double rc2, float band, int cap,
+                            int* __restrict__ nbr, int* __restrict__ off, int* __restrict__ cnt, DevScalars* sc) {
+  // Threads take the atoms in cell order: the atoms of one cell walk the same stencil
+  // cells with the same atom counts, so a warp diverges only on the per-atom gap test.
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
   const int i = catoms[t];
   const SysInfo& S = sys_of(sys, atom_sys, i);
-  const int c = build_row_warp(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, band, cap, nbr + (size_t)i * cap,
-                               off ? off + (size_t)i * cap : nullptr, s_scan[threadIdx.x >> 5]);
-  if ((threadIdx.x & 31) == 0) {
-    cnt[i] = c < cap ? c : cap;
-    if (c > cap) {
-      atomicMax(&sc->need_eam, c);
-      atomicOr(&sc->err, kErrCapacity);
-    }
+  int c = build_row(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, band, cap, nbr + (size_t)i * cap,
+                    off ? off + (size_t)i * cap : nullptr);
+  cnt[i] = c < cap ? c : cap;
+  if (c > cap) {
+    atomicMax(&sc->need_eam, c);
+    atomicOr(&sc->err, kErrCapacity);
   }
 }
 
@@ -332,14 +368,13 @@ __global__ void __launch_bounds__(256) k_build_ace(const int* __restrict__ queue
                                                    const int* __restrict__ catoms, float rcf2, double rc2,
                                                    float band, int cap, int* __restrict__ nbr, int* __restrict__ off,
                                                    int* __restrict__ cnt, DevScalars* sc) {
-  __shared__ int s_scan[kBuildWarps][4][32];
   const int m = *nq;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < m; q += warps) {
     const int i = queue[q];
     const SysInfo& S = sys_of(sys, atom_sys, i);
     const int c = build_row_warp(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, band, cap, nbr + (size_t)q * cap,
-                                 off ? off + (size_t)q * cap : nullptr, s_scan[threadIdx.x >> 5]);
+                                 off ? off + (size_t)q * cap : nullptr);
     if ((threadIdx.x & 31) == 0) {
       cnt[q] = c < cap ? c : cap;
       if (c > cap) {
@@ -426,7 +461,7 @@ static constexpr float kBand = 1e-3f;   // guard band on r^2 (A^2) around the cu
 void launch_build_eam(ap_ctx* c, const double* d_x, cudaStream_t s) {
   double r = c->cfg.eam_rc + c->cfg.skin;
   double rc2 = r * r;
-  k_build_eam<<<nblk(c->n, kBuildWarps), kBuildWarps * 32, 0, s>>>((int)c->n, d_x, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
+  k_build_eam<<<nblk(c->n, 128), 128, 0, s>>>((int)c->n, d_x, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
                                               c->d_cell_start, c->d_cell_atoms, (float)rc2, rc2, kBand, c->cap_eam,
                                               c->d_nbr_eam, c->stored_off ? c->d_off_eam : nullptr, c->d_cnt_eam,
                                               c->d_sc);
