@@ -535,13 +535,6 @@ ap_status ap_create(const ap_config* h_cfg, ap_ctx** out) {
   upload_ace_tables(c);
   e = cudaMalloc(&c->d_sc, sizeof(DevScalars));
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_sc, sizeof(DevScalars));
-  if (e == cudaSuccess) {
-    int least = 0, greatest = 0;
-    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s_ace, cudaStreamNonBlocking, greatest);
-  }
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemset(c->d_sc, 0, sizeof(DevScalars));
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -572,9 +565,6 @@ void ap_destroy(ap_ctx* c) {
     if (p) cudaFree(p);
   if (c->h_sc) cudaFreeHost(c->h_sc);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-  if (c->ev_join) cudaEventDestroy(c->ev_join);
-  if (c->s_ace) cudaStreamDestroy(c->s_ace);
   delete c;
 }
 
@@ -852,21 +842,15 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
       PhaseTimer t(c, s, AP_PHASE_NEIGHBORS);
       launch_shadow(c, d_x, s);
     }
-    // EAM and ACE are independent until the finalize: ACE on s_ace (highest priority,
-    // enqueued first so its persistent blocks are placed first), EAM on s.
-    CK(cudaEventRecord(c->ev_fork, s));
-    CK(cudaStreamWaitEvent(c->s_ace, c->ev_fork, 0));
-    {
-      PhaseTimer t(c, c->s_ace, AP_PHASE_ACE);
-      CK(cudaMemsetAsync(c->d_eprec, 0, sizeof(double) * (size_t)n, c->s_ace));
-      launch_ace(c, c->d_lam_int, c->d_precise, c->d_eprec, true, c->s_ace);
-    }
     {
       PhaseTimer t(c, s, AP_PHASE_EAM);
       launch_eam(c, c->d_lam_int, c->d_efast, d_f, false, s);
     }
-    CK(cudaEventRecord(c->ev_join, c->s_ace));
-    CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+    {
+      PhaseTimer t(c, s, AP_PHASE_ACE);
+      CK(cudaMemsetAsync(c->d_eprec, 0, sizeof(double) * (size_t)n, s));
+      launch_ace(c, c->d_lam_int, c->d_precise, c->d_eprec, true, s);
+    }
     {
       PhaseTimer t(c, s, AP_PHASE_OTHER);
       launch_ace_finalize(c, d_f, s);

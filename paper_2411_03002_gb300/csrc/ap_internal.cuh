@@ -273,10 +273,6 @@ struct ap_ctx {
   // profiling (ap_profile_enable / ap_profile_read)
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;   // reusable events
-  // ap_step runs the ACE kernels on s_ace (highest priority) concurrently with the EAM
-  // passes on the caller's stream, between a fork and a join event.
-  cudaStream_t s_ace = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   struct EvSpan {
     int phase, start, end;
   };
