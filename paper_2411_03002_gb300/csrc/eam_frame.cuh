@@ -44,17 +44,21 @@ __device__ inline double rexp(double v) { return exp(v); }
 __device__ inline float rsqrt_(float v) { return rsqrtf(v); }
 __device__ inline double rsqrt_(double v) { return rsqrt(v); }
 // Tuning parameters of the EAM passes (compile-time): lanes per atom, minimum
-// resident blocks per SM (register cap), and the FP32 reciprocal (1: approximate
-// MUFU reciprocal, 0: correctly rounded).
+// resident blocks per SM (register cap), unroll depth of the neighbour loops, and
+// the FP32 reciprocal (1: approximate MUFU reciprocal, 0: correctly rounded).
 #ifndef AP_EAM_LANES
 #define AP_EAM_LANES 4
 #endif
 #ifndef AP_EAM_MINB
 #define AP_EAM_MINB 6   // FP32 only: <= 42 registers, 48 resident warps per SM
 #endif
+#ifndef AP_EAM_UNROLL
+#define AP_EAM_UNROLL 4   // unroll depth of the per-lane neighbour loops
+#endif
 #ifndef AP_EAM_FAST_RCP
 #define AP_EAM_FAST_RCP 1
 #endif
+constexpr int kEamUnroll = AP_EAM_UNROLL;   // (#pragma unroll takes a constant expression, not a macro)
 
 __device__ inline float rcp_(float v) {
 #if AP_EAM_FAST_RCP

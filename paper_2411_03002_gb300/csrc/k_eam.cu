@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   const int c = active ? cnt[i] : 0;
   const size_t row = (size_t)i * cap;
   R rho = R(0);
-#pragma unroll 4
+#pragma unroll kEamUnroll
   for (int t = sub; t < c; t += G) {
     const int j = nbr[row + t];
     const auto sj = sh[j];
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   const int c = active ? cnt[i] : 0;
   const size_t row = (size_t)i * cap;
   R fx = R(0), fy = R(0), fz = R(0), phi = R(0);
-#pragma unroll 4
+#pragma unroll kEamUnroll
   for (int t = sub; t < c; t += G) {
     const int j = nbr[row + t];
     const auto sj = sh[j];
