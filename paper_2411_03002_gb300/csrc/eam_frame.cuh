@@ -50,10 +50,10 @@ __device__ inline double rsqrt_(double v) { return rsqrt(v); }
 #define AP_EAM_LANES 4
 #endif
 #ifndef AP_EAM_MINB
-#define AP_EAM_MINB 6   // FP32 only: <= 42 registers, 48 resident warps per SM
+#define AP_EAM_MINB 5   // FP32 only: <= 51 registers, 40 resident warps per SM
 #endif
 #ifndef AP_EAM_UNROLL
-#define AP_EAM_UNROLL 4   // unroll depth of the per-lane neighbour loops
+#define AP_EAM_UNROLL 8   // unroll depth of the per-lane neighbour loops
 #endif
 #ifndef AP_EAM_FAST_RCP
 #define AP_EAM_FAST_RCP 1
