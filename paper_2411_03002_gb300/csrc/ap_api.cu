@@ -197,7 +197,9 @@ ap_status ensure_capacity(ap_ctx* c, int64_t n) {
   CK(dalloc(c->d_changeable, m));
   {
     const size_t rb = c->cfg.precision == AP_PREC_FP64 ? sizeof(double) : sizeof(float);
-    CK(dalloc(c->d_ace_slots, (size_t)m * 192));
+    if (c->d_ace_list) cudaFree(c->d_ace_list);
+    c->d_ace_list = nullptr;
+    CK(cudaMalloc(&c->d_ace_list, rb * 4 * 192 * (size_t)m));
     CK(dalloc(c->d_ace_nin, m));
     CK(dalloc(c->d_ace_e12, m));
     CK(dalloc(c->d_ace_e3, m));
@@ -554,7 +556,7 @@ void ap_destroy(ap_ctx* c) {
                   c->d_nbr_ace, c->d_off_ace, c->d_cnt_ace, c->d_csp, c->d_csp_slow, c->d_csp_avg, c->d_lam0, c->d_lam_min,
                   c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected,
                   c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_efast, c->d_eprec,
-                  c->d_eatom, c->d_eext, c->d_changeable, c->d_W32, c->d_W64, c->d_ace_slots, c->d_ace_nin,
+                  c->d_eatom, c->d_eext, c->d_changeable, c->d_W32, c->d_W64, c->d_ace_list, c->d_ace_nin,
                   c->d_ace_a48, c->d_ace_dA, c->d_ace_e12, c->d_ace_de3, c->d_ace_e3, c->d_ace_dAb, c->d_ace_e12b,
                   c->d_ace_fs, c->d_scan_tmp, c->d_red,
                   c->d_sel_model, c->d_sel_master, c->d_sel_m1, c->d_sel_m2, c->d_sel_grad, c->d_sel_partial,

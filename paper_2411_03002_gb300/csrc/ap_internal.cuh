@@ -212,7 +212,7 @@ struct ap_ctx {
   float* d_W32 = nullptr;        // [W (320) | M2 (320) | C1 (8)]
   double* d_W64 = nullptr;
   // ACE scratch per precise-queue position (sized for n atoms, working precision)
-  uint16_t* d_ace_slots = nullptr;  // [n][192] row entries inside ace_rc
+  void* d_ace_list = nullptr;       // [n][192] in-range (d_x, d_y, d_z, j) records, working precision
   int* d_ace_nin = nullptr;         // [n]
   void* d_ace_a48 = nullptr;        // [n][48]
   void* d_ace_dA = nullptr;         // [n][200]

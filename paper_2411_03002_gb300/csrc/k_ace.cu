@@ -280,6 +280,8 @@ __device__ inline T warp_sum(T v) {
 __device__ inline float pack_j(int j, float) { return __int_as_float(j); }
 __device__ inline double pack_j(int j, double) { return __longlong_as_double((long long)j); }
 __device__ inline int unpack_j(float v) { return __float_as_int(v); }
+__device__ inline float4 make_r4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+__device__ inline double4_32a make_r4(double a, double b, double c, double d) { return make_double4_32a(a, b, c, d); }
 __device__ inline int unpack_j(double v) { return (int)__double_as_longlong(v); }
 
 constexpr int kListCap = 192;   // neighbours inside ace_rc kept per precise atom (FCC bulk: 134)
@@ -324,7 +326,7 @@ struct AceArgs {
   double* e_prec;
   float4* facc32;
   double* facc64;
-  uint16_t* slots;   // [q][kListCap] row entries inside ace_rc, in row order
+  typename V<R>::R4* list4;   // [q][kListCap] in-range (d, j) records in row order (kernel 1 -> 3)
   int* nin;          // [q] their number
   R* a48;            // [q][48] A entries with n <= 2, l <= 3 (input of nu = 3)
   R* dA;             // [q][200] dE/dA of nu = 1, 2
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
         e[1] = d[1];
         e[2] = d[2];
         e[3] = pack_j(j, R(0));
-        a.slots[(size_t)q * kListCap + pos] = (uint16_t)slot;
+        a.list4[(size_t)q * kListCap + pos] = make_r4(d[0], d[1], d[2], e[3]);
       }
       nin += __popc(mask);
     }
@@ -626,29 +628,21 @@ __global__ void __launch_bounds__(kWarps3<R> * 32, sizeof(R) == 4 ? AP_ACE3_MINB
       U[o] = s * a.inv_n0;
     }
     __syncwarp();
-    const SysInfo& S = a.sys[a.atom_sys ? a.atom_sys[i] : 0];
-    const auto si = a.sh[i];
-    const size_t row = (size_t)q * a.cap;
     const int nin = a.nin[q];
     const R wgt = (R)(a.wgt ? a.wgt[i] : 1.0 - (a.lam ? a.lam[i] : 0.0));
     R pix = R(0), piy = R(0), piz = R(0);
-    // the row entry and neighbour index of the lane's next pair are loaded one
-    // iteration ahead, so only the neighbour-shadow load is exposed per pair
-    int ent_n = 0, j_n = 0;
-    if (lane < nin) {
-      ent_n = a.slots[(size_t)q * kListCap + lane];
-      j_n = a.nbr[row + ent_n];
-    }
+    // the pair records kernel 1 kept (displacement and j, coalesced), the lane's next
+    // one loaded an iteration ahead
+    const typename V<R>::R4* lst = a.list4 + (size_t)q * kListCap;
+    typename V<R>::R4 e_n = make_r4(R(0), R(0), R(0), R(0));
+    if (lane < nin) e_n = lst[lane];
     for (int base = 0; base < nin; base += 32) {
       const int slot = base + lane;
-      const int ent = ent_n, j = j_n;
-      if (slot + 32 < nin) {
-        ent_n = a.slots[(size_t)q * kListCap + slot + 32];
-        j_n = a.nbr[row + ent_n];
-      }
+      const auto e = e_n;
+      if (slot + 32 < nin) e_n = lst[slot + 32];
       if (slot >= nin) continue;
-      R d[3];
-      pair_disp<R>(S, si, a.sh[j], a.off, row + ent, d);
+      const int j = unpack_j(e.w);
+      const R d[3] = {e.x, e.y, e.z};
       R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
       R ir = rsqrt_(r2);
       R ux = d[0] * ir, uy = d[1] * ir, uz = d[2] * ir;
@@ -753,7 +747,7 @@ void run_ace(ap_ctx* c, const double* d_lam, const double* d_wgt, const int* d_q
   a.inv_n0 = (R)(1.0 / c->cfg.ace_n0);
   a.mode = c->cfg.fcut_mode;
   a.e_prec = d_e_prec;
-  a.slots = c->d_ace_slots;
+  a.list4 = reinterpret_cast<typename V<R>::R4*>(c->d_ace_list);
   a.nin = c->d_ace_nin;
   a.a48 = reinterpret_cast<R*>(c->d_ace_a48);
   a.dA = reinterpret_cast<R*>(c->d_ace_dA);
