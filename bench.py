@@ -47,11 +47,10 @@ ADJ_FLOP_PER_ATOM = 3300
 # nu = 1, 2 energy and gradient (~7000) and the nu = 3 monomials (~11400).
 ACE_FLOP_PER_PAIR = ADJ_FLOP_PER_PAIR + 520
 ACE_FLOP_PER_ATOM = ADJ_FLOP_PER_ATOM + 7000 + 11400
-# DRAM bytes (read + write) of one k_ace_adjoint launch on this workload: the ncu
-# capture of the 500k-atom case (60,000 precise atoms; 383.0 GB/s over 346.5 us = 132.7 MB,
-# taken on the current kernel) scaled by the precise atoms to 240,000
-# (profiles/k_ace_adjoint_slab50_mixed.md).
-ADJ_TRAFFIC_BYTES = 132.7e6 * 240000 / 60000
+# DRAM bytes (read + write) of one k_ace_adjoint launch on this workload, from an ncu
+# capture of the current kernel (profiles/k_ace_adjoint_slab50_mixed.md); None until the
+# kernel that now reads the basis kernel's pair records has been captured.
+ADJ_TRAFFIC_BYTES = None
 # FP32 SIMT peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 

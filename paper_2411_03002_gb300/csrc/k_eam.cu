@@ -80,11 +80,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   for (int t = sub; t < c; t += G) {
     const int j = nbr[row + t];
     const auto sj = sh[j];
+#if !AP_EAM_LATE_Q
     const auto qj = q[j];
+#endif
     R d[3];
     fr.disp(sj, off, row + t, d);
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     if (r2 < p.rc2) {
+#if AP_EAM_LATE_Q
+      const auto qj = q[j];   // only the in-range entries gather (lambda xi', lambda)
+#endif
       const R inv_r = rsqrt_(r2);
       const R r = r2 * inv_r;
       R dzeta, ph, dphi;
