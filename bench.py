@@ -47,10 +47,11 @@ ADJ_FLOP_PER_ATOM = 3300
 # nu = 1, 2 energy and gradient (~7000) and the nu = 3 monomials (~11400).
 ACE_FLOP_PER_PAIR = ADJ_FLOP_PER_PAIR + 520
 ACE_FLOP_PER_ATOM = ADJ_FLOP_PER_ATOM + 7000 + 11400
-# DRAM bytes (read + write) of one k_ace_adjoint launch on this workload, from an ncu
-# capture of the current kernel (profiles/k_ace_adjoint_slab50_mixed.md); None until the
-# kernel that now reads the basis kernel's pair records has been captured.
-ADJ_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one k_ace_adjoint launch on this workload: the ncu capture
+# of the current kernel on the 500k-atom case (60,000 precise atoms: 185.6 MB read, mostly
+# the basis kernel's pair records, + 0.7 MB written) scaled by the precise atoms to 240,000
+# (profiles/k_ace_adjoint_slab50_mixed.md).
+ADJ_TRAFFIC_BYTES = 186.3e6 * 240000 / 60000
 # FP32 SIMT peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
