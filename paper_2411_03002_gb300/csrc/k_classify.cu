@@ -411,6 +411,10 @@ __global__ void k_compact(int n, const int* __restrict__ flag, const int* __rest
 // lanes share out (lane k takes candidates k, k + 32, ...; its cell is found by a
 // binary search over the 32 prefix sums), so lanes stay busy whatever the cells hold.
 constexpr int kSpreadWarps = 8;
+#ifndef AP_SPREAD_UNROLL
+#define AP_SPREAD_UNROLL 1   // unroll depth of the per-lane candidate loop (compile-time tuning)
+#endif
+constexpr int kSpreadUnroll = AP_SPREAD_UNROLL;
 
 __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
     const int* __restrict__ det, const int* __restrict__ n_det, const double* __restrict__ x,
@@ -479,6 +483,9 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
       s_t[wib][lane] = t;
       s_img[wib][lane] = imgp;
       __syncwarp();
+#if AP_SPREAD_UNROLL > 1
+#pragma unroll kSpreadUnroll
+#endif
       for (int k = lane; k < total; k += 32) {
         // cell of candidate k: the first c with s_pre[c] > k
         int lo = 0, hi = 31;

@@ -270,6 +270,12 @@ __device__ inline int build_row_warp(int i, const double* __restrict__ x, const 
   return cnt;
 }
 
+// Unroll depth of the per-cell candidate loop of the EAM row build (compile-time tuning).
+#ifndef AP_BUILD_UNROLL
+#define AP_BUILD_UNROLL 1
+#endif
+constexpr int kBuildUnroll = AP_BUILD_UNROLL;
+
 // One thread builds one row (EAM rows of all atoms): scan the 5x5x5 stencil around atom i and append accepted (j, offset) to a row.
 __device__ inline int build_row(int i, const double* __restrict__ x, const SysInfo& S, const float4* __restrict__ s32,
                                 const int4* __restrict__ cunw, const int* __restrict__ cstart,
@@ -315,6 +321,9 @@ __device__ inline int build_row(int i, const double* __restrict__ x, const SysIn
         const float ox = (float)dx * S.hf[0] - si.x;
         const float oy = (float)dy * S.hf[1] - si.y;
         const float oz = (float)dz * S.hf[2] - si.z;
+#if AP_BUILD_UNROLL > 1
+#pragma unroll kBuildUnroll
+#endif
         for (int a = b; a < e; ++a) {
           int j = catoms[a];
           if (j == i && dx == 0 && dy == 0 && dz == 0) continue;
