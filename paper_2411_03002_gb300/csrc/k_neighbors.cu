@@ -272,7 +272,7 @@ __device__ inline int build_row_warp(int i, const double* __restrict__ x, const 
 
 // Unroll depth of the per-cell candidate loop of the EAM row build (compile-time tuning).
 #ifndef AP_BUILD_UNROLL
-#define AP_BUILD_UNROLL 1
+#define AP_BUILD_UNROLL 2
 #endif
 constexpr int kBuildUnroll = AP_BUILD_UNROLL;
 
