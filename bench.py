@@ -54,6 +54,23 @@ ACE_FLOP_PER_ATOM = ADJ_FLOP_PER_ATOM + 7000 + 11400
 ADJ_TRAFFIC_BYTES = 186.3e6 * 240000 / 60000
 # FP32 SIMT peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Algorithmic bytes of one k_eam_force launch (the largest kernel of the step): the row
+# entries (4 B each) plus, per atom, its own shadow, (lambda xi', lambda), xi and row count
+# (16 + 8 + 8 + 4 B), its force and E^f (24 + 8 B), and one read of its shadow and q as
+# some other atom's neighbour (24 B): 4 E + 92 n.
+EAM_FORCE_BYTES_PER_ENTRY = 4
+EAM_FORCE_BYTES_PER_ATOM = 92
+# DRAM bytes of one k_eam_force launch from an ncu capture of the current kernel, or None.
+EAM_FORCE_TRAFFIC_BYTES = None
+
+
+def hbm_peak():
+    """(GB/s, source) from MEASURED_PEAKS.json, else the profiling recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s)"
 
 
 def parse():
@@ -249,6 +266,11 @@ def run_ours(args, ws, rank, local):
     flops = ACE_FLOP_PER_PAIR * prof["ace_pairs"] + ACE_FLOP_PER_ATOM * prof["ace_atoms"]
     adj_flops = ADJ_FLOP_PER_PAIR * prof["ace_pairs"] + ADJ_FLOP_PER_ATOM * prof["ace_atoms"]
     achieved = adj_flops / (adj_ms / 1e3) / 1e12 if adj_ms > 0 else 0.0
+    ef_ms, ef_calls = prof["phases"]["eam_force"]               # a sub-phase of "eam"
+    eam_entries = ctx.neighbor_total(0)
+    ef_bytes = EAM_FORCE_BYTES_PER_ENTRY * eam_entries + EAM_FORCE_BYTES_PER_ATOM * w.n
+    ef_gbs = ef_bytes / (ef_ms / max(1, ef_calls) / 1e3) / 1e9 if ef_ms > 0 else 0.0
+    hbm_gbs, hbm_src = hbm_peak()
     top = {k: v for k, v in prof["phases"].items() if k != "ace_adjoint"}
     phase_share = {k: round(m / max(1e-9, sum(p[0] for p in top.values())), 4) for k, (m, c) in top.items()}
 
@@ -379,7 +401,12 @@ def run_ours(args, ws, rank, local):
             "e2e": {"value": atom_steps / (ms_e2e / 1e3), "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": prof["kernels"],
-            "roofline": {"bound": "alu", "kernel": "k_ace_adjoint (ACE force stage)",
+            "roofline": {"bound": "hbm", "kernel": "k_eam_force (EAM force pass, the largest kernel of the step)",
+                         "achieved": ef_gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": ef_gbs / hbm_gbs,
+                         "traffic": EAM_FORCE_TRAFFIC_BYTES, "peak_source": hbm_src,
+                         "algorithmic_bytes_per_launch": ef_bytes, "eam_row_entries": eam_entries,
+                         "ms_per_launch": ef_ms / max(1, ef_calls)},
+            "roofline_ace_adjoint": {"bound": "alu", "kernel": "k_ace_adjoint (ACE force stage)",
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ADJ_TRAFFIC_BYTES,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived, not measured)",

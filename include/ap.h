@@ -225,6 +225,14 @@ ap_status ap_build_neighbors_batch(ap_ctx* ctx, int32_t n_sys, const int64_t* h_
 ap_status ap_get_neighbors(ap_ctx* ctx, int32_t which, int32_t* d_cnt, int32_t* d_idx, int32_t* d_shift, int64_t cap,
                            int64_t* h_rows);
 
+/* Total number of entries in the current EAM rows (which = 0) or ACE rows (which = 1,
+ * the precise queue's rows), summed on the device by one reduction kernel; *h_total
+ * is a host pointer.  Synchronises the legacy default stream.  No paper counterpart:
+ * instrumentation (the EAM passes read these entries every MD step).  Errors:
+ * AP_ERR_STATE before ap_build_neighbors, AP_ERR_ARG for a null pointer or another
+ * `which`. */
+ap_status ap_neighbor_total(ap_ctx* ctx, int32_t which, int64_t* h_total);
+
 /* ----------------------------------------------------------------- lambda */
 
 /* One lambda update (Appendix B) from the current neighbour rows, in FP64 with
@@ -393,7 +401,8 @@ ap_status ap_eval_eam_static(const ap_config* h_cfg, int64_t n, const double* d_
 #define AP_PHASE_OTHER 4       /* integrator, finalize, indenter, reductions      */
 #define AP_PHASE_THERMOSTAT 5  /* local thermostat: difference forces, Delta E, corrections */
 #define AP_PHASE_ACE_ADJOINT 6 /* k_ace_adjoint alone (the force stage; also counted in ACE) */
-#define AP_NUM_PHASES 7
+#define AP_PHASE_EAM_FORCE 7   /* k_eam_force alone (the force pass; also counted in EAM)   */
+#define AP_NUM_PHASES 8
 
 /* Turn per-phase event timing in ap_step on (1) or off (0) and clear the totals.
  * No paper counterpart: instrumentation of this implementation. */

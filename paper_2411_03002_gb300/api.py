@@ -189,6 +189,12 @@ class Context:
         self.n = int(offsets[-1])
         self._ck(self.lib.ap_build_neighbors_batch(self.h, ns, off, arr, _ptr(x), _ptr(species), _stream(stream)))
 
+    def neighbor_total(self, which: int = 0) -> int:
+        """Total entries of the current EAM (0) or ACE (1) rows (synchronises)."""
+        t = ctypes.c_int64()
+        self._ck(self.lib.ap_neighbor_total(self.h, which, ctypes.byref(t)))
+        return t.value
+
     def get_neighbors(self, which: int = 0, cap: int = 320):
         """(cnt [rows], idx [rows, cap], shift [rows, cap, 3]) as CUDA int32 tensors."""
         rows = ctypes.c_int64()
@@ -266,7 +272,7 @@ class Context:
         return StepStats(st.step, st.n_precise, st.n_detected, st.rebuilds, st.e_pot, st.e_kin, st.max_disp,
                          st.error_bits, st.th_corrected, st.th_refused, st.th_energy)
 
-    PHASES = ("neighbors", "classify", "eam", "ace", "other", "thermostat", "ace_adjoint")
+    PHASES = ("neighbors", "classify", "eam", "ace", "other", "thermostat", "ace_adjoint", "eam_force")
 
     def profile_enable(self, on: bool = True):
         self._ck(self.lib.ap_profile_enable(self.h, 1 if on else 0))

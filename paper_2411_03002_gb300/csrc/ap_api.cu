@@ -652,6 +652,22 @@ ap_status ap_get_neighbors(ap_ctx* c, int32_t which, int32_t* d_cnt, int32_t* d_
   return AP_OK;
 }
 
+ap_status ap_neighbor_total(ap_ctx* c, int32_t which, int64_t* h_total) {
+  if (!c) return AP_ERR_ARG;
+  if (!h_total) return fail(c, AP_ERR_ARG, "null argument");
+  if (!c->built) return fail(c, AP_ERR_STATE, "no neighbour build yet");
+  if (which != 0 && which != 1) return fail(c, AP_ERR_ARG, "which must be 0 (EAM) or 1 (ACE)");
+  ap_status st = read_scalars(c, 0);
+  if (st) return st;
+  const int64_t rows = which == 0 ? c->n : c->h_sc->n_precise;
+  launch_row_total(c, which, (int)rows, 0);
+  unsigned long long t = 0;
+  CK(cudaMemcpy(&t, &c->d_sc->row_total, sizeof(t), cudaMemcpyDeviceToHost));
+  CK(cudaGetLastError());
+  *h_total = (int64_t)t;
+  return AP_OK;
+}
+
 ap_status ap_classify(ap_ctx* c, int64_t n, const double* d_x, const uint8_t* d_changeable, double* d_lam,
                       int32_t* d_precise_idx, int64_t* d_n_precise, void* stream) {
   if (!c) return AP_ERR_ARG;

@@ -78,6 +78,7 @@ struct DevScalars {
   int work_counter;   // persistent-kernel work counter
   int work_counter2;  // second persistent-kernel work counter (right after work_counter)
   int n_csp_slow;     // atoms handed from the FP32 CSP kernel to the exact one
+  unsigned long long row_total;   // ap_neighbor_total's result
   unsigned int max_disp2_bits;  // float bits of the largest squared displacement
   long long n_precise64;
   double e_total;
@@ -294,6 +295,7 @@ void launch_bin(ap_ctx* c, const double* d_x, const int32_t* d_species, cudaStre
 void launch_cell_sort(ap_ctx* c, cudaStream_t s);
 void launch_shadow(ap_ctx* c, const double* d_x, cudaStream_t s);
 void launch_build_eam(ap_ctx* c, const double* d_x, cudaStream_t s);
+void launch_row_total(ap_ctx* c, int which, int rows, cudaStream_t s);   // -> c->d_sc->row_total
 void launch_build_ace(ap_ctx* c, const double* d_x, const int* d_queue, const int* d_nq, cudaStream_t s);
 void launch_export_rows(ap_ctx* c, int which, int rows, int cap_out, int* d_cnt, int* d_idx, int* d_shift,
                         cudaStream_t s);

@@ -131,9 +131,11 @@ void run_eam(ap_ctx* c, const P& p, const typename Shadow<R>::T* sh, const doubl
   const int* off = STORED ? c->d_off_eam : nullptr;
   k_eam_density<R, G, STORED, P><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam,
                                                          off, c->d_cnt_eam, c->cap_eam, p, d_lam, q, c->d_xi);
+  const int t0 = prof_mark(c, s);
   k_eam_force<R, G, STORED, P><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam, off,
                                                        c->d_cnt_eam, c->cap_eam, p, q, c->d_xi, d_e_fast, d_f,
                                                        accumulate ? 1 : 0);
+  prof_add(c, AP_PHASE_EAM_FORCE, t0, prof_mark(c, s));
   c->kernels += 2;
 }
 

@@ -467,6 +467,29 @@ void launch_shadow(ap_ctx* c, const double* d_x, cudaStream_t s) {
 
 static constexpr float kBand = 1e-3f;   // guard band on r^2 (A^2) around the cutoff
 
+// Sum of the row counts (block sums, one 64-bit atomic per block).
+__global__ void k_row_total(int rows, const int* __restrict__ cnt, unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long part[8];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long v = i < rows ? (unsigned long long)cnt[i] : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+    atomicAdd(out, s);
+  }
+}
+
+void launch_row_total(ap_ctx* c, int which, int rows, cudaStream_t s) {
+  cudaMemsetAsync(&c->d_sc->row_total, 0, sizeof(unsigned long long), s);
+  if (rows > 0)
+    k_row_total<<<nblk(rows, 256), 256, 0, s>>>(rows, which == 0 ? c->d_cnt_eam : c->d_cnt_ace,
+                                                &c->d_sc->row_total);
+}
+
 void launch_build_eam(ap_ctx* c, const double* d_x, cudaStream_t s) {
   double r = c->cfg.eam_rc + c->cfg.skin;
   double rc2 = r * r;

@@ -288,3 +288,17 @@ def test_precise_queue_from_lambda(c1):
     assert np.array_equal(idx[:k].cpu().numpy(), np.nonzero(lam < 1.0)[0])
     idx, cnt = ctx.precise_queue(T(np.ones(c1.n)))
     assert int(cnt.item()) == 0
+
+
+def test_neighbor_total_is_the_sum_of_the_row_counts(c1):
+    """ap_neighbor_total (instrumentation) against the exported EAM and ACE row counts."""
+    w = c1
+    ctx = ctx_for(w, ap.PREC_FP64)
+    x = T(w.x)
+    ctx.build_neighbors(x, w.box)
+    cnt, _, _ = ctx.get_neighbors(0)
+    assert ctx.neighbor_total(0) == int(cnt.sum().item()) > 0
+    lam, q, nq = ctx.classify(x)
+    ctx.eval_ace(x, lam, q, nq)
+    cnt1, _, _ = ctx.get_neighbors(1)
+    assert ctx.neighbor_total(1) == int(cnt1.sum().item())
