@@ -60,8 +60,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # some other atom's neighbour (24 B): 4 E + 92 n.
 EAM_FORCE_BYTES_PER_ENTRY = 4
 EAM_FORCE_BYTES_PER_ATOM = 92
-# DRAM bytes of one k_eam_force launch from an ncu capture of the current kernel, or None.
-EAM_FORCE_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one k_eam_force launch: the ncu capture of the current kernel
+# on the 500k-atom case (208.7 MB read + 9.2 MB written) scaled by the atoms to 4,000,000
+# (profiles/k_eam_force_slab50_mixed.md).  It matches the algorithmic bytes: no DRAM re-reads.
+EAM_FORCE_TRAFFIC_BYTES = 218.0e6 * 4000000 / 500000
 
 
 def hbm_peak():
