@@ -186,7 +186,7 @@ ap_status ensure_capacity(ap_ctx* c, int64_t n) {
   CK(dalloc(c->d_lam_int, m));
   void* q = c->d_q;
   if (q) cudaFree(q);
-  CK(cudaMalloc(&c->d_q, 32 * (size_t)m));   // FP32: 32-byte records; FP64: double2
+  CK(cudaMalloc(&c->d_q, 16 * (size_t)m));
   CK(dalloc(c->d_xi, m));
   CK(dalloc(c->d_facc32, m));
   CK(dalloc(c->d_facc64, 3 * m));

@@ -200,7 +200,7 @@ struct ap_ctx {
   double* d_lam_int = nullptr;   // [n] internal lambda (ap_step)
 
   // potentials scratch
-  void* d_q = nullptr;           // [n] FP32: record (shadow, lambda xi', lambda, 0, 0); FP64: (lambda xi', lambda)
+  void* d_q = nullptr;           // [n] (lambda xi', lambda) as float2 or double2
   double* d_xi = nullptr;        // [n] xi(rho)
   float4* d_facc32 = nullptr;    // [n] ACE force accumulator (mixed)
   double* d_facc64 = nullptr;    // [n][3] ACE force accumulator (FP64)

@@ -19,20 +19,6 @@ namespace ap {
 
 namespace {
 
-// FP32 neighbour record of the force pass: (s_x, s_y, s_z, cell code, lambda xi', lambda, 0, 0),
-// 32 bytes, written by the density pass and fetched by the force pass with one 256-bit
-// load, in place of two gathers (shadow and q).
-struct __align__(32) Rec8 {
-  float v[8];
-};
-
-__device__ __forceinline__ void ld_rec8(const Rec8* p, float4& s, float2& q) {
-  float pad0, pad1;
-  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=f"(s.x), "=f"(s.y), "=f"(s.z), "=f"(s.w), "=f"(q.x), "=f"(q.y), "=f"(pad0), "=f"(pad1)
-               : "l"(p));
-}
-
 template <typename R, int G, bool STORED, typename P>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam_density(int n, const SysInfo* __restrict__ sys,
                                                      const int* __restrict__ atom_sys,
@@ -66,13 +52,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
     const R li = lam ? (R)lam[i] : R(1);
     R xi, dxi;
     p.embed(rho, xi, dxi);
-    if constexpr (sizeof(R) == 4) {
-      float4* r = reinterpret_cast<float4*>(reinterpret_cast<Rec8*>(q) + i);
-      r[0] = si;
-      r[1] = make_float4(li * dxi, li, 0.f, 0.f);
-    } else {
-      q[i] = Q2<R>::make(li * dxi, li);
-    }
+    q[i] = Q2<R>::make(li * dxi, li);
     xi_out[i] = (double)xi;
   }
 }
@@ -92,29 +72,24 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   const int i = active ? gid : n - 1;
   const auto si = sh[i];
   const Frame<R, STORED> fr(sys[atom_sys ? atom_sys[i] : 0], si);
-  typename Q2<R>::T qi;
-  if constexpr (sizeof(R) == 4)
-    qi = reinterpret_cast<const float2*>(reinterpret_cast<const Rec8*>(q) + i)[2];
-  else
-    qi = q[i];
+  const auto qi = q[i];
   const int c = active ? cnt[i] : 0;
   const size_t row = (size_t)i * cap;
   R fx = R(0), fy = R(0), fz = R(0), phi = R(0);
 #pragma unroll kEamUnroll
   for (int t = sub; t < c; t += G) {
     const int j = nbr[row + t];
-    typename Shadow<R>::T sj;
-    typename Q2<R>::T qj;
-    if constexpr (sizeof(R) == 4) {
-      ld_rec8(reinterpret_cast<const Rec8*>(q) + j, sj, qj);
-    } else {
-      sj = sh[j];
-      qj = q[j];
-    }
+    const auto sj = sh[j];
+#if !AP_EAM_LATE_Q
+    const auto qj = q[j];
+#endif
     R d[3];
     fr.disp(sj, off, row + t, d);
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     if (r2 < p.rc2) {
+#if AP_EAM_LATE_Q
+      const auto qj = q[j];   // only the in-range entries gather (lambda xi', lambda)
+#endif
       const R inv_r = rsqrt_(r2);
       const R r = r2 * inv_r;
       R dzeta, ph, dphi;
