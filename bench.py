@@ -273,7 +273,7 @@ def run_ours(args, ws, rank, local):
     ef_bytes = EAM_FORCE_BYTES_PER_ENTRY * eam_entries + EAM_FORCE_BYTES_PER_ATOM * w.n
     ef_gbs = ef_bytes / (ef_ms / max(1, ef_calls) / 1e3) / 1e9 if ef_ms > 0 else 0.0
     hbm_gbs, hbm_src = hbm_peak()
-    top = {k: v for k, v in prof["phases"].items() if k != "ace_adjoint"}
+    top = {k: v for k, v in prof["phases"].items() if k not in ("ace_adjoint", "eam_force")}   # sub-phases
     phase_share = {k: round(m / max(1e-9, sum(p[0] for p in top.values())), 4) for k, (m, c) in top.items()}
 
     # end-to-end through the public call with host buffers (pinned), copies inside the timed region
