@@ -30,8 +30,8 @@ def fresh_hyb(h):
     return dataclasses.replace(h, n_csp_avg=1, n_lam_avg=1, dlam_min=0.0)
 
 
-def gpu_step(w, hyb, v0, ace_p, thermostat, nsteps=1):
-    cfg = ap.make_config(I.eam_params(0), ace_p, hyb, precision=ap.PREC_FP64, dt=w.dt, lambda_every=1,
+def gpu_step(w, hyb, v0, ace_p, thermostat, nsteps=1, eam_p=None):
+    cfg = ap.make_config(eam_p or I.eam_params(0), ace_p, hyb, precision=ap.PREC_FP64, dt=w.dt, lambda_every=1,
                          thermostat=thermostat)
     ctx = ap.Context(cfg)
     x = torch.as_tensor(w.x, device="cuda").clone()
@@ -45,8 +45,9 @@ def gpu_step(w, hyb, v0, ace_p, thermostat, nsteps=1):
     return s0, s1, v.cpu().numpy()
 
 
-def oracle_step(w, hyb, v0, ace_p):
-    eam, ace = I.eam_params(0), O.ACE(ace_p)
+def oracle_step(w, hyb, v0, ace_p, eam_p=None):
+    eam = eam_p or I.eam_params(0)
+    ace = O.ACEFS(ace_p) if getattr(ace_p, "c2", None) is not None else O.ACE(ace_p)
     m, dt = w.mass, w.dt
     st = O.LambdaState(w.n, hyb.n_csp_avg, hyb.n_lam_avg)
     lam0, *_ = O.classify(st, w.x, w.box, hyb)
@@ -59,7 +60,7 @@ def oracle_step(w, hyb, v0, ace_p):
     ep, _ = ace.eval(x1, w.box)
     dE = TH.delta_v(lam0, lam1, ef, ep) + TH.delta_t(fc, fd, vh, m, dt)
     v1 = vh + 0.5 * dt * fd * O.ACC / m[:, None]
-    v1c, n_ok, n_bad = TH.correct(x1, w.box, v1, m, dE, 6.5, 1.0)
+    v1c, n_ok, n_bad = TH.correct(x1, w.box, v1, m, dE, float(eam.rc) + 1.0, 1.0)   # rows at eam_rc + skin
     return v1, v1c, dE, n_ok, n_bad, float(np.abs(lam1 - lam0).sum())
 
 
@@ -115,3 +116,24 @@ def test_thermostat_conserves_energy_with_changing_lambda():
     drift_off = np.abs(e_off - e_off[0]).max()
     drift_on = np.abs(e_on - e_on[0]).max()
     assert drift_on < 0.01 * drift_off, (drift_on, drift_off)
+
+
+@pytest.mark.parametrize("eam_kind", ["analytic", "mishin"])
+@pytest.mark.parametrize("ace_kind", ["linear", "fs"])
+def test_one_update_step_other_potentials(eam_kind, ace_kind):
+    """The same one-update step with the Mishin EAM2 fast potential and/or the
+    Finnis-Sinclair ACE form: the thermostat's difference forces and Delta V go through
+    both potentials' kernels (the 237-atom cell, FP64, 1e-9 relative)."""
+    w = I.config_c1()
+    hyb = dataclasses.replace(fresh_hyb(I.SINGLE_EVAL), csp_lo=1.0, csp_hi=4.0)
+    v0 = I.maxwell_boltzmann(w.mass, np.ones(w.n, bool), 900.0, np.random.Generator(np.random.PCG64(I.seed_for(9, 6))))
+    ace_p = I.ace_params(0) if ace_kind == "linear" else I.ace_params_fs(0, c2_scale=0.1)
+    eam_p = I.eam_params(0) if eam_kind == "analytic" else I.MISHIN_ORIGINAL
+    w = dataclasses.replace(w, hyb=hyb)
+    v1, v1c, dE, n_ok, n_bad, changes = oracle_step(w, hyb, v0, ace_p, eam_p)
+    assert changes > 0 and n_ok > 0 and n_bad == 0
+    _, s1, v_gpu = gpu_step(w, hyb, v0, ace_p, thermostat=True, eam_p=eam_p)
+    assert s1.th_refused == 0 and s1.th_corrected == n_ok
+    scale = np.abs(v1c).max()
+    assert np.abs(v_gpu - v1c).max() <= 1e-9 * scale, np.abs(v_gpu - v1c).max() / scale
+    assert s1.th_energy == pytest.approx(float(dE.sum()), rel=1e-9, abs=1e-12)
