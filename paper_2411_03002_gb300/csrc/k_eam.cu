@@ -19,6 +19,40 @@ namespace ap {
 
 namespace {
 
+// The per-lane walk over row entries t = sub, sub + G, ... < c, calling body(j, t).
+// AP_EAM_PIPE = 0: one loop unrolled kEamUnroll deep.  AP_EAM_PIPE = 1: groups of
+// kEamUnroll entries, the next group's row entries (DRAM) loaded before the current
+// group's gathers and arithmetic.
+template <int G, typename F>
+__device__ __forceinline__ void walk_row(const int* __restrict__ rowp, int sub, int c, F&& body) {
+#if AP_EAM_PIPE
+  constexpr int U = kEamUnroll;
+  int jn[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int t = sub + G * u;
+    jn[u] = t < c ? rowp[t] : 0;
+  }
+  for (int t0 = sub; t0 < c; t0 += G * U) {
+    int jc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      jc[u] = jn[u];
+      const int t = t0 + G * (U + u);
+      jn[u] = t < c ? rowp[t] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = t0 + G * u;
+      if (t < c) body(jc[u], t);
+    }
+  }
+#else
+#pragma unroll kEamUnroll
+  for (int t = sub; t < c; t += G) body(rowp[t], t);
+#endif
+}
+
 template <typename R, int G, bool STORED, typename P>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam_density(int n, const SysInfo* __restrict__ sys,
                                                      const int* __restrict__ atom_sys,
@@ -36,17 +70,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   const int c = active ? cnt[i] : 0;
   const size_t row = (size_t)i * cap;
   R rho = R(0);
-#pragma unroll kEamUnroll
-  for (int t = sub; t < c; t += G) {
-    const int j = nbr[row + t];
+  walk_row<G>(nbr + row, sub, c, [&](int j, int t) {
     const auto sj = sh[j];
     R d[3];
     fr.disp(sj, off, row + t, d);
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    if (r2 < p.rc2) {
-      rho += p.zeta(r2 * rsqrt_(r2));
-    }
-  }
+    if (r2 < p.rc2) rho += p.zeta(r2 * rsqrt_(r2));
+  });
   rho = group_sum<R, G>(rho);
   if (active && sub == 0) {
     const R li = lam ? (R)lam[i] : R(1);
@@ -76,20 +106,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   const int c = active ? cnt[i] : 0;
   const size_t row = (size_t)i * cap;
   R fx = R(0), fy = R(0), fz = R(0), phi = R(0);
-#pragma unroll kEamUnroll
-  for (int t = sub; t < c; t += G) {
-    const int j = nbr[row + t];
+  walk_row<G>(nbr + row, sub, c, [&](int j, int t) {
     const auto sj = sh[j];
-#if !AP_EAM_LATE_Q
     const auto qj = q[j];
-#endif
     R d[3];
     fr.disp(sj, off, row + t, d);
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     if (r2 < p.rc2) {
-#if AP_EAM_LATE_Q
-      const auto qj = q[j];   // only the in-range entries gather (lambda xi', lambda)
-#endif
       const R inv_r = rsqrt_(r2);
       const R r = r2 * inv_r;
       R dzeta, ph, dphi;
@@ -101,7 +124,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
       fy += s * d[1];
       fz += s * d[2];
     }
-  }
+  });
   fx = group_sum<R, G>(fx);
   fy = group_sum<R, G>(fy);
   fz = group_sum<R, G>(fz);
