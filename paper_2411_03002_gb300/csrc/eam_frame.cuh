@@ -55,9 +55,6 @@ __device__ inline double rsqrt_(double v) { return rsqrt(v); }
 #ifndef AP_EAM_UNROLL
 #define AP_EAM_UNROLL 8   // unroll depth of the per-lane neighbour loops
 #endif
-#ifndef AP_EAM_PIPE
-#define AP_EAM_PIPE 0   // 1: load the next group's row entries before the current group's work
-#endif
 #ifndef AP_EAM_FAST_RCP
 #define AP_EAM_FAST_RCP 1
 #endif

@@ -19,38 +19,13 @@ namespace ap {
 
 namespace {
 
-// The per-lane walk over row entries t = sub, sub + G, ... < c, calling body(j, t).
-// AP_EAM_PIPE = 0: one loop unrolled kEamUnroll deep.  AP_EAM_PIPE = 1: groups of
-// kEamUnroll entries, the next group's row entries (DRAM) loaded before the current
-// group's gathers and arithmetic.
+// The per-lane walk over row entries t = sub, sub + G, ... < c, calling body(j, t),
+// unrolled kEamUnroll deep.  (Loading the next group's row entries ahead of the current
+// group by hand was measured slower than the compiler's schedule of this loop.)
 template <int G, typename F>
 __device__ __forceinline__ void walk_row(const int* __restrict__ rowp, int sub, int c, F&& body) {
-#if AP_EAM_PIPE
-  constexpr int U = kEamUnroll;
-  int jn[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int t = sub + G * u;
-    jn[u] = t < c ? rowp[t] : 0;
-  }
-  for (int t0 = sub; t0 < c; t0 += G * U) {
-    int jc[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      jc[u] = jn[u];
-      const int t = t0 + G * (U + u);
-      jn[u] = t < c ? rowp[t] : 0;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int t = t0 + G * u;
-      if (t < c) body(jc[u], t);
-    }
-  }
-#else
 #pragma unroll kEamUnroll
   for (int t = sub; t < c; t += G) body(rowp[t], t);
-#endif
 }
 
 template <typename R, int G, bool STORED, typename P>
