@@ -324,11 +324,11 @@ def run_ours(args, ws, rank, local):
         # atoms whose full-ACE and full-EAM forces differ by more than the selector's label threshold
         _, fe_ = ev.eval_eam(xs, torch.ones_like(lams))
         mobile = torch.as_tensor(w.fixed, device=dev) == 0
-        # judged region: mobile atoms with no fixed (always-EAM) atom inside the ACE cutoff,
+        # scored region: mobile atoms with no fixed (always-EAM) atom inside the ACE cutoff,
         # since no detector can remove the error that the fixed layers contribute
         z_fixed = float(w.x[w.fixed != 0, 2].max()) if (w.fixed != 0).any() else -1e30
-        judged = mobile & (torch.as_tensor(w.x[:, 2], device=dev) > z_fixed + float(acep.rc))
-        pos = (torch.linalg.vector_norm(fa_ - fe_, dim=1) > float(sel["tau"])) & judged
+        scored = mobile & (torch.as_tensor(w.x[:, 2], device=dev) > z_fixed + float(acep.rc))
+        pos = (torch.linalg.vector_norm(fa_ - fe_, dim=1) > float(sel["tau"])) & scored
         dp = (fh_ - fa_)[pos]
         ev.close()
         del ev
@@ -341,7 +341,7 @@ def run_ours(args, ws, rank, local):
         ds = (fs_ - fa_)[pos]
         extras["selector"] = {
             "model": "paper_2411_03002_gb300/selector_cu.npz (p_lo %.2f, p_hi %.2f)" % (sel["p_lo"], sel["p_hi"]),
-            "label_positive_fraction_of_judged": float((pos.sum() / judged.sum()).item()),
+            "label_positive_fraction_of_scored": float((pos.sum() / scored.sum()).item()),
             "precise_fraction": float((lam_s < 1.0).float().mean().item()),
             "force_err_rms_meV_A_label_positive": float(torch.sqrt((ds * ds).mean()).item() * 1e3),
             "csp_force_err_rms_meV_A_label_positive": float(torch.sqrt((dp * dp).mean()).item() * 1e3),

@@ -85,8 +85,9 @@ typedef struct {
   /* Linear ACE (Eq. energy_ace): E_i = sum_v c_v B_iv.  Radial basis
    * g_k(r) = T_k(2r/rc - 1) f_cut(r/rc), R_nl = sum_k W[l][n][k] g_k (n,k < 8,
    * l <= 4); A_nlm = (1/n0) sum_j R_nl Y_lm; B: nu = 1, 2 (all n1 <= n2, l) and 3
-   * (n <= 2, l <= 3, Gaunt-coupled), 325 functions in the order documented in
-   * the design doc.  ace_c holds ace_nc >= 325 coefficients (extra ignored). */
+   * (n <= 2, l <= 3, Gaunt-coupled), 325 functions ordered nu = 1 by n, nu = 2 by
+   * (n1, n2, l), nu = 3 by (p1 <= p2 <= p3) with p = 4n + l (ap_ace_basis_desc lists
+   * them).  ace_c holds ace_nc >= 325 coefficients (extra ignored). */
   double ace_W[5 * 8 * 8];
   double ace_c[512];
   int32_t ace_nc;

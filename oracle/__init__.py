@@ -15,7 +15,7 @@ Everything is FP64 and follows the paper's definitions in the paper's order:
     (Eq. F_i_d): ``hybrid``;
   * velocity Verlet with the lambda step (Eq. vv): ``md_step``.
 
-Readings where the paper is ambiguous (each one listed in the design doc):
+Readings where the paper is ambiguous:
   * lambda_0 = 1 - f_cut((CSP_hi - CSP_avg)/(CSP_hi - CSP_lo)): the printed argument
     is oriented so that it is 0 for precise and 1 for fast atoms, as Appendix B
     states in words.

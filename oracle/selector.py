@@ -8,8 +8,8 @@ The paper leaves the detection mechanism open: the argument of f_cut in
 Eq. lambda_1_i may come from any detector, provided it is 0 for atoms to be
 treated precisely and 1 for atoms to be treated fast (Appendix B, the remark after
 the definition of f_cut).  The project's learned detector is defined here; the
-centro-symmetry parameter stays in the loop as one feature and as the judge the
-selector is evaluated against.
+centro-symmetry parameter stays in the loop as one feature and as the reference
+detector the selector is evaluated against.
 
 Score.  p_i = sigmoid(MLP(standardised features_i)); it is pushed into the same
 history as the CSP samples would be, averaged over the same window (Eq. csp_2_i

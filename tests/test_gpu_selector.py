@@ -218,5 +218,5 @@ def test_classification_with_the_selector_matches_oracle():
     assert det_o.sum() > 10
     # interior lambda_0 within |f_cut'| <= 1.875 times the score difference over the window
     assert np.abs(l0g - l0o)[~band].max() <= 1.875 * 0.0125 / (p_hi - p_lo) + 1e-12
-    # the CSP sample is still the exact one (kept as the judge)
+    # the CSP sample is still the exact one (kept as the reference detector)
     assert np.array_equal(st["csp"].cpu().numpy(), O.csp(w.x, w.box))
