@@ -35,35 +35,72 @@ import ap_inputs as I  # noqa: E402
 
 MD_PER_STEP = 10
 METRIC = "atom-steps/s adaptive vs full-ACE on 1 GB300 at <=10 meV/A force error"
-# Algorithmic FLOPs of the ACE force stage k_ace_adjoint (the dominant kernel), per
-# neighbour pair within r_c and per precise atom (FMA = 2): per pair the radial
-# functions and derivatives (~100), the solid harmonics and gradients for l <= 4
-# (~400), the two 8-term contractions and the accumulations for 25 (l, m) (~1040)
-# and the scatter (~40); per atom u = W^T dE/dA / N0 (~3300).
+# The step's three largest kernels are instrumented (CUDA events around each launch);
+# `roofline` describes the one with the most measured time, `rooflines` all three.
+#
+# Algorithmic FLOPs of the ACE force stage k_ace_adjoint, per neighbour pair within r_c
+# and per precise atom (FMA = 2): per pair the radial functions and derivatives (~100),
+# the solid harmonics and gradients for l <= 4 (~400), the two 8-term contractions and
+# the accumulations for 25 (l, m) (~1040) and the scatter (~40); per atom
+# u = W^T dE/dA / N0 (~3300).
 ADJ_FLOP_PER_PAIR = 1580
 ADJ_FLOP_PER_ATOM = 3300
-# The whole ACE evaluation (k_ace_basis + k_ace_nu3 + k_ace_adjoint): per pair add the
-# basis stage (g, Y and the G = g^T Y contraction, ~520); per atom add A = W G, the
-# nu = 1, 2 energy and gradient (~7000) and the nu = 3 monomials (~11400).
-ACE_FLOP_PER_PAIR = ADJ_FLOP_PER_PAIR + 520
-ACE_FLOP_PER_ATOM = ADJ_FLOP_PER_ATOM + 7000 + 11400
-# DRAM bytes (read + write) of one k_ace_adjoint launch on this workload: the ncu capture
-# of the current kernel on the 500k-atom case (60,000 precise atoms: 185.6 MB read, mostly
-# the basis kernel's pair records, + 0.7 MB written) scaled by the precise atoms to 240,000
-# (profiles/k_ace_adjoint_slab50_mixed.md).
+# Algorithmic FLOPs of k_ace_basis: per pair g (~30), Y (~70), the normalisation (~10)
+# and the G = g^T Y accumulation over 8 x 25 (l, m, k) (400); per atom A = W G (3200)
+# and the nu = 1, 2 energy and gradient (~3800).
+BASIS_FLOP_PER_PAIR = 510
+BASIS_FLOP_PER_ATOM = 7000
+# The whole ACE evaluation (k_ace_basis + k_ace_nu3 + k_ace_adjoint): per atom add the
+# nu = 3 monomials (~11400).
+ACE_FLOP_PER_PAIR = ADJ_FLOP_PER_PAIR + BASIS_FLOP_PER_PAIR
+ACE_FLOP_PER_ATOM = ADJ_FLOP_PER_ATOM + BASIS_FLOP_PER_ATOM + 11400
+# DRAM bytes (read + write) per launch on this workload, from ncu captures of the
+# current kernels on the 500k-atom case (60,000 precise atoms), scaled to 4,000,000 atoms
+# and 240,000 precise atoms (profiles/k_ace_adjoint_slab50_mixed.md,
+# profiles/k_eam_force_slab50_mixed.md):
+#   k_ace_adjoint  185.6 MB read (mostly the basis kernel's pair records) + 0.7 MB written;
+#   k_ace_basis    45.4 MB read + 121.8 MB written (the pair records, 16 B per pair);
+#   k_eam_force    146.1 MB read + 6.5 MB written.
 ADJ_TRAFFIC_BYTES = 186.3e6 * 240000 / 60000
+BASIS_TRAFFIC_BYTES = 167.2e6 * 240000 / 60000
+EAM_FORCE_TRAFFIC_BYTES = 152.6e6 * 4000000 / 500000
 # FP32 SIMT peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# Algorithmic bytes of one k_eam_force launch (the largest kernel of the step): the row
-# entries (4 B each) plus, per atom, its own shadow, (lambda xi', lambda), xi and row count
-# (16 + 8 + 8 + 4 B), its force and E^f (24 + 8 B), and one read of its shadow and q as
-# some other atom's neighbour (24 B): 4 E + 92 n.
+# Algorithmic bytes of one k_eam_force launch: the row entries it walks (4 B each; per
+# atom the prefix up to the last entry inside r_c) plus, per atom, its own shadow,
+# (lambda xi', lambda), xi and prefix length (16 + 8 + 8 + 4 B), its force and E^f
+# (24 + 8 B), and one read of its shadow and q as some other atom's neighbour (24 B):
+# 4 E_walked + 92 n.  The ncu traffic above matches it: no DRAM byte is read twice.
 EAM_FORCE_BYTES_PER_ENTRY = 4
 EAM_FORCE_BYTES_PER_ATOM = 92
-# DRAM bytes (read + write) of one k_eam_force launch: the ncu capture of the current kernel
-# on the 500k-atom case (208.7 MB read + 9.2 MB written) scaled by the atoms to 4,000,000
-# (profiles/k_eam_force_slab50_mixed.md).  It matches the algorithmic bytes: no DRAM re-reads.
-EAM_FORCE_TRAFFIC_BYTES = 218.0e6 * 4000000 / 500000
+
+
+def kernel_rooflines(ctx, prof, n, hbm_gbs, hbm_src):
+    """Roofline objects of the instrumented kernels from the step's own CUDA-event timers."""
+    ph = prof["phases"]
+    pairs, atoms = prof["ace_pairs"], prof["ace_atoms"]
+    alu_src = "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived, not measured)"
+    out = {}
+    for name, key, fpp, fpa, traffic in (("k_ace_basis", "ace_basis", BASIS_FLOP_PER_PAIR, BASIS_FLOP_PER_ATOM,
+                                          BASIS_TRAFFIC_BYTES),
+                                         ("k_ace_adjoint", "ace_adjoint", ADJ_FLOP_PER_PAIR, ADJ_FLOP_PER_ATOM,
+                                          ADJ_TRAFFIC_BYTES)):
+        ms, calls = ph[key]
+        tf = (fpp * pairs + fpa * atoms) / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+        out[name] = {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": tf / FP32_PEAK_TFLOPS, "traffic": traffic, "peak_source": alu_src,
+                     "ms_per_launch": ms / max(1, calls), "ms_total": ms, "launches": calls,
+                     "pairs_per_launch": pairs / max(1, calls), "atoms_per_launch": atoms / max(1, calls)}
+    ms, calls = ph["eam_force"]
+    walked = ctx.neighbor_total(2)            # row entries the last force pass walked
+    b = EAM_FORCE_BYTES_PER_ENTRY * walked + EAM_FORCE_BYTES_PER_ATOM * n
+    gbs = b / (ms / max(1, calls) / 1e3) / 1e9 if ms > 0 else 0.0
+    out["k_eam_force"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs,
+                          "traffic": EAM_FORCE_TRAFFIC_BYTES, "peak_source": hbm_src,
+                          "algorithmic_bytes_per_launch": b, "row_entries_walked": walked,
+                          "row_entries_total": ctx.neighbor_total(0), "ms_per_launch": ms / max(1, calls),
+                          "ms_total": ms, "launches": calls}
+    return out
 
 
 def hbm_peak():
@@ -264,16 +301,12 @@ def run_ours(args, ws, rank, local):
     atom_steps = w.n * MD_PER_STEP * args.steps * ws
     value = job_rate(w.n * MD_PER_STEP * args.steps, ws, ms)
     ace_ms, ace_calls = prof["phases"]["ace"]
-    adj_ms, adj_calls = prof["phases"]["ace_adjoint"]          # a sub-phase of "ace"
     flops = ACE_FLOP_PER_PAIR * prof["ace_pairs"] + ACE_FLOP_PER_ATOM * prof["ace_atoms"]
-    adj_flops = ADJ_FLOP_PER_PAIR * prof["ace_pairs"] + ADJ_FLOP_PER_ATOM * prof["ace_atoms"]
-    achieved = adj_flops / (adj_ms / 1e3) / 1e12 if adj_ms > 0 else 0.0
-    ef_ms, ef_calls = prof["phases"]["eam_force"]               # a sub-phase of "eam"
-    eam_entries = ctx.neighbor_total(0)
-    ef_bytes = EAM_FORCE_BYTES_PER_ENTRY * eam_entries + EAM_FORCE_BYTES_PER_ATOM * w.n
-    ef_gbs = ef_bytes / (ef_ms / max(1, ef_calls) / 1e3) / 1e9 if ef_ms > 0 else 0.0
     hbm_gbs, hbm_src = hbm_peak()
-    top = {k: v for k, v in prof["phases"].items() if k not in ("ace_adjoint", "eam_force")}   # sub-phases
+    rooflines = kernel_rooflines(ctx, prof, w.n, hbm_gbs, hbm_src)
+    dominant = max(rooflines, key=lambda k: rooflines[k]["ms_total"])
+    sub = ("ace_adjoint", "eam_force", "ace_basis")
+    top = {k: v for k, v in prof["phases"].items() if k not in sub}   # the sub-phases are inside ace / eam
     phase_share = {k: round(m / max(1e-9, sum(p[0] for p in top.values())), 4) for k, (m, c) in top.items()}
 
     # end-to-end through the public call with host buffers (pinned), copies inside the timed region
@@ -403,19 +436,10 @@ def run_ours(args, ws, rank, local):
             "e2e": {"value": atom_steps / (ms_e2e / 1e3), "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": prof["kernels"],
-            "roofline": {"bound": "hbm", "kernel": "k_eam_force (EAM force pass, the largest kernel of the step)",
-                         "achieved": ef_gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": ef_gbs / hbm_gbs,
-                         "traffic": EAM_FORCE_TRAFFIC_BYTES, "peak_source": hbm_src,
-                         "algorithmic_bytes_per_launch": ef_bytes, "eam_row_entries": eam_entries,
-                         "ms_per_launch": ef_ms / max(1, ef_calls)},
-            "roofline_ace_adjoint": {"bound": "alu", "kernel": "k_ace_adjoint (ACE force stage)",
-                         "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ADJ_TRAFFIC_BYTES,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived, not measured)",
-                         "ms_per_launch": adj_ms / max(1, adj_calls), "pairs": prof["ace_pairs"],
-                         "atoms": prof["ace_atoms"],
-                         "ace_all_kernels": {"tflops": flops / (ace_ms / 1e3) / 1e12 if ace_ms > 0 else 0.0,
-                                             "ms_per_step": ace_ms / max(1, ace_calls)}},
+            "roofline": dict(rooflines[dominant], kernel=dominant + " (the kernel with the most time in the step)"),
+            "rooflines": rooflines,
+            "ace_all_kernels": {"tflops": flops / (ace_ms / 1e3) / 1e12 if ace_ms > 0 else 0.0,
+                                "ms_per_call": ace_ms / max(1, ace_calls)},
             "phase_share": phase_share,
             "clocks": ck,
             "cpu_baseline": cpu,

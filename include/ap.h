@@ -222,16 +222,21 @@ ap_status ap_build_neighbors_batch(ap_ctx* ctx, int32_t n_sys, const int64_t* h_
 /* Export the neighbour rows (which = 0: EAM rows of all atoms; 1: ACE rows of
  * the last precise queue, radius ace_rc + skin).  d_cnt [rows], d_idx
  * [rows][cap], d_shift [rows][cap][3] = s of each entry relative to the d_x of
- * the build.  *h_rows receives the number of rows.  Synchronises. */
+ * the build.  *h_rows receives the number of rows.  Synchronises.  An EAM row
+ * lists the entries inside the potential's cutoff at the build (by an FP32 test)
+ * before the skin entries; within each part the order is the build's own. */
 ap_status ap_get_neighbors(ap_ctx* ctx, int32_t which, int32_t* d_cnt, int32_t* d_idx, int32_t* d_shift, int64_t cap,
                            int64_t* h_rows);
 
 /* Total number of entries in the current EAM rows (which = 0) or ACE rows (which = 1,
- * the precise queue's rows), summed on the device by one reduction kernel; *h_total
- * is a host pointer.  Synchronises the legacy default stream.  No paper counterpart:
- * instrumentation (the EAM passes read these entries every MD step).  Errors:
- * AP_ERR_STATE before ap_build_neighbors, AP_ERR_ARG for a null pointer or another
- * `which`. */
+ * the precise queue's rows), or the EAM row prefixes that the last EAM force pass
+ * walked (which = 2: per atom, one past the last entry that the density pass found
+ * inside the potential's cutoff), summed on the device by one reduction kernel;
+ * *h_total is a host pointer.  Synchronises the legacy default stream.  No paper
+ * counterpart: instrumentation (the EAM density pass reads the which = 0 entries, the
+ * force pass the which = 2 ones, every MD step).  Errors: AP_ERR_STATE before
+ * ap_build_neighbors, or for which = 2 before an EAM evaluation on the current rows;
+ * AP_ERR_ARG for a null pointer or another `which`. */
 ap_status ap_neighbor_total(ap_ctx* ctx, int32_t which, int64_t* h_total);
 
 /* ----------------------------------------------------------------- lambda */
@@ -403,7 +408,8 @@ ap_status ap_eval_eam_static(const ap_config* h_cfg, int64_t n, const double* d_
 #define AP_PHASE_THERMOSTAT 5  /* local thermostat: difference forces, Delta E, corrections */
 #define AP_PHASE_ACE_ADJOINT 6 /* k_ace_adjoint alone (the force stage; also counted in ACE) */
 #define AP_PHASE_EAM_FORCE 7   /* k_eam_force alone (the force pass; also counted in EAM)   */
-#define AP_NUM_PHASES 8
+#define AP_PHASE_ACE_BASIS 8   /* k_ace_basis alone (rows, G, A, nu = 1, 2; also counted in ACE) */
+#define AP_NUM_PHASES 9
 
 /* Turn per-phase event timing in ap_step on (1) or off (0) and clear the totals.
  * No paper counterpart: instrumentation of this implementation. */

@@ -190,7 +190,8 @@ class Context:
         self._ck(self.lib.ap_build_neighbors_batch(self.h, ns, off, arr, _ptr(x), _ptr(species), _stream(stream)))
 
     def neighbor_total(self, which: int = 0) -> int:
-        """Total entries of the current EAM (0) or ACE (1) rows (synchronises)."""
+        """Total entries of the current EAM (0) or ACE (1) rows, or of the EAM row prefixes
+        the last EAM force pass walked (2) (synchronises)."""
         t = ctypes.c_int64()
         self._ck(self.lib.ap_neighbor_total(self.h, which, ctypes.byref(t)))
         return t.value
@@ -272,7 +273,7 @@ class Context:
         return StepStats(st.step, st.n_precise, st.n_detected, st.rebuilds, st.e_pot, st.e_kin, st.max_disp,
                          st.error_bits, st.th_corrected, st.th_refused, st.th_energy)
 
-    PHASES = ("neighbors", "classify", "eam", "ace", "other", "thermostat", "ace_adjoint", "eam_force")
+    PHASES = ("neighbors", "classify", "eam", "ace", "other", "thermostat", "ace_adjoint", "eam_force", "ace_basis")
 
     def profile_enable(self, on: bool = True):
         self._ck(self.lib.ap_profile_enable(self.h, 1 if on else 0))

@@ -167,6 +167,7 @@ ap_status ensure_capacity(ap_ctx* c, int64_t n) {
   CK(dalloc(c->d_xbuild, 3 * m));
   CK(dalloc(c->d_vscale, m));
   CK(dalloc(c->d_cnt_eam, m));
+  CK(dalloc(c->d_lim_eam, m));
   CK(dalloc(c->d_cnt_ace, m));
   ap_status st = alloc_rows(c, true, true);
   if (st) return st;
@@ -261,6 +262,7 @@ void build_async(ap_ctx* c, const double* d_x, const int32_t* d_species, cudaStr
   launch_cell_sort(c, s);
   launch_shadow(c, d_x, s);
   launch_build_eam(c, d_x, s);
+  c->lim_valid = false;
   cudaMemcpyAsync(c->d_xbuild, d_x, sizeof(double) * 3 * (size_t)c->n, cudaMemcpyDeviceToDevice, s);
   cudaMemsetAsync(&c->d_sc->max_disp2_bits, 0, sizeof(unsigned int), s);
   c->rebuilds++;
@@ -553,7 +555,7 @@ void ap_destroy(ap_ctx* c) {
   cudaDeviceSynchronize();
   void* ptrs[] = {c->d_sys, c->d_atom_sys, c->d_cell, c->d_cunw, c->d_cell_start, c->d_cell_count, c->d_cell_atoms,
                   c->d_slot, c->d_sh32, c->d_sh64, c->d_xbuild, c->d_vscale, c->d_nbr_eam, c->d_off_eam, c->d_cnt_eam,
-                  c->d_nbr_ace, c->d_off_ace, c->d_cnt_ace, c->d_csp, c->d_csp_slow, c->d_csp_avg, c->d_lam0, c->d_lam_min,
+                  c->d_lim_eam, c->d_nbr_ace, c->d_off_ace, c->d_cnt_ace, c->d_csp, c->d_csp_slow, c->d_csp_avg, c->d_lam0, c->d_lam_min,
                   c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected,
                   c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_efast, c->d_eprec,
                   c->d_eatom, c->d_eext, c->d_changeable, c->d_W32, c->d_W64, c->d_ace_list, c->d_ace_nin,
@@ -656,10 +658,11 @@ ap_status ap_neighbor_total(ap_ctx* c, int32_t which, int64_t* h_total) {
   if (!c) return AP_ERR_ARG;
   if (!h_total) return fail(c, AP_ERR_ARG, "null argument");
   if (!c->built) return fail(c, AP_ERR_STATE, "no neighbour build yet");
-  if (which != 0 && which != 1) return fail(c, AP_ERR_ARG, "which must be 0 (EAM) or 1 (ACE)");
+  if (which < 0 || which > 2) return fail(c, AP_ERR_ARG, "which must be 0 (EAM), 1 (ACE) or 2 (EAM force prefixes)");
+  if (which == 2 && !c->lim_valid) return fail(c, AP_ERR_STATE, "no EAM evaluation on the current rows");
   ap_status st = read_scalars(c, 0);
   if (st) return st;
-  const int64_t rows = which == 0 ? c->n : c->h_sc->n_precise;
+  const int64_t rows = which == 1 ? c->h_sc->n_precise : c->n;
   launch_row_total(c, which, (int)rows, 0);
   unsigned long long t = 0;
   CK(cudaMemcpy(&t, &c->d_sc->row_total, sizeof(t), cudaMemcpyDeviceToHost));

@@ -151,6 +151,7 @@ struct ap_ctx {
   int* d_atom_sys = nullptr;     // null when n_sys == 1
   int n_cells = 0;
   bool stored_off = false;
+  bool lim_valid = false;        // d_lim_eam holds the prefixes of an EAM pass on the current rows
   int sten_spread[3] = {0, 0, 0};
 
   // capacity
@@ -176,6 +177,7 @@ struct ap_ctx {
   int* d_nbr_eam = nullptr;      // [n][cap_eam]
   int* d_off_eam = nullptr;      // [n][cap_eam] (stored offsets only)
   int* d_cnt_eam = nullptr;      // [n]
+  int* d_lim_eam = nullptr;      // [n] end of the in-cutoff entries, written by the EAM density pass
   int* d_nbr_ace = nullptr;      // [n][cap_ace] rows in queue order
   int* d_off_ace = nullptr;
   int* d_cnt_ace = nullptr;

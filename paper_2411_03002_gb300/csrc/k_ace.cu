@@ -775,7 +775,9 @@ void run_ace(ap_ctx* c, const double* d_lam, const double* d_wgt, const int* d_q
       cudaMemsetAsync(c->d_facc64, 0, sizeof(double) * 3 * (size_t)c->n, s);
   }
   cudaMemsetAsync(a.counter, 0, 2 * sizeof(int), s);   // work_counter and work_counter2
+  const int tb = prof_mark(c, s);
   k_ace_basis<R><<<c->num_sms * b1[pi], kWarps<R> * 32, s1, s>>>(a);
+  prof_add(c, AP_PHASE_ACE_BASIS, tb, prof_mark(c, s));
   const int t2 = sizeof(R) == 4 ? 128 : 64;
   if (fs)
     k_ace_nu3<R, true><<<c->num_sms * (sizeof(R) == 4 ? 8 : 16), t2, 0, s>>>(a, P, Q);

@@ -12,6 +12,11 @@
 // Pair displacements come from cell-relative shadows: d = k h + s_j - s_i with k
 // the pair's cell offset, either stored per entry (small periodic boxes) or
 // unwrapped from the packed cell codes (branch-free, per-atom constants hoisted).
+//
+// Rows hold every neighbour within r_c + skin, the ones inside r_c first (the row
+// build orders them so).  The density pass tests every entry and stores lim_i, one
+// past the last entry it found inside r_c; the force pass walks entries [0, lim_i)
+// only, with the same test, so the entries it skips are exactly ones that add nothing.
 #include "ap_internal.cuh"
 #include "eam_frame.cuh"
 
@@ -28,6 +33,13 @@ __device__ __forceinline__ void walk_row(const int* __restrict__ rowp, int sub, 
   for (int t = sub; t < c; t += G) body(rowp[t], t);
 }
 
+template <int G>
+__device__ inline int group_max(int v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o, G));
+  return v;
+}
+
 template <typename R, int G, bool STORED, typename P>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam_density(int n, const SysInfo* __restrict__ sys,
                                                      const int* __restrict__ atom_sys,
@@ -35,7 +47,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
                                                      const int* __restrict__ nbr, const int* __restrict__ off,
                                                      const int* __restrict__ cnt, int cap, P p,
                                                      const double* __restrict__ lam,
-                                                     typename Q2<R>::T* __restrict__ q, double* __restrict__ xi_out) {
+                                                     typename Q2<R>::T* __restrict__ q, double* __restrict__ xi_out,
+                                                     int* __restrict__ lim) {
   const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int sub = threadIdx.x & (G - 1);
   const bool active = gid < n;
@@ -45,15 +58,21 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   const int c = active ? cnt[i] : 0;
   const size_t row = (size_t)i * cap;
   R rho = R(0);
+  int last = -1;
   walk_row<G>(nbr + row, sub, c, [&](int j, int t) {
     const auto sj = sh[j];
     R d[3];
     fr.disp(sj, off, row + t, d);
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    if (r2 < p.rc2) rho += p.zeta(r2 * rsqrt_(r2));
+    if (r2 < p.rc2) {
+      rho += p.zeta(r2 * rsqrt_(r2));
+      last = t;
+    }
   });
   rho = group_sum<R, G>(rho);
+  last = group_max<G>(last);
   if (active && sub == 0) {
+    lim[i] = last + 1;
     const R li = lam ? (R)lam[i] : R(1);
     R xi, dxi;
     p.embed(rho, xi, dxi);
@@ -69,8 +88,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
                                                    const int* __restrict__ nbr, const int* __restrict__ off,
                                                    const int* __restrict__ cnt, int cap, P p,
                                                    const typename Q2<R>::T* __restrict__ q,
-                                                   const double* __restrict__ xi, double* __restrict__ e_fast,
-                                                   double* __restrict__ f, int accumulate) {
+                                                   const double* __restrict__ xi, const int* __restrict__ lim,
+                                                   double* __restrict__ e_fast, double* __restrict__ f,
+                                                   int accumulate) {
   const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int sub = threadIdx.x & (G - 1);
   const bool active = gid < n;
@@ -78,7 +98,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? P::kMinBlocks : 1) k_eam
   const auto si = sh[i];
   const Frame<R, STORED> fr(sys[atom_sys ? atom_sys[i] : 0], si);
   const auto qi = q[i];
-  const int c = active ? cnt[i] : 0;
+  const int c = active ? lim[i] : 0;
   const size_t row = (size_t)i * cap;
   R fx = R(0), fy = R(0), fz = R(0), phi = R(0);
   walk_row<G>(nbr + row, sub, c, [&](int j, int t) {
@@ -128,13 +148,15 @@ void run_eam(ap_ctx* c, const P& p, const typename Shadow<R>::T* sh, const doubl
   auto* q = reinterpret_cast<typename Q2<R>::T*>(c->d_q);
   const int* off = STORED ? c->d_off_eam : nullptr;
   k_eam_density<R, G, STORED, P><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam,
-                                                         off, c->d_cnt_eam, c->cap_eam, p, d_lam, q, c->d_xi);
+                                                         off, c->d_cnt_eam, c->cap_eam, p, d_lam, q, c->d_xi,
+                                                         c->d_lim_eam);
   const int t0 = prof_mark(c, s);
   k_eam_force<R, G, STORED, P><<<blocks, threads, 0, s>>>((int)c->n, c->d_sys, c->d_atom_sys, sh, c->d_nbr_eam, off,
-                                                       c->d_cnt_eam, c->cap_eam, p, q, c->d_xi, d_e_fast, d_f,
-                                                       accumulate ? 1 : 0);
+                                                       c->d_cnt_eam, c->cap_eam, p, q, c->d_xi, c->d_lim_eam,
+                                                       d_e_fast, d_f, accumulate ? 1 : 0);
   prof_add(c, AP_PHASE_EAM_FORCE, t0, prof_mark(c, s));
   c->kernels += 2;
+  c->lim_valid = true;
 }
 
 template <typename R>

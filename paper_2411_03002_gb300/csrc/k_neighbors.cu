@@ -270,23 +270,30 @@ __device__ inline int build_row_warp(int i, const double* __restrict__ x, const 
   return cnt;
 }
 
+#ifndef AP_BUILD_MINB
+#define AP_BUILD_MINB 9   // resident 128-thread blocks per SM the EAM row build is compiled for (<= 56 registers)
+#endif
 // Unroll depth of the per-cell candidate loop of the EAM row build (compile-time tuning).
 #ifndef AP_BUILD_UNROLL
 #define AP_BUILD_UNROLL 2
 #endif
 constexpr int kBuildUnroll = AP_BUILD_UNROLL;
 
-// One thread builds one row (EAM rows of all atoms): scan the 5x5x5 stencil around atom i and append accepted (j, offset) to a row.
+// One thread builds one row (EAM rows of all atoms): scan the 5x5x5 stencil around atom i and keep the
+// accepted (j, offset).  The row is ordered in two parts: first the entries whose FP32 distance
+// lies inside the potential cutoff (rpf2 = r_c^2), in stencil order, then the skin entries.  The
+// density pass records, per atom, where the in-range entries end (it re-tests every entry), so
+// the force pass walks only that prefix; the split at build time only makes the prefix short.
 __device__ inline int build_row(int i, const double* __restrict__ x, const SysInfo& S, const float4* __restrict__ s32,
                                 const int4* __restrict__ cunw, const int* __restrict__ cstart,
-                                const int* __restrict__ catoms, float rcf2, double rc2, float band, int cap,
-                                int* __restrict__ row, int* __restrict__ offrow) {
+                                const int* __restrict__ catoms, float rcf2, double rc2, float rpf2, float band,
+                                int cap, int* __restrict__ row, int* __restrict__ offrow) {
   const float4 si = s32[i];
   const int4 ci = cunw[i];
   const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
   const float sv[3] = {si.x, si.y, si.z};
   const float rmax2 = rcf2 + band;
-  int cnt = 0;
+  int n_in = 0, n_skin = 0;   // in-range entries fill the row from the front, skin entries from the back
   for (int dz = -kStencil; dz <= kStencil; ++dz) {
     int tz = cw[2] + dz, iz = 0;
     if (S.periodic[2]) {
@@ -337,32 +344,69 @@ __device__ inline int build_row(int i, const double* __restrict__ x, const SysIn
             take = exact_within(x, S, i, j, ci, cunw[j], img, rc2);
           }
           if (take) {
-            if (cnt < cap) {
-              row[cnt] = j;
-              if (offrow) offrow[cnt] = pack_off(dx, dy, dz);
+            const bool in = r2f < rpf2;
+            if (n_in + n_skin < cap) {
+              const int pos = in ? n_in : cap - 1 - n_skin;
+              row[pos] = j;
+              if (offrow) offrow[pos] = pack_off(dx, dy, dz);
             }
-            ++cnt;
+            if (in)
+              ++n_in;
+            else
+              ++n_skin;
           }
         }
+      }
+    }
+  }
+  const int cnt = n_in + n_skin;
+  if (cnt < cap) {
+    // Close the gap: the skin entries move from [cap - n_skin, cap) to [n_in, cnt) in
+    // chunks of 8, each chunk read in full before it is written.  A chunk's
+    // destinations lie below every source of the later chunks (n_in + n_skin < cap),
+    // so no entry is overwritten before it is read.  (A full row has no gap.)
+    int* src = row + cap - n_skin;
+    int* dst = row + n_in;
+    for (int k0 = 0; k0 < n_skin; k0 += 8) {
+      int v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = k0 + u < n_skin ? src[k0 + u] : 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < n_skin) dst[k0 + u] = v[u];
+    }
+    if (offrow) {
+      int* osrc = offrow + cap - n_skin;
+      int* odst = offrow + n_in;
+      for (int k0 = 0; k0 < n_skin; k0 += 8) {
+        int v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = k0 + u < n_skin ? osrc[k0 + u] : 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (k0 + u < n_skin) odst[k0 + u] = v[u];
       }
     }
   }
   return cnt;
 }
 
-__global__ void k_build_eam(int n, const double* __restrict__ x, const SysInfo* __restrict__ sys,
+__global__ void __launch_bounds__(128, AP_BUILD_MINB) k_build_eam(int n, const double* __restrict__ x, const SysInfo* __restrict__ sys,
                             const int* __restrict__ atom_sys, const float4* __restrict__ s32,
                             const int4* __restrict__ cunw, const int* __restrict__ cstart,
-                            const int* __restrict__ catoms, float rcf2, double rc2, float band, int cap,
-                            int* __restrict__ nbr, int* __restrict__ off, int* __restrict__ cnt, DevScalars* sc) {
+                            const int* __restrict__ catoms, float rcf2, double rc2, float rpf2, float band,
+                            int cap, int* __restrict__ nbr, int* __restrict__ off, int* __restrict__ cnt,
+                            DevScalars* sc) {
   // Threads take the atoms in cell order: the atoms of one cell walk the same stencil
   // cells with the same atom counts, so a warp diverges only on the per-atom gap test.
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int i = catoms[t];
   const SysInfo& S = sys_of(sys, atom_sys, i);
-  int c = build_row(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, band, cap, nbr + (size_t)i * cap,
+  int c = build_row(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, rpf2, band, cap, nbr + (size_t)i * cap,
                     off ? off + (size_t)i * cap : nullptr);
+  // an overflowing row holds cap valid entries (the capacity error makes the caller
+  // rebuild or fail before any result is used)
   cnt[i] = c < cap ? c : cap;
   if (c > cap) {
     atomicMax(&sc->need_eam, c);
@@ -486,17 +530,19 @@ __global__ void k_row_total(int rows, const int* __restrict__ cnt, unsigned long
 void launch_row_total(ap_ctx* c, int which, int rows, cudaStream_t s) {
   cudaMemsetAsync(&c->d_sc->row_total, 0, sizeof(unsigned long long), s);
   if (rows > 0)
-    k_row_total<<<nblk(rows, 256), 256, 0, s>>>(rows, which == 0 ? c->d_cnt_eam : c->d_cnt_ace,
-                                                &c->d_sc->row_total);
+    k_row_total<<<nblk(rows, 256), 256, 0, s>>>(
+        rows, which == 0 ? c->d_cnt_eam : which == 1 ? c->d_cnt_ace : c->d_lim_eam, &c->d_sc->row_total);
 }
 
 void launch_build_eam(ap_ctx* c, const double* d_x, cudaStream_t s) {
   double r = c->cfg.eam_rc + c->cfg.skin;
   double rc2 = r * r;
+  // the potential's own cutoff: rows are split at it (the Mishin rc may lie below eam_rc)
+  const double rp = c->cfg.eam_type == AP_EAM_MISHIN ? c->cfg.eam_mishin[28] : c->cfg.eam_rc;
   k_build_eam<<<nblk(c->n, 128), 128, 0, s>>>((int)c->n, d_x, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
-                                              c->d_cell_start, c->d_cell_atoms, (float)rc2, rc2, kBand, c->cap_eam,
-                                              c->d_nbr_eam, c->stored_off ? c->d_off_eam : nullptr, c->d_cnt_eam,
-                                              c->d_sc);
+                                              c->d_cell_start, c->d_cell_atoms, (float)rc2, rc2, (float)(rp * rp),
+                                              kBand, c->cap_eam, c->d_nbr_eam,
+                                              c->stored_off ? c->d_off_eam : nullptr, c->d_cnt_eam, c->d_sc);
   c->kernels += 1;
 }
 
