@@ -493,9 +493,10 @@ ap_status prep_detector(ap_ctx* c) {
   return ensure_sel_feat(c, c->n);
 }
 
+// fresh_rows: the EAM rows were built at d_x in this call (ap_step).
 void classify_async(ap_ctx* c, const double* d_x, const uint8_t* d_ch, double* d_lam, int* d_queue,
-                    int64_t* d_nq64, cudaStream_t s) {
-  launch_csp(c, d_x, d_ch, s);
+                    int64_t* d_nq64, cudaStream_t s, bool fresh_rows = false) {
+  launch_csp(c, d_x, d_ch, s, fresh_rows);
   if (c->cfg.detector == AP_DETECT_SELECTOR) {
     launch_sel_features(c, c->d_sel_feat, s);
     launch_sel_mlp(c, c->n, c->d_sel_feat, nullptr, nullptr, c->d_sel_score, nullptr, nullptr, nullptr, s);
@@ -808,7 +809,7 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
       queue_from_lambda(c, s);
       c->restart_pending = false;
     } else {
-      classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s);
+      classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s, true);
     }
     st = build_ace_checked(c, d_x, c->d_precise, s);
     if (st) return st;
@@ -848,7 +849,7 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
         if (lam_step) {
           if (thermo)
             CK(cudaMemcpyAsync(c->d_th_lamc, c->d_lam_int, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
-          classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s);
+          classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s, true);
         }
       }
       if (lam_step && thermo) {

@@ -152,6 +152,7 @@ struct ap_ctx {
   int n_cells = 0;
   bool stored_off = false;
   bool lim_valid = false;        // d_lim_eam holds the prefixes of an EAM pass on the current rows
+  float split_rpf2 = 0.f;        // r_c^2 (FP32) at which the EAM rows were split
   int sten_spread[3] = {0, 0, 0};
 
   // capacity
@@ -177,7 +178,8 @@ struct ap_ctx {
   int* d_nbr_eam = nullptr;      // [n][cap_eam]
   int* d_off_eam = nullptr;      // [n][cap_eam] (stored offsets only)
   int* d_cnt_eam = nullptr;      // [n]
-  int* d_lim_eam = nullptr;      // [n] end of the in-cutoff entries, written by the EAM density pass
+  int* d_lim_eam = nullptr;      // [n] the row build's in-range count, then (after each EAM density
+                                 //     pass) one past the last entry found inside r_c
   int* d_nbr_ace = nullptr;      // [n][cap_ace] rows in queue order
   int* d_off_ace = nullptr;
   int* d_cnt_ace = nullptr;
@@ -308,7 +310,8 @@ int prof_mark(ap_ctx* c, cudaStream_t s);
 void prof_add(ap_ctx* c, int phase, int start, int end);
 
 // k_classify.cu
-void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s);
+// fresh_rows: the EAM rows were built at d_x (the CSP may stop after their in-range part)
+void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s, bool fresh_rows = false);
 void launch_lambda0(ap_ctx* c, const uint8_t* d_ch, const double* d_score, double lo, double hi, cudaStream_t s);
 void launch_spread(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s);
 void launch_lambda_final(ap_ctx* c, const uint8_t* d_ch, double* d_lam, int* d_queue, int64_t* d_nq64,

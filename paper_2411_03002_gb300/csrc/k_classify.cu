@@ -120,13 +120,19 @@ __device__ inline bool entry_less(const double* __restrict__ x, const SysInfo& S
 // cannot decide (an r_search band hit, an ambiguous 12/13 or 6/7 boundary) is
 // appended to `slow`.  !FAST: the atoms of `slow`, with the exact FP64 selections.
 // CSP of atom i (128-thread blocks: the shared arrays are indexed by threadIdx.x).
+// nin (FAST, rows built at these positions, else null): the row's first nin[i] entries
+// are the ones inside r_c^2 = rpf2 at the build (FP32), the rest lie beyond it.  When the
+// 13th smallest r^2 of that part lies more than two guard bands inside rpf2, no skin
+// entry can enter the 13 nearest or come within a band of the 12/13 boundary, and the
+// skin part is skipped; otherwise it is walked too.
 template <bool FAST>
 __device__ __forceinline__ void csp_atom(int i, const double* __restrict__ x, const uint8_t* __restrict__ ch,
                                          const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
                                          const float4* __restrict__ s32, const int4* __restrict__ cunw,
                                          const int* __restrict__ nbr, const int* __restrict__ off,
                                          const int* __restrict__ cnt, int cap, float rsf2, double rs2,
-                                         double* __restrict__ csp, int* __restrict__ slow, int* __restrict__ n_slow) {
+                                         double* __restrict__ csp, int* __restrict__ slow, int* __restrict__ n_slow,
+                                         const int* __restrict__ nin = nullptr, float rpf2 = 0.f) {
   static_assert(kNN <= 255, "neighbour slots are packed in 8 bits");
   if (ch && !ch[i]) {
     csp[i] = 0.0;
@@ -147,7 +153,12 @@ __device__ __forceinline__ void csp_atom(int i, const double* __restrict__ x, co
     tq[a] = -1;
   }
   int n_in = 0;
+  int q_end = (FAST && nin) ? nin[i] : c;
   for (int q = 0; q < c; ++q) {
+    if (q == q_end) {   // end of the in-range part (FAST with nin only)
+      if (tr[kNN] + 2.f * kBand < rpf2) break;
+      q_end = c;
+    }
     const int j = nbr[row + q];
     const float4 sj = s32[j];
     int k[3];
@@ -340,9 +351,10 @@ __global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x
                                                 const int* __restrict__ nbr, const int* __restrict__ off,
                                                 const int* __restrict__ cnt, int cap, float rsf2, double rs2,
                                                 double* __restrict__ csp, int* __restrict__ slow,
-                                                int* __restrict__ n_slow) {
+                                                int* __restrict__ n_slow, const int* __restrict__ nin, float rpf2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) csp_atom<true>(i, x, ch, sys, atom_sys, s32, cunw, nbr, off, cnt, cap, rsf2, rs2, csp, slow, n_slow);
+  if (i < n)
+    csp_atom<true>(i, x, ch, sys, atom_sys, s32, cunw, nbr, off, cnt, cap, rsf2, rs2, csp, slow, n_slow, nin, rpf2);
 }
 
 __global__ void __launch_bounds__(128) k_csp_exact(const double* __restrict__ x, const uint8_t* __restrict__ ch,
@@ -567,7 +579,7 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s) {
+void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s, bool fresh_rows) {
   double r = c->cfg.eam_rc + c->cfg.skin;
   double rs2 = r * r;
   const int* off = c->stored_off ? c->d_off_eam : nullptr;
@@ -575,7 +587,8 @@ void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t 
   cudaMemsetAsync(n_slow, 0, sizeof(int), s);
   k_csp<<<nblk(c->n, 128), 128, 0, s>>>((int)c->n, d_x, d_ch, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
                                               c->d_nbr_eam, off, c->d_cnt_eam, c->cap_eam, (float)rs2, rs2, c->d_csp,
-                                              c->d_csp_slow, n_slow);
+                                              c->d_csp_slow, n_slow, fresh_rows ? c->d_lim_eam : nullptr,
+                                              c->split_rpf2);
   // the handed-over atoms (a small fraction), grid-stride over the device-side count
   k_csp_exact<<<c->num_sms * 4, 128, 0, s>>>(d_x, d_ch, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw, c->d_nbr_eam,
                                              off, c->d_cnt_eam, c->cap_eam, (float)rs2, rs2, c->d_csp,

@@ -287,7 +287,7 @@ constexpr int kBuildUnroll = AP_BUILD_UNROLL;
 __device__ inline int build_row(int i, const double* __restrict__ x, const SysInfo& S, const float4* __restrict__ s32,
                                 const int4* __restrict__ cunw, const int* __restrict__ cstart,
                                 const int* __restrict__ catoms, float rcf2, double rc2, float rpf2, float band,
-                                int cap, int* __restrict__ row, int* __restrict__ offrow) {
+                                int cap, int* __restrict__ row, int* __restrict__ offrow, int& n_in_out) {
   const float4 si = s32[i];
   const int4 ci = cunw[i];
   const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
@@ -360,6 +360,7 @@ __device__ inline int build_row(int i, const double* __restrict__ x, const SysIn
     }
   }
   const int cnt = n_in + n_skin;
+  n_in_out = n_in;
   if (cnt < cap) {
     // Close the gap: the skin entries move from [cap - n_skin, cap) to [n_in, cnt) in
     // chunks of 8, each chunk read in full before it is written.  A chunk's
@@ -396,18 +397,20 @@ __global__ void __launch_bounds__(128, AP_BUILD_MINB) k_build_eam(int n, const d
                             const int4* __restrict__ cunw, const int* __restrict__ cstart,
                             const int* __restrict__ catoms, float rcf2, double rc2, float rpf2, float band,
                             int cap, int* __restrict__ nbr, int* __restrict__ off, int* __restrict__ cnt,
-                            DevScalars* sc) {
+                            int* __restrict__ nin, DevScalars* sc) {
   // Threads take the atoms in cell order: the atoms of one cell walk the same stencil
   // cells with the same atom counts, so a warp diverges only on the per-atom gap test.
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int i = catoms[t];
   const SysInfo& S = sys_of(sys, atom_sys, i);
+  int a = 0;
   int c = build_row(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, rpf2, band, cap, nbr + (size_t)i * cap,
-                    off ? off + (size_t)i * cap : nullptr);
+                    off ? off + (size_t)i * cap : nullptr, a);
   // an overflowing row holds cap valid entries (the capacity error makes the caller
   // rebuild or fail before any result is used)
   cnt[i] = c < cap ? c : cap;
+  nin[i] = a < cap ? a : cap;   // the in-range part (read by the CSP on rows built at its positions)
   if (c > cap) {
     atomicMax(&sc->need_eam, c);
     atomicOr(&sc->err, kErrCapacity);
@@ -539,10 +542,12 @@ void launch_build_eam(ap_ctx* c, const double* d_x, cudaStream_t s) {
   double rc2 = r * r;
   // the potential's own cutoff: rows are split at it (the Mishin rc may lie below eam_rc)
   const double rp = c->cfg.eam_type == AP_EAM_MISHIN ? c->cfg.eam_mishin[28] : c->cfg.eam_rc;
+  c->split_rpf2 = (float)(rp * rp);
   k_build_eam<<<nblk(c->n, 128), 128, 0, s>>>((int)c->n, d_x, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
-                                              c->d_cell_start, c->d_cell_atoms, (float)rc2, rc2, (float)(rp * rp),
+                                              c->d_cell_start, c->d_cell_atoms, (float)rc2, rc2, c->split_rpf2,
                                               kBand, c->cap_eam, c->d_nbr_eam,
-                                              c->stored_off ? c->d_off_eam : nullptr, c->d_cnt_eam, c->d_sc);
+                                              c->stored_off ? c->d_off_eam : nullptr, c->d_cnt_eam, c->d_lim_eam,
+                                              c->d_sc);
   c->kernels += 1;
 }
 

@@ -101,3 +101,27 @@ def test_eam_after_moves_without_rebuild(name, precision):
         assert np.abs(efn - e_o).max() < 1e-4
         assert abs(efn.sum() - e_o.sum()) / w.n < 1e-6
     ctx.close()
+
+
+def test_csp_on_fresh_rows_matches_the_full_row_walk():
+    """ap_step classifies on rows built at the same positions, where the CSP may stop after
+    a row's in-range part; ap_classify walks whole rows.  Both, and the oracle, agree bit
+    for bit on the 32,000-atom slab (with its disordered hemisphere)."""
+    w = I.config_c2()
+    cfg = ap.make_config(I.eam_params(0), I.ace_params(0), w.hyb, precision=ap.PREC_MIXED, dt=w.dt)
+    ctx = ap.Context(cfg)
+    x = T(w.x)
+    v = T(w.v)
+    f = torch.zeros_like(x)
+    lam = torch.empty(w.n, dtype=torch.float64, device="cuda")
+    ctx.build_neighbors(x, w.box)
+    ctx.step(x, v, f, T(w.mass), None, lam, 0)
+    csp_step = ctx.get_lambda_state()["csp"].cpu().numpy()
+    ctx2 = ap.Context(cfg)
+    ctx2.build_neighbors(x, w.box)
+    ctx2.classify(x)
+    csp_full = ctx2.get_lambda_state()["csp"].cpu().numpy()
+    assert np.array_equal(csp_step, csp_full)
+    assert np.array_equal(csp_step, O.csp(x.cpu().numpy(), w.box))
+    ctx.close()
+    ctx2.close()
