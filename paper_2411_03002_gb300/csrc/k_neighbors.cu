@@ -281,9 +281,11 @@ constexpr int kBuildUnroll = AP_BUILD_UNROLL;
 
 // One thread builds one row (EAM rows of all atoms): scan the 5x5x5 stencil around atom i and keep the
 // accepted (j, offset).  The row is ordered in two parts: first the entries whose FP32 distance
-// lies inside the potential cutoff (rpf2 = r_c^2), in stencil order, then the skin entries.  The
-// density pass records, per atom, where the in-range entries end (it re-tests every entry), so
-// the force pass walks only that prefix; the split at build time only makes the prefix short.
+// lies inside the potential cutoff (rpf2 = r_c^2), in stencil order, then the skin entries;
+// n_in_out receives the length of the first part.  The EAM density pass records, per atom,
+// where the in-range entries end at the current positions (it re-tests every entry), so the
+// force pass walks only that prefix; the split at build time only makes the prefix short.
+// The CSP on rows built at its own positions may stop after the first part.
 __device__ inline int build_row(int i, const double* __restrict__ x, const SysInfo& S, const float4* __restrict__ s32,
                                 const int4* __restrict__ cunw, const int* __restrict__ cstart,
                                 const int* __restrict__ catoms, float rcf2, double rc2, float rpf2, float band,
