@@ -172,6 +172,7 @@ struct ap_ctx {
   int* d_cell_atoms = nullptr;   // [n]
   int* d_slot = nullptr;         // [n] slot inside cell
   float4* d_sh32 = nullptr;      // FP32 cell-relative shadow
+  float4* d_sh32c = nullptr;     // the same in cell order (the EAM row build's candidate stream)
   double4_32a* d_sh64 = nullptr;     // FP64 cell-relative shadow
   double* d_xbuild = nullptr;    // [n][3] positions at the last build
   double* d_vscale = nullptr;    // [n] 0.5 dt ACC / m_i of the current ap_step call

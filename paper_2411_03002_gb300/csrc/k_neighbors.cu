@@ -285,8 +285,10 @@ constexpr int kBuildUnroll = AP_BUILD_UNROLL;
 // n_in_out receives the length of the first part.  The EAM density pass records, per atom,
 // where the in-range entries end at the current positions (it re-tests every entry), so the
 // force pass walks only that prefix; the split at build time only makes the prefix short.
-// The CSP on rows built at its own positions may stop after the first part.
-__device__ inline int build_row(int i, const double* __restrict__ x, const SysInfo& S, const float4* __restrict__ s32,
+// The CSP on rows built at its own positions may stop after the first part.  Candidates are
+// read from s32c, the shadows in cell order; t_self is atom i's own position in that order.
+__device__ inline int build_row(int i, int t_self, const double* __restrict__ x, const SysInfo& S,
+                                const float4* __restrict__ s32, const float4* __restrict__ s32c,
                                 const int4* __restrict__ cunw, const int* __restrict__ cstart,
                                 const int* __restrict__ catoms, float rcf2, double rc2, float rpf2, float band,
                                 int cap, int* __restrict__ row, int* __restrict__ offrow, int& n_in_out) {
@@ -334,9 +336,10 @@ __device__ inline int build_row(int i, const double* __restrict__ x, const SysIn
 #pragma unroll kBuildUnroll
 #endif
         for (int a = b; a < e; ++a) {
-          int j = catoms[a];
-          if (j == i && dx == 0 && dy == 0 && dz == 0) continue;
-          float4 sj = s32[j];
+          // the shadows in cell order: the candidate's shadow and index load independently
+          if (a == t_self && dx == 0 && dy == 0 && dz == 0) continue;
+          const float4 sj = s32c[a];
+          const int j = catoms[a];
           float ddx = ox + sj.x, ddy = oy + sj.y, ddz = oz + sj.z;
           float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
           if (r2f > rcf2 + band) continue;
@@ -394,8 +397,16 @@ __device__ inline int build_row(int i, const double* __restrict__ x, const SysIn
   return cnt;
 }
 
+// FP32 shadows in cell order (s32c[a] = s32[catoms[a]]), for the EAM row build.
+__global__ void k_shadow_cells(int n, const int* __restrict__ catoms, const float4* __restrict__ s32,
+                               float4* __restrict__ s32c) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < n) s32c[a] = s32[catoms[a]];
+}
+
 __global__ void __launch_bounds__(128, AP_BUILD_MINB) k_build_eam(int n, const double* __restrict__ x, const SysInfo* __restrict__ sys,
                             const int* __restrict__ atom_sys, const float4* __restrict__ s32,
+                            const float4* __restrict__ s32c,
                             const int4* __restrict__ cunw, const int* __restrict__ cstart,
                             const int* __restrict__ catoms, float rcf2, double rc2, float rpf2, float band,
                             int cap, int* __restrict__ nbr, int* __restrict__ off, int* __restrict__ cnt,
@@ -407,7 +418,7 @@ __global__ void __launch_bounds__(128, AP_BUILD_MINB) k_build_eam(int n, const d
   const int i = catoms[t];
   const SysInfo& S = sys_of(sys, atom_sys, i);
   int a = 0;
-  int c = build_row(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, rpf2, band, cap, nbr + (size_t)i * cap,
+  int c = build_row(i, t, x, S, s32, s32c, cunw, cstart, catoms, rcf2, rc2, rpf2, band, cap, nbr + (size_t)i * cap,
                     off ? off + (size_t)i * cap : nullptr, a);
   // an overflowing row holds cap valid entries (the capacity error makes the caller
   // rebuild or fail before any result is used)
@@ -545,7 +556,10 @@ void launch_build_eam(ap_ctx* c, const double* d_x, cudaStream_t s) {
   // the potential's own cutoff: rows are split at it (the Mishin rc may lie below eam_rc)
   const double rp = c->cfg.eam_type == AP_EAM_MISHIN ? c->cfg.eam_mishin[28] : c->cfg.eam_rc;
   c->split_rpf2 = (float)(rp * rp);
-  k_build_eam<<<nblk(c->n, 128), 128, 0, s>>>((int)c->n, d_x, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
+  k_shadow_cells<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, c->d_cell_atoms, c->d_sh32, c->d_sh32c);
+  c->kernels += 1;
+  k_build_eam<<<nblk(c->n, 128), 128, 0, s>>>((int)c->n, d_x, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_sh32c,
+                                              c->d_cunw,
                                               c->d_cell_start, c->d_cell_atoms, (float)rc2, rc2, c->split_rpf2,
                                               kBand, c->cap_eam, c->d_nbr_eam,
                                               c->stored_off ? c->d_off_eam : nullptr, c->d_cnt_eam, c->d_lim_eam,
