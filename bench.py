@@ -103,6 +103,11 @@ def kernel_rooflines(ctx, prof, n, hbm_gbs, hbm_src):
     return out
 
 
+def dominant_kernel(rooflines):
+    """The instrumented kernel with the most measured time in the timed region."""
+    return max(rooflines, key=lambda k: rooflines[k]["ms_total"])
+
+
 def hbm_peak():
     """(GB/s, source) from MEASURED_PEAKS.json, else the profiling recipe's fallback."""
     try:
@@ -304,7 +309,7 @@ def run_ours(args, ws, rank, local):
     flops = ACE_FLOP_PER_PAIR * prof["ace_pairs"] + ACE_FLOP_PER_ATOM * prof["ace_atoms"]
     hbm_gbs, hbm_src = hbm_peak()
     rooflines = kernel_rooflines(ctx, prof, w.n, hbm_gbs, hbm_src)
-    dominant = max(rooflines, key=lambda k: rooflines[k]["ms_total"])
+    dominant = dominant_kernel(rooflines)
     sub = ("ace_adjoint", "eam_force", "ace_basis")
     top = {k: v for k, v in prof["phases"].items() if k not in sub}   # the sub-phases are inside ace / eam
     phase_share = {k: round(m / max(1e-9, sum(p[0] for p in top.values())), 4) for k, (m, c) in top.items()}
