@@ -99,3 +99,14 @@ def test_generated_nu3_code_matches_the_basis(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
     with open(os.path.join(csrc, "ace_nu3.inc")) as fh:
         assert fh.read() == out
+
+
+def test_profile_phase_names_match_the_header():
+    """Context.PHASES lists one name per AP_PHASE_* constant, in index order, and
+    AP_NUM_PHASES entries in all (ap_profile_read fills that many)."""
+    src = open(HEADER).read()
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (AP_PHASE_[A-Z_0-9]+) (\d+)", src)}
+    num = int(re.search(r"#define AP_NUM_PHASES (\d+)", src).group(1))
+    assert len(consts) == num == len(api.Context.PHASES)
+    for name, idx in consts.items():
+        assert api.Context.PHASES[idx] == name[len("AP_PHASE_"):].lower(), name
