@@ -34,6 +34,14 @@ namespace {
 
 constexpr int kCols = 36;            // 32 neighbour slots + 4 pad (16-byte rows, conflict-free)
 constexpr int kRows = 33;            // 8 radial + 25 angular rows
+// Tensor-core staging of one 32-neighbour batch (FP32 path), per k-step of 8 neighbours:
+// the Y^T operand fragments [m-tile 2][lane 32][4] + 16 pad floats, and the g operand
+// fragments [lane 32][2] + 8 pad floats.  The pads put the four k-steps of one store
+// on different banks.
+constexpr int kTyStep = 2 * 128 + 16;
+constexpr int kTgStep = 64 + 8;
+template <typename R>
+constexpr int kTileWords = sizeof(R) == 4 ? 4 * kTyStep + 4 * kTgStep : kRows * kCols;
 // Warps per CTA and the minimum resident CTAs per SM
 // the compiler budgets registers for; compile-time tuning parameters.
 #ifndef AP_ACE_WARPS
@@ -277,6 +285,78 @@ __device__ inline T warp_sum(T v) {
   return v;
 }
 
+// ---- 3xTF32 on warp-level tensor cores (FP32 path).  An FP32 value x is carried as
+// hi + lo: hi = x rounded to the 10-bit TF32 significand (ties away from zero), lo =
+// x - hi (exact in FP32); the tensor core reads the leading TF32 bits of lo.  A
+// product of two such pairs drops lo * lo', which leaves about the error of an FP32
+// product (relative 2^-21 per term).
+__device__ inline void tf32_split(float x, uint32_t& h, uint32_t& l) {
+  h = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+  l = __float_as_uint(x - __uint_as_float(h));
+}
+
+// D += A B on one m16n8k8 tile (A 16x8 row-major, B 8x8 column-major, TF32 inputs, FP32
+// accumulation).  Fragments of lane (g = lane / 4, t = lane % 4):
+//   a = A[g][t], A[g+8][t], A[g][t+4], A[g+8][t+4];  b = B[t][g], B[t+4][g];
+//   d = D[g][2t], D[g][2t+1], D[g+8][2t], D[g+8][2t+1].
+__device__ inline void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// D += (Ah + Al)(Bh + Bl) without Al Bl, the small products first.
+__device__ inline void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], uint32_t bh0,
+                            uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+  mma_tf32(d, al, bh0, bh1);
+  mma_tf32(d, ah, bl0, bl1);
+  mma_tf32(d, ah, bh0, bh1);
+}
+
+// out[lm][n] = sum_k in[lm][k] F[l(lm)][n][k] for the 25 (l, m) rows (two m-tiles, rows
+// 25..31 zero) and an 8 x 8 factor per l (F in shared memory, F[(l * 8 + n) * 8 + k]).
+// `in` is held as m16n8k8 accumulator fragments (rows lm = 16 mt + g, + 8; columns
+// k = 2t, 2t + 1), and so is `out`: the accumulator feeds the next product directly,
+// with the contraction index relabelled (operand column t <-> k = 2t, t + 4 <-> 2t + 1,
+// and B's rows the same way).  Rows of one m-tile carry several l, so tile 0 takes one
+// product per l = 0..3 and every lane keeps the rows of its own l; tile 1 is l = 4.
+__device__ inline void lm_mix(const float (&in)[2][4], const float* __restrict__ F, int g, int t,
+                              float (&out)[2][4]) {
+  uint32_t ah[2][4], al[2][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    tf32_split(in[mt][0], ah[mt][0], al[mt][0]);
+    tf32_split(in[mt][2], ah[mt][1], al[mt][1]);
+    tf32_split(in[mt][1], ah[mt][2], al[mt][2]);
+    tf32_split(in[mt][3], ah[mt][3], al[mt][3]);
+  }
+  const int l0 = g == 0 ? 0 : g < 4 ? 1 : 2;   // l of row g
+  const int l1 = g == 0 ? 2 : 3;               // l of row g + 8
+#pragma unroll
+  for (int l = 0; l < 5; ++l) {
+    const float2 f = *reinterpret_cast<const float2*>(&F[l * 64 + g * 8 + 2 * t]);
+    uint32_t bh0, bl0, bh1, bl1;
+    tf32_split(f.x, bh0, bl0);
+    tf32_split(f.y, bh1, bl1);
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    if (l < 4) {
+      mma3(d, ah[0], al[0], bh0, bh1, bl0, bl1);
+      if (l == l0) {
+        out[0][0] = d[0];
+        out[0][1] = d[1];
+      }
+      if (l == l1) {
+        out[0][2] = d[2];
+        out[0][3] = d[3];
+      }
+    } else {
+      mma3(d, ah[1], al[1], bh0, bh1, bl0, bl1);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) out[1][e] = d[e];
+    }
+  }
+}
+
 __device__ inline float pack_j(int j, float) { return __int_as_float(j); }
 __device__ inline double pack_j(int j, double) { return __longlong_as_double((long long)j); }
 __device__ inline int unpack_j(float v) { return __float_as_int(v); }
@@ -348,13 +428,16 @@ struct Nu3Coef {
 //   pass 0   row entries inside r_c compacted (displacement and j) into shared memory,
 //            their row positions kept for kernel 3;
 //   stage A  lanes evaluate g and Y for 32 neighbours into a shared tile, then
-//            contract G = g^T Y with 4-wide vector loads along the neighbour axis,
-//            and A = (1/N0) W . G;
+//            contract G = g^T Y; A = (1/N0) W . G;
 //   nu = 1, 2: E12 and dE12/dA (symmetric 8x8 matrix-vector products per (l, m)).
+// FP32: the three contractions run on the tensor cores (warp-level m16n8k8 TF32 MMAs
+// with the 3xTF32 split, FP32 accumulation), G and A staying in accumulator fragments.
+// FP64: SIMT loops, G with 4-wide vector loads along the neighbour axis.
 template <typename R>
 __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB : 1) k_ace_basis(AceArgs<R> a) {
   // Shared memory: W [320] | M2 [320] | C1 [8] | M2b [320] | C1b [8] | per warp: list
-  // [kListCap][4] | tile [kRows][kCols] (A and the G scratch alias the tile after stage A).
+  // [kListCap][4] | tile [kTileWords] (FP32: operand fragments of one batch; FP64: the
+  // g/Y tile [kRows][kCols], which A and the G scratch alias after stage A).
   extern __shared__ __align__(128) unsigned char smem_raw[];
   R* Ws = reinterpret_cast<R*>(smem_raw);
   R* M2 = Ws + 320;
@@ -363,10 +446,8 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
   R* C1b = M2b + 320;
   R* wbase = C1b + 8;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  R* list = wbase + warp * (4 * kListCap + kRows * kCols);
+  R* list = wbase + warp * (4 * kListCap + kTileWords<R>);
   R* tile = list + 4 * kListCap;
-  R* A = tile;
-  R* Gs = tile + 600;
   for (int t = threadIdx.x; t < 320; t += blockDim.x) {
     Ws[t] = a.W[t];
     M2[t] = a.M2[t];
@@ -423,87 +504,203 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
     if (lane == 0) a.nin[q] = nin;
     __syncwarp();
 
-    // ---------------- stage A: G_klm = sum_j g_k Y_lm over the compacted neighbours
-    R acc[7];
+    // ---------------- stage A: G_klm = sum_j g_k Y_lm over the compacted neighbours,
+    // then A = (1/N0) W . G and nu = 1, 2: E12 and dE12/dA
+    R e = R(0);
+    if constexpr (sizeof(R) == 4) {
+      // Tensor cores, 3xTF32: per k-step of 8 neighbours, D[lm][k] += Y^T[lm][j] g[j][k]
+      // for two m-tiles of 16 (l, m) rows.  Each lane evaluates g and Y of one neighbour
+      // and stores them as operand fragments; the accumulators end as G in fragment form.
+      const int g8 = lane >> 2, t4 = lane & 3;
+      float* ty = tile;
+      float* tg = tile + 4 * kTyStep;
+      float acc[2][4];
 #pragma unroll
-    for (int t = 0; t < 7; ++t) acc[t] = R(0);
-    for (int base = 0; base < nin; base += 32) {
-      const int slot = base + lane;
-      R g[8], Y[25];
-      if (slot < nin) {
-        auto e = ld4<R>(&list[4 * slot]);
-        R r2 = e.x * e.x + e.y * e.y + e.z * e.z;
-        R ir = rsqrt_(r2);
-        radial<R, false>(r2 * ir, a.inv_rc, a.mode, g, nullptr);
-        sh_values<R>(e.x * ir, e.y * ir, e.z * ir, Y);
-      } else {
+      for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) g[k] = R(0);
+        for (int u = 0; u < 4; ++u) acc[mt][u] = 0.f;
+      // this lane's neighbour slot c of k-step ks: Y pairs (rows r, r + 8) go to the
+      // fragment of lane (r % 8) * 4 + c % 4, elements 2 (c / 4) and 2 (c / 4) + 1; g_k
+      // to lane k * 4 + c % 4, element c / 4
+      const int pks = lane >> 3, pc = lane & 7;
+      float* yb = ty + pks * kTyStep + (pc & 3) * 4 + (pc >> 2) * 2;
+      float* gb = tg + pks * kTgStep + (pc & 3) * 2 + (pc >> 2);
+      for (int base = 0; base < nin; base += 32) {
+        const int slot = base + lane;
+        float g[8], Y[25];
+        if (slot < nin) {
+          auto en = ld4<R>(&list[4 * slot]);
+          float r2 = en.x * en.x + en.y * en.y + en.z * en.z;
+          float ir = rsqrt_(r2);
+          radial<float, false>(r2 * ir, a.inv_rc, a.mode, g, nullptr);
+          sh_values<float>(en.x * ir, en.y * ir, en.z * ir, Y);
+        } else {
 #pragma unroll
-        for (int k = 0; k < 25; ++k) Y[k] = R(0);
-      }
+          for (int k = 0; k < 8; ++k) g[k] = 0.f;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) tile[k * kCols + lane] = g[k];
+          for (int k = 0; k < 25; ++k) Y[k] = 0.f;
+        }
 #pragma unroll
-      for (int k = 0; k < 25; ++k) tile[(8 + k) * kCols + lane] = Y[k];
-      __syncwarp();
-      const int nv = min(32, nin - base);
-      for (int s4 = 0; s4 < (nv + 3) / 4; ++s4) {
-        auto g4 = ld4<R>(&tile[kq * kCols + 4 * s4]);
+        for (int r = 0; r < 8; ++r) {
+          *reinterpret_cast<float2*>(yb + r * 16) = make_float2(Y[r], Y[r + 8]);
+          *reinterpret_cast<float2*>(yb + 128 + r * 16) = make_float2(Y[16 + r], r == 0 ? Y[24] : 0.f);
+        }
 #pragma unroll
-        for (int t = 0; t < 7; ++t) {
-          const int lm = grp + 4 * t;
-          if (lm < 25) {
-            auto y4 = ld4<R>(&tile[(8 + lm) * kCols + 4 * s4]);
-            acc[t] += g4.x * y4.x + g4.y * y4.y + g4.z * y4.z + g4.w * y4.w;
+        for (int k = 0; k < 8; ++k) gb[k * 8] = g[k];
+        __syncwarp();
+        const int nks = (min(32, nin - base) + 7) >> 3;
+        for (int ks = 0; ks < nks; ++ks) {
+          const float4 y0 = *reinterpret_cast<const float4*>(ty + ks * kTyStep + lane * 4);
+          const float4 y1 = *reinterpret_cast<const float4*>(ty + ks * kTyStep + 128 + lane * 4);
+          const float2 gg = *reinterpret_cast<const float2*>(tg + ks * kTgStep + lane * 2);
+          uint32_t yh0[4], yl0[4], yh1[4], yl1[4], gh0, gl0, gh1, gl1;
+          tf32_split(y0.x, yh0[0], yl0[0]);
+          tf32_split(y0.y, yh0[1], yl0[1]);
+          tf32_split(y0.z, yh0[2], yl0[2]);
+          tf32_split(y0.w, yh0[3], yl0[3]);
+          tf32_split(y1.x, yh1[0], yl1[0]);
+          tf32_split(y1.y, yh1[1], yl1[1]);
+          tf32_split(y1.z, yh1[2], yl1[2]);
+          tf32_split(y1.w, yh1[3], yl1[3]);
+          tf32_split(gg.x, gh0, gl0);
+          tf32_split(gg.y, gh1, gl1);
+          // each k-step's products from zero, summed into acc with round-to-nearest FP32
+          // adds: the tensor core's own accumulation does not round to nearest, and 48
+          // chained MMAs would bias G
+          float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+          mma3(d0, yh0, yl0, gh0, gh1, gl0, gl1);
+          mma3(d1, yh1, yl1, gh0, gh1, gl0, gl1);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            acc[0][u] += d0[u];
+            acc[1][u] += d1[u];
           }
         }
+        __syncwarp();
+      }
+      // acc = G^T as fragments (rows lm, columns k); A = W G, then S = M2 A per l
+      float am[2][4], sm[2][4];
+      lm_mix(acc, Ws, g8, t4, am);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) am[mt][u] *= a.inv_n0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {   // the nu = 3 inputs: n <= 2, lm < 16 (tile 0)
+        const int lm = g8 + 8 * (u >> 1), n = 2 * t4 + (u & 1);
+        if (n < 3) a.a48[(size_t)q * 48 + n * 16 + lm] = am[0][u];
+      }
+      lm_mix(am, M2, g8, t4, sm);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int lm = 16 * mt + g8 + 8 * (u >> 1), n = 2 * t4 + (u & 1);
+          if (lm < 25) {
+            const float lin = lm == 0 ? C1[n] : 0.f;
+            e += am[mt][u] * (0.5f * sm[mt][u] + lin);
+            a.dA[(size_t)q * 200 + n * 25 + lm] = sm[mt][u] + lin;
+          }
+        }
+      if (a.fs_on) {   // the same products with the phi^(2) coefficients
+        lm_mix(am, M2b, g8, t4, sm);
+        float eb = 0.f;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int lm = 16 * mt + g8 + 8 * (u >> 1), n = 2 * t4 + (u & 1);
+            if (lm < 25) {
+              const float lin = lm == 0 ? C1b[n] : 0.f;
+              eb += am[mt][u] * (0.5f * sm[mt][u] + lin);
+              a.dAb[(size_t)q * 200 + n * 25 + lm] = sm[mt][u] + lin;
+            }
+          }
+        const double Eb = warp_sum<double>((double)eb);
+        if (lane == 0) a.e12b[q] = Eb;
+      }
+    } else {
+      // FP64: SIMT, G = g^T Y with 4-wide vector loads along the neighbour axis
+      R* A = tile;
+      R* Gs = tile + 600;
+      R acc[7];
+#pragma unroll
+      for (int t = 0; t < 7; ++t) acc[t] = R(0);
+      for (int base = 0; base < nin; base += 32) {
+        const int slot = base + lane;
+        R g[8], Y[25];
+        if (slot < nin) {
+          auto en = ld4<R>(&list[4 * slot]);
+          R r2 = en.x * en.x + en.y * en.y + en.z * en.z;
+          R ir = rsqrt_(r2);
+          radial<R, false>(r2 * ir, a.inv_rc, a.mode, g, nullptr);
+          sh_values<R>(en.x * ir, en.y * ir, en.z * ir, Y);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) g[k] = R(0);
+#pragma unroll
+          for (int k = 0; k < 25; ++k) Y[k] = R(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) tile[k * kCols + lane] = g[k];
+#pragma unroll
+        for (int k = 0; k < 25; ++k) tile[(8 + k) * kCols + lane] = Y[k];
+        __syncwarp();
+        const int nv = min(32, nin - base);
+        for (int s4 = 0; s4 < (nv + 3) / 4; ++s4) {
+          auto g4 = ld4<R>(&tile[kq * kCols + 4 * s4]);
+#pragma unroll
+          for (int t = 0; t < 7; ++t) {
+            const int lm = grp + 4 * t;
+            if (lm < 25) {
+              auto y4 = ld4<R>(&tile[(8 + lm) * kCols + 4 * s4]);
+              acc[t] += g4.x * y4.x + g4.y * y4.y + g4.z * y4.z + g4.w * y4.w;
+            }
+          }
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int t = 0; t < 7; ++t) {
+        const int lm = grp + 4 * t;
+        if (lm < 25) Gs[kq * 25 + lm] = acc[t];
       }
       __syncwarp();
-    }
-#pragma unroll
-    for (int t = 0; t < 7; ++t) {
-      const int lm = grp + 4 * t;
-      if (lm < 25) Gs[kq * 25 + lm] = acc[t];
-    }
-    __syncwarp();
-    for (int o = lane; o < 200; o += 32) {
-      const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
-      const R* w = &Ws[(l * 8 + n) * 8];
-      R s = R(0);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) s += w[k] * Gs[k * 25 + lm];
-      A[o] = s * a.inv_n0;
-    }
-    __syncwarp();
-    for (int v = lane; v < 48; v += 32) a.a48[(size_t)q * 48 + v] = A[(v >> 4) * 25 + (v & 15)];
-
-    // ---------------- nu = 1, 2: E12 and dE12/dA
-    R e = R(0);
-    for (int o = lane; o < 200; o += 32) {
-      const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
-      const R* mrow = &M2[l * 64 + n * 8];
-      R s = R(0);
-#pragma unroll
-      for (int n2 = 0; n2 < 8; ++n2) s += mrow[n2] * A[n2 * 25 + lm];
-      const R lin = lm == 0 ? C1[n] : R(0);
-      e += A[o] * (R(0.5) * s + lin);
-      a.dA[(size_t)q * 200 + o] = s + lin;
-    }
-    if (a.fs_on) {   // the same products with the phi^(2) coefficients
-      R eb = R(0);
       for (int o = lane; o < 200; o += 32) {
         const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
-        const R* mrow = &M2b[l * 64 + n * 8];
-        R sb = R(0);
+        const R* w = &Ws[(l * 8 + n) * 8];
+        R s = R(0);
 #pragma unroll
-        for (int n2 = 0; n2 < 8; ++n2) sb += mrow[n2] * A[n2 * 25 + lm];
-        const R lin = lm == 0 ? C1b[n] : R(0);
-        eb += A[o] * (R(0.5) * sb + lin);
-        a.dAb[(size_t)q * 200 + o] = sb + lin;
+        for (int k = 0; k < 8; ++k) s += w[k] * Gs[k * 25 + lm];
+        A[o] = s * a.inv_n0;
       }
-      const double Eb = warp_sum<double>((double)eb);
-      if (lane == 0) a.e12b[q] = Eb;
+      __syncwarp();
+      for (int v = lane; v < 48; v += 32) a.a48[(size_t)q * 48 + v] = A[(v >> 4) * 25 + (v & 15)];
+      for (int o = lane; o < 200; o += 32) {
+        const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
+        const R* mrow = &M2[l * 64 + n * 8];
+        R s = R(0);
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) s += mrow[n2] * A[n2 * 25 + lm];
+        const R lin = lm == 0 ? C1[n] : R(0);
+        e += A[o] * (R(0.5) * s + lin);
+        a.dA[(size_t)q * 200 + o] = s + lin;
+      }
+      if (a.fs_on) {   // the same products with the phi^(2) coefficients
+        R eb = R(0);
+        for (int o = lane; o < 200; o += 32) {
+          const int n = o / 25, lm = o - 25 * n, l = l_of(lm);
+          const R* mrow = &M2b[l * 64 + n * 8];
+          R sb = R(0);
+#pragma unroll
+          for (int n2 = 0; n2 < 8; ++n2) sb += mrow[n2] * A[n2 * 25 + lm];
+          const R lin = lm == 0 ? C1b[n] : R(0);
+          eb += A[o] * (R(0.5) * sb + lin);
+          a.dAb[(size_t)q * 200 + o] = sb + lin;
+        }
+        const double Eb = warp_sum<double>((double)eb);
+        if (lane == 0) a.e12b[q] = Eb;
+      }
     }
     const double E = warp_sum<double>((double)e);
     if (lane == 0) {
@@ -689,7 +886,7 @@ __global__ void k_ace_finalize64(int n, const double* __restrict__ acc, double* 
 
 template <typename R>
 size_t basis_smem() {
-  return sizeof(R) * (320 + 320 + 8 + 320 + 8) + sizeof(R) * kWarps<R> * (4 * kListCap + kRows * kCols);
+  return sizeof(R) * (320 + 320 + 8 + 320 + 8) + sizeof(R) * kWarps<R> * (4 * kListCap + kTileWords<R>);
 }
 
 template <typename R>
