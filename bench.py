@@ -59,13 +59,16 @@ ACE_FLOP_PER_ATOM = ADJ_FLOP_PER_ATOM + BASIS_FLOP_PER_ATOM + 11400
 # and 240,000 precise atoms (profiles/k_ace_adjoint_slab50_mixed.md,
 # profiles/k_eam_force_slab50_mixed.md):
 #   k_ace_adjoint  185.6 MB read (mostly the basis kernel's pair records) + 0.7 MB written;
-#   k_ace_basis    45.4 MB read + 121.8 MB written (the pair records, 16 B per pair);
 #   k_eam_force    146.1 MB read + 6.5 MB written.
 ADJ_TRAFFIC_BYTES = 186.3e6 * 240000 / 60000
-BASIS_TRAFFIC_BYTES = 167.2e6 * 240000 / 60000
+BASIS_TRAFFIC_BYTES = None      # k_ace_basis changed (tensor cores) since its last DRAM capture
 EAM_FORCE_TRAFFIC_BYTES = 152.6e6 * 4000000 / 500000
-# FP32 SIMT peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 SIMT peak from unit counts: SMs (read from the device) x 128 FP32 lanes x 2 flop x the
+# maximum SM clock; reported for context beside the measured FFMA peak (ap_probe_peak), which
+# is the denominator of the ALU rooflines.
+FP32_LANES_PER_SM = 128
+SM_MAX_GHZ = 2.07
+MMA_TILE_FLOP = 2 * 16 * 8 * 8       # one m16n8k8 tensor-core tile
 # Algorithmic bytes of one k_eam_force launch: the row entries it walks (4 B each; per
 # atom the prefix up to the last entry inside r_c) plus, per atom, its own shadow,
 # (lambda xi', lambda), xi and prefix length (16 + 8 + 8 + 4 B), its force and E^f
@@ -75,11 +78,27 @@ EAM_FORCE_BYTES_PER_ENTRY = 4
 EAM_FORCE_BYTES_PER_ATOM = 92
 
 
-def kernel_rooflines(ctx, prof, n, hbm_gbs, hbm_src):
+def measured_peaks(dev_index: int):
+    """FP32 FFMA and warp-level TF32 MMA peaks of this GPU, measured now by the library's
+    probe (best of 5 timed runs, SM clock read during the probe), and the derived FP32 figure."""
+    import torch
+    import paper_2411_03002_gb300 as ap
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    ffma, mhz_f = ap.probe_peak(ap.PEAK_FFMA)
+    tf32, mhz_t = ap.probe_peak(ap.PEAK_TF32_MMA)
+    return {"fp32_tflops": ffma, "fp32_sm_mhz": mhz_f, "tf32_mma_tflops": tf32, "tf32_sm_mhz": mhz_t, "sms": sms,
+            "fp32_derived_tflops": sms * FP32_LANES_PER_SM * 2 * SM_MAX_GHZ * 1e9 / 1e12,
+            "source": "measured by ap_probe_peak on this GPU before the timed region (FFMA chains; mma.sync "
+                      "m16n8k8 TF32 tiles)"}
+
+
+def kernel_rooflines(ctx, prof, n, hbm_gbs, hbm_src, peaks):
     """Roofline objects of the instrumented kernels from the step's own CUDA-event timers."""
     ph = prof["phases"]
     pairs, atoms = prof["ace_pairs"], prof["ace_atoms"]
-    alu_src = "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived, not measured)"
+    fp32 = peaks["fp32_tflops"]
+    alu_src = ("measured FFMA peak (ap_probe_peak, %d SMs at %.0f MHz; %.1f TFLOP/s derived from unit counts at "
+               "2.07 GHz)" % (peaks["sms"], peaks["fp32_sm_mhz"], peaks["fp32_derived_tflops"]))
     out = {}
     for name, key, fpp, fpa, traffic in (("k_ace_basis", "ace_basis", BASIS_FLOP_PER_PAIR, BASIS_FLOP_PER_ATOM,
                                           BASIS_TRAFFIC_BYTES),
@@ -87,10 +106,19 @@ def kernel_rooflines(ctx, prof, n, hbm_gbs, hbm_src):
                                           ADJ_TRAFFIC_BYTES)):
         ms, calls = ph[key]
         tf = (fpp * pairs + fpa * atoms) / (ms / 1e3) / 1e12 if ms > 0 else 0.0
-        out[name] = {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": tf / FP32_PEAK_TFLOPS, "traffic": traffic, "peak_source": alu_src,
+        out[name] = {"bound": "alu", "achieved": tf, "peak": fp32, "unit": "TFLOP/s",
+                     "frac": tf / fp32, "traffic": traffic, "peak_source": alu_src,
                      "ms_per_launch": ms / max(1, calls), "ms_total": ms, "launches": calls,
                      "pairs_per_launch": pairs / max(1, calls), "atoms_per_launch": atoms / max(1, calls)}
+    ms, calls = ph["ace_basis"]
+    if ms > 0 and prof.get("ace_mma", 0) > 0:      # tensor-pipe use of the basis kernel
+        tcf = MMA_TILE_FLOP * prof["ace_mma"]
+        out["k_ace_basis"]["tensor"] = {
+            "mma_tiles_per_launch": prof["ace_mma"] / max(1, calls), "achieved": tcf / (ms / 1e3) / 1e12,
+            "peak": peaks["tf32_mma_tflops"], "unit": "TFLOP/s",
+            "frac": tcf / (ms / 1e3) / 1e12 / peaks["tf32_mma_tflops"],
+            "peak_source": "measured mma.sync m16n8k8 TF32 rate (ap_probe_peak)",
+            "note": "issued MMA flops incl. the 3xTF32 split and padding of 25 (l, m) rows to 32"}
     ms, calls = ph["eam_force"]
     walked = ctx.neighbor_total(2)            # row entries the last force pass walked
     b = EAM_FORCE_BYTES_PER_ENTRY * walked + EAM_FORCE_BYTES_PER_ATOM * n
@@ -282,6 +310,7 @@ def run_ours(args, ws, rank, local):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
+    peaks = measured_peaks(local)
     ctx = new_ctx(hyb, detector=ap.DETECT_SELECTOR if args.detector == "selector" else ap.DETECT_CSP)
     x, v, f, mass, fixed, lam = tensors()
     ctx.build_neighbors(x, w.box)
@@ -308,7 +337,7 @@ def run_ours(args, ws, rank, local):
     ace_ms, ace_calls = prof["phases"]["ace"]
     flops = ACE_FLOP_PER_PAIR * prof["ace_pairs"] + ACE_FLOP_PER_ATOM * prof["ace_atoms"]
     hbm_gbs, hbm_src = hbm_peak()
-    rooflines = kernel_rooflines(ctx, prof, w.n, hbm_gbs, hbm_src)
+    rooflines = kernel_rooflines(ctx, prof, w.n, hbm_gbs, hbm_src, peaks)
     dominant = dominant_kernel(rooflines)
     sub = ("ace_adjoint", "eam_force", "ace_basis")
     top = {k: v for k, v in prof["phases"].items() if k not in sub}   # the sub-phases are inside ace / eam
@@ -443,6 +472,7 @@ def run_ours(args, ws, rank, local):
             "gpu_launches": prof["kernels"],
             "roofline": dict(rooflines[dominant], kernel=dominant + " (the kernel with the most time in the step)"),
             "rooflines": rooflines,
+            "peaks": peaks,
             "ace_all_kernels": {"tflops": flops / (ace_ms / 1e3) / 1e12 if ace_ms > 0 else 0.0,
                                 "ms_per_call": ace_ms / max(1, ace_calls)},
             "phase_share": phase_share,

@@ -424,6 +424,23 @@ ap_status ap_profile_enable(ap_ctx* ctx, int32_t on);
 ap_status ap_profile_read(ap_ctx* ctx, double* h_ms, int64_t* h_calls, int64_t* h_kernels, int64_t* h_ace_pairs,
                           int64_t* h_ace_atoms);
 
+/* Tensor-core work counted since the last ap_profile_enable, as of the last
+ * synchronising call: the m16n8k8 TF32 MMA tiles (2 x 16 x 8 x 8 flops each) that
+ * the ACE basis kernel issued (mixed precision; 0 in FP64).  *h_mma is a host
+ * pointer.  No paper counterpart: instrumentation.  Errors: AP_ERR_ARG. */
+ap_status ap_profile_mma(ap_ctx* ctx, int64_t* h_mma);
+
+/* Throughput peak of the current device, measured: which = 0 the FP32 FFMA rate
+ * (eight independent FFMA chains per thread on 4 x 256 threads per SM), which = 1
+ * the warp-level TF32 tensor-core rate (mma m16n8k8, eight independent accumulator
+ * tiles per warp), in TFLOP/s (*h_tflops; an FMA counts 2 flops), and the SM clock
+ * during the best of `reps` runs (*h_sm_mhz, may be NULL: SM cycle counter over the
+ * global nanosecond timer).  reps in [2, 100]; the first run is a warm-up and is not
+ * counted.  Allocates and frees a small device buffer; synchronises the stream.  No
+ * paper counterpart: the denominators of the arithmetic rooflines.
+ * Errors: AP_ERR_ARG (which, reps, null h_tflops), AP_ERR_CUDA. */
+ap_status ap_probe_peak(int32_t which, int32_t reps, void* stream, double* h_tflops, double* h_sm_mhz);
+
 /* ----------------------------------------------------------------- checkpoint */
 
 /* Serialise the lambda histories, previous lambda, ring positions and step

@@ -77,6 +77,8 @@ SIGNATURES = [
     ("ap_eval_eam_static", I32, [P, I64, P, P, P, P, P, P]),
     ("ap_profile_enable", I32, [P, I32]),
     ("ap_profile_read", I32, [P, P, P, P, P, P]),
+    ("ap_profile_mma", I32, [P, P]),
+    ("ap_probe_peak", I32, [I32, I32, P, P, P]),
     ("ap_state_export", I32, [P, P, P]),
     ("ap_state_import", I32, [P, P, ctypes.c_size_t]),
     ("ap_sel_set_model", I32, [P, P, P, P]),

@@ -119,6 +119,19 @@ def ace_gaunt() -> np.ndarray:
     return g
 
 
+PEAK_FFMA = 0
+PEAK_TF32_MMA = 1
+
+
+def probe_peak(which: int = PEAK_FFMA, reps: int = 6, stream=None):
+    """(TFLOP/s, SM MHz) measured on the current device by ap_probe_peak: the FP32
+    FFMA rate (which = PEAK_FFMA) or the warp-level TF32 tensor-core rate
+    (PEAK_TF32_MMA), best of reps - 1 timed runs."""
+    tf, mhz = ctypes.c_double(), ctypes.c_double()
+    _check(None, N.lib().ap_probe_peak(int(which), int(reps), _stream(stream), ctypes.byref(tf), ctypes.byref(mhz)))
+    return tf.value, mhz.value
+
+
 def _check(ctx, st: int):
     if st != N.AP_OK:
         msg = N.lib().ap_last_error(ctx).decode() if ctx else ""
@@ -284,8 +297,10 @@ class Context:
         kern, pairs, atoms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         self._ck(self.lib.ap_profile_read(self.h, ms, calls, ctypes.byref(kern), ctypes.byref(pairs),
                                           ctypes.byref(atoms)))
+        mma = ctypes.c_int64()
+        self._ck(self.lib.ap_profile_mma(self.h, ctypes.byref(mma)))
         return {"phases": {p: (ms[k], calls[k]) for k, p in enumerate(self.PHASES)}, "kernels": kern.value,
-                "ace_pairs": pairs.value, "ace_atoms": atoms.value}
+                "ace_pairs": pairs.value, "ace_atoms": atoms.value, "ace_mma": mma.value}
 
     def state_export(self) -> bytes:
         ln = ctypes.c_size_t()

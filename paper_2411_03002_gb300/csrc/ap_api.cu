@@ -1050,8 +1050,8 @@ ap_status ap_profile_enable(ap_ctx* c, int32_t on) {
   c->ev_used = 0;
   c->kernels = 0;
   CK(cudaDeviceSynchronize());
-  CK(cudaMemset(&c->d_sc->ace_pairs, 0, 2 * sizeof(unsigned long long)));
-  c->h_sc->ace_pairs = c->h_sc->ace_atoms = 0;
+  CK(cudaMemset(&c->d_sc->ace_pairs, 0, 3 * sizeof(unsigned long long)));
+  c->h_sc->ace_pairs = c->h_sc->ace_atoms = c->h_sc->ace_mma = 0;
   return AP_OK;
 }
 
@@ -1065,6 +1065,12 @@ ap_status ap_profile_read(ap_ctx* c, double* h_ms, int64_t* h_calls, int64_t* h_
   if (h_kernels) *h_kernels = c->kernels;
   if (h_ace_pairs) *h_ace_pairs = (int64_t)c->h_sc->ace_pairs;
   if (h_ace_atoms) *h_ace_atoms = (int64_t)c->h_sc->ace_atoms;
+  return AP_OK;
+}
+
+ap_status ap_profile_mma(ap_ctx* c, int64_t* h_mma) {
+  if (!c || !h_mma) return AP_ERR_ARG;
+  *h_mma = (int64_t)c->h_sc->ace_mma;
   return AP_OK;
 }
 

@@ -86,6 +86,7 @@ struct DevScalars {
   double e_ind;
   unsigned long long ace_pairs;   // neighbour pairs within the ACE cutoff processed (cumulative)
   unsigned long long ace_atoms;   // precise atoms processed by the ACE kernel (cumulative)
+  unsigned long long ace_mma;     // m16n8k8 TF32 tensor-core MMAs issued by k_ace_basis (cumulative)
   int n_th_k;                     // local thermostat: |{Delta lambda != 0}| of the last update
   int n_th_e;                     // local thermostat: |{Delta E != 0}| of the last update
   unsigned long long th_n;        // corrections applied (cumulative)

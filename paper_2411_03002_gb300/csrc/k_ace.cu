@@ -707,6 +707,8 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
       a.e12[q] = E;
       atomicAdd(&a.stats->ace_pairs, (unsigned long long)nin);
       atomicAdd(&a.stats->ace_atoms, 1ull);
+      // tensor-core tiles: 6 per k-step of 8 neighbours, 15 per lm_mix
+      if (sizeof(R) == 4) atomicAdd(&a.stats->ace_mma, (unsigned long long)(6 * ((nin + 7) / 8) + (a.fs_on ? 45 : 30)));
     }
     __syncwarp();
   }
