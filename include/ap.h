@@ -251,12 +251,16 @@ ap_status ap_neighbor_total(ap_ctx* ctx, int32_t which, int64_t* h_total);
  *   lambda_avg: mean of the last n_lam_avg lambda_min samples (Eq. lambda_3_i);
  *   lambda = lambda_avg,msz (Eq. lambda_4_i).
  * d_changeable [n] uint8 (NULL = all changeable; 0 = lambda fixed at 1).
+ * sample_now = 1: the update above, pushing this call's CSP and lambda_min samples
+ * into the histories; sample_now = 0: no sample, the lambda of the last update and
+ * its queue are returned (d_x unused; AP_ERR_STATE without an earlier update).
  * Outputs: d_lam [n] FP64; d_precise_idx [n] int32 = ascending indices with
- * lambda < 1 (the precise work queue); d_n_precise device int64.  The first call
- * after creation or ap_reset_lambda fills the histories with its sample.
- * Requires a neighbour build at the same positions for exact CSP candidates. */
-ap_status ap_classify(ap_ctx* ctx, int64_t n, const double* d_x, const uint8_t* d_changeable, double* d_lam,
-                      int32_t* d_precise_idx, int64_t* d_n_precise, void* stream);
+ * lambda < 1 (the precise work queue); d_n_precise device int64 (may be NULL).
+ * The first sampling call after creation or ap_reset_lambda fills the histories
+ * with its sample.  Requires a neighbour build at the same positions for exact
+ * CSP candidates. */
+ap_status ap_classify(ap_ctx* ctx, int64_t n, const double* d_x, const uint8_t* d_changeable, int32_t sample_now,
+                      double* d_lam, int32_t* d_precise_idx, int64_t* d_n_precise, void* stream);
 
 /* The precise work queue of a given lambda (section 2.4: only atoms with
  * lambda_i < 1 need the precise potential): d_queue[0..k) = the ascending
@@ -279,9 +283,13 @@ ap_status ap_get_lambda_state(ap_ctx* ctx, double* d_csp, double* d_csp_avg, dou
 /* EAM for every atom (Eq. energy_eam) with lambda weights (Eq. F_i_d):
  *   d_e_fast[i] = xi(rho_i) + 1/2 sum_j Phi(r_ij)              (written, FP64)
  *   d_f[i]     += -grad_i sum_k lambda_k E_k^(f)  at fixed lambda (accumulated)
- * d_lam [n] FP64 (NULL = all 1).  Requires ap_build_neighbors on the same n. */
+ * d_lam [n] FP64 (NULL = all 1).  d_feat [n][24] FP32 (may be NULL): the
+ * selector's EAM-level features of every atom (ap_sel_features with all atoms
+ * changeable; analytic EAM only, AP_ERR_ARG otherwise); computing them replaces the
+ * CSP sample that ap_get_lambda_state returns.  Requires ap_build_neighbors on the
+ * same n. */
 ap_status ap_eval_eam(ap_ctx* ctx, int64_t n, const double* d_x, const double* d_lam, double* d_e_fast, double* d_f,
-                      void* stream);
+                      float* d_feat, void* stream);
 
 /* Linear ACE for the atoms of the precise queue (Eq. energy_ace) with weights
  * w_i = 1 - lambda_i:
@@ -289,7 +297,9 @@ ap_status ap_eval_eam(ap_ctx* ctx, int64_t n, const double* d_x, const double* d
  *   d_f[k]     += -grad_k sum_i w_i E_i^(p)                           (accumulated)
  * d_precise_idx [*d_n_precise] int32 atom indices (e.g. from ap_classify);
  * d_n_precise is a DEVICE int64.  Builds the ACE rows (ace_rc + skin) for the
- * queue.  d_f may be NULL (energies only). */
+ * queue; the ACE storage (rows, pair records, per-atom scratch) is sized for the
+ * queue's length, read back with one synchronisation of the stream, and grows
+ * when a longer queue arrives.  d_f may be NULL (energies only). */
 ap_status ap_eval_ace(ap_ctx* ctx, int64_t n, const double* d_x, const double* d_lam, const int32_t* d_precise_idx,
                       const int64_t* d_n_precise, double* d_e_prec, double* d_f, void* stream);
 
@@ -307,9 +317,12 @@ ap_status ap_blend_forces(ap_ctx* ctx, int64_t n, const double* d_lam, const dou
  * Fixed atoms (d_fixed[i] != 0) keep v = 0, do not move and keep lambda = 1.
  * On the first call the context prepares neighbours, lambda and F(x(0)) itself.
  * d_x, d_v, d_f [n][3] FP64 in/out; d_mass [n] FP64; d_fixed [n] uint8 or NULL;
- * d_lam [n] FP64 out.  h_stats (may be NULL) is filled at the end; the call
- * synchronises the stream once at its end.  Errors: as above plus AP_ERR_SKIN
- * (an atom moved more than skin/2 before a rebuild) and AP_ERR_NONFINITE. */
+ * d_lam [n] FP64 out.  h_stats (may be NULL) is filled at the end.  The call
+ * synchronises the stream at its end and at every rebuild: there it checks the
+ * error bits so far (an error ends the call), grows the EAM rows if one overflowed,
+ * and reads the new precise queue's length to size the ACE storage for it.
+ * Errors: as above plus AP_ERR_SKIN (an atom moved more than skin/2 before a
+ * rebuild) and AP_ERR_NONFINITE. */
 ap_status ap_step(ap_ctx* ctx, int64_t n, double* d_x, double* d_v, double* d_f, const double* d_mass,
                   const uint8_t* d_fixed, double* d_lam, int64_t nsteps, ap_step_stats* h_stats, void* stream);
 
@@ -391,9 +404,10 @@ ap_status ap_sel_get_grad(ap_ctx* ctx, float* h_grad, float* h_loss);
  * share it, so calls whose kernels overlap on the GPU (e.g. on two streams)
  * race: serialise them.  The first call on each device looks up the array's
  * device address (with that device current); make that first call before any
- * stream capture.  Errors: AP_ERR_ARG for n > 32768, n < 0, null pointers or a
- * bad box/config (including eam_type other than AP_EAM_ANALYTIC); AP_ERR_CUDA if
- * the address lookup or a launch fails. */
+ * stream capture.  `stream` must belong to the current device (NULL: the legacy
+ * default stream).  Errors: AP_ERR_ARG for n > 32768, n < 0, null pointers, a
+ * stream of another device or a bad box/config (including eam_type other than
+ * AP_EAM_ANALYTIC); AP_ERR_CUDA if the address lookup or a launch fails. */
 ap_status ap_eval_eam_static(const ap_config* h_cfg, int64_t n, const double* d_x, const ap_box* h_box,
                              const double* d_lam, double* d_e_fast, double* d_f, void* stream);
 

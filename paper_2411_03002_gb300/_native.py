@@ -66,11 +66,11 @@ SIGNATURES = [
     ("ap_build_neighbors_batch", I32, [P, I32, P, P, P, P, P]),
     ("ap_get_neighbors", I32, [P, I32, P, P, P, I64, P]),
     ("ap_neighbor_total", I32, [P, I32, P]),
-    ("ap_classify", I32, [P, I64, P, P, P, P, P, P]),
+    ("ap_classify", I32, [P, I64, P, P, I32, P, P, P, P]),
     ("ap_reset_lambda", I32, [P]),
     ("ap_precise_queue", I32, [P, I64, P, P, P, P]),
     ("ap_get_lambda_state", I32, [P, P, P, P, P, P, P]),
-    ("ap_eval_eam", I32, [P, I64, P, P, P, P, P]),
+    ("ap_eval_eam", I32, [P, I64, P, P, P, P, P, P]),
     ("ap_eval_ace", I32, [P, I64, P, P, P, P, P, P, P]),
     ("ap_blend_forces", I32, [P, I64, P, P, P, P, P, P]),
     ("ap_step", I32, [P, I64, P, P, P, P, P, P, I64, P, P]),

@@ -222,13 +222,14 @@ class Context:
         return cnt[:r], idx[:r], sh[:r]
 
     # ---------------------------------------------------------------- lambda
-    def classify(self, x: torch.Tensor, changeable: Optional[torch.Tensor] = None, stream=None):
+    def classify(self, x: torch.Tensor, changeable: Optional[torch.Tensor] = None, sample_now: bool = True,
+                 stream=None):
         n = x.shape[0]
         lam = torch.empty(n, dtype=torch.float64, device=x.device)
         idx = torch.empty(max(n, 1), dtype=torch.int32, device=x.device)
         cnt = torch.zeros(1, dtype=torch.int64, device=x.device)
-        self._ck(self.lib.ap_classify(self.h, n, _ptr(x), _ptr(changeable), _ptr(lam), _ptr(idx), _ptr(cnt),
-                                      _stream(stream)))
+        self._ck(self.lib.ap_classify(self.h, n, _ptr(x), _ptr(changeable), 1 if sample_now else 0, _ptr(lam),
+                                      _ptr(idx), _ptr(cnt), _stream(stream)))
         return lam, idx, cnt
 
     def precise_queue(self, lam, stream=None):
@@ -250,13 +251,15 @@ class Context:
         return dict(zip(("csp", "csp_avg", "lam0", "lam_min", "lam_avg"), out))
 
     # ---------------------------------------------------------------- potentials
-    def eval_eam(self, x, lam=None, e_fast=None, f=None, stream=None):
+    def eval_eam(self, x, lam=None, e_fast=None, f=None, feat=None, stream=None):
+        """(e_fast, f); feat, a [n, 24] float32 CUDA tensor, also receives the selector features."""
         n = x.shape[0]
         if e_fast is None:
             e_fast = torch.empty(n, dtype=torch.float64, device=x.device)
         if f is None:
             f = torch.zeros((n, 3), dtype=torch.float64, device=x.device)
-        self._ck(self.lib.ap_eval_eam(self.h, n, _ptr(x), _ptr(lam), _ptr(e_fast), _ptr(f), _stream(stream)))
+        self._ck(self.lib.ap_eval_eam(self.h, n, _ptr(x), _ptr(lam), _ptr(e_fast), _ptr(f), _ptr(feat),
+                                      _stream(stream)))
         return e_fast, f
 
     def eval_ace(self, x, lam, precise_idx, n_precise, e_prec=None, f=None, forces: bool = True, stream=None):
@@ -368,12 +371,12 @@ def ap_build_neighbors(ctx: Context, x, box, species=None, stream=None):
     return ctx.build_neighbors(x, box, species, stream)
 
 
-def ap_classify(ctx: Context, x, changeable=None, stream=None):
-    return ctx.classify(x, changeable, stream)
+def ap_classify(ctx: Context, x, changeable=None, sample_now=True, stream=None):
+    return ctx.classify(x, changeable, sample_now, stream)
 
 
-def ap_eval_eam(ctx: Context, x, lam=None, e_fast=None, f=None, stream=None):
-    return ctx.eval_eam(x, lam, e_fast, f, stream)
+def ap_eval_eam(ctx: Context, x, lam=None, e_fast=None, f=None, feat=None, stream=None):
+    return ctx.eval_eam(x, lam, e_fast, f, feat, stream)
 
 
 def ap_eval_ace(ctx: Context, x, lam, precise_idx, n_precise, e_prec=None, f=None, stream=None):

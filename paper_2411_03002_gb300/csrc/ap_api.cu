@@ -146,10 +146,57 @@ ap_status alloc_rows(ap_ctx* c, bool eam, bool ace) {
     if (c->stored_off) CK(dalloc(c->d_off_eam, (size_t)c->n_cap * c->cap_eam));
   }
   if (ace) {
-    CK(dalloc(c->d_nbr_ace, (size_t)c->n_cap * c->cap_ace));
-    if (c->stored_off) CK(dalloc(c->d_off_ace, (size_t)c->n_cap * c->cap_ace));
+    CK(dalloc(c->d_nbr_ace, (size_t)c->ace_q_cap * c->cap_ace));
+    if (c->stored_off) CK(dalloc(c->d_off_ace, (size_t)c->ace_q_cap * c->cap_ace));
   }
   return AP_OK;
+}
+
+cudaError_t dalloc_bytes(void*& p, size_t bytes) {
+  if (p) cudaFree(p);
+  p = nullptr;
+  return cudaMalloc(&p, bytes ? bytes : 16);
+}
+
+// Pair-record slots per queue position for rows of up to `need` entries (rounded up
+// to 8), reallocated when they grow.
+ap_status ensure_ace_records(ap_ctx* c, int need) {
+  const int r = (need + 7) & ~7;
+  if (c->d_ace_list && r <= c->ace_rec_cap) return AP_OK;
+  c->ace_rec_cap = std::max(r, c->ace_rec_cap);
+  const size_t rb = c->cfg.precision == AP_PREC_FP64 ? sizeof(double) : sizeof(float);
+  CK(dalloc_bytes(c->d_ace_list, rb * 4 * (size_t)c->ace_rec_cap * (size_t)c->ace_q_cap));
+  return AP_OK;
+}
+
+// ACE rows, pair records and per-atom ACE scratch for at least `need` queue positions:
+// sized by the precise queue, not by the atom count, and grown by half again when a
+// longer queue arrives (at most n_cap).
+ap_status ensure_ace_queue(ap_ctx* c, int64_t need) {
+  if (need <= c->ace_q_cap && c->d_cnt_ace) return AP_OK;
+  int64_t m = std::max<int64_t>(need + need / 2, 1024);
+  m = std::max<int64_t>(std::min<int64_t>(m, c->n_cap), need);
+  c->ace_q_cap = m;
+  CK(dalloc(c->d_cnt_ace, m));
+  ap_status st = alloc_rows(c, false, true);
+  if (st) return st;
+  const size_t rb = c->cfg.precision == AP_PREC_FP64 ? sizeof(double) : sizeof(float);
+  CK(dalloc(c->d_ace_nin, m));
+  CK(dalloc(c->d_ace_e12, m));
+  CK(dalloc(c->d_ace_e3, m));
+  CK(dalloc_bytes(c->d_ace_a48, rb * 48 * (size_t)m));
+  CK(dalloc_bytes(c->d_ace_dA, rb * 200 * (size_t)m));
+  CK(dalloc_bytes(c->d_ace_de3, rb * 48 * (size_t)m));
+  CK(dalloc_bytes(c->d_ace_dAb, rb * (c->cfg.ace_fs_on ? 200 : 1) * (size_t)m));
+  if (c->cfg.ace_fs_on) {
+    CK(dalloc(c->d_ace_e12b, m));
+    CK(dalloc(c->d_ace_fs, 2 * m));
+  }
+  if (c->d_ace_list) {   // keep the record width, resize for the new queue length
+    cudaFree(c->d_ace_list);
+    c->d_ace_list = nullptr;
+  }
+  return ensure_ace_records(c, std::max(c->ace_rec_cap, 8));
 }
 
 ap_status ensure_capacity(ap_ctx* c, int64_t n) {
@@ -169,7 +216,6 @@ ap_status ensure_capacity(ap_ctx* c, int64_t n) {
   CK(dalloc(c->d_vscale, m));
   CK(dalloc(c->d_cnt_eam, m));
   CK(dalloc(c->d_lim_eam, m));
-  CK(dalloc(c->d_cnt_ace, m));
   ap_status st = alloc_rows(c, true, true);
   if (st) return st;
   CK(dalloc(c->d_csp, m));
@@ -197,26 +243,6 @@ ap_status ensure_capacity(ap_ctx* c, int64_t n) {
   CK(dalloc(c->d_eatom, m));
   CK(dalloc(c->d_eext, m));
   CK(dalloc(c->d_changeable, m));
-  {
-    const size_t rb = c->cfg.precision == AP_PREC_FP64 ? sizeof(double) : sizeof(float);
-    if (c->d_ace_list) cudaFree(c->d_ace_list);
-    c->d_ace_list = nullptr;
-    CK(cudaMalloc(&c->d_ace_list, rb * 4 * 192 * (size_t)m));
-    CK(dalloc(c->d_ace_nin, m));
-    CK(dalloc(c->d_ace_e12, m));
-    CK(dalloc(c->d_ace_e3, m));
-    void** bufs[4] = {&c->d_ace_a48, &c->d_ace_dA, &c->d_ace_de3, &c->d_ace_dAb};
-    const size_t per[4] = {48, 200, 48, c->cfg.ace_fs_on ? (size_t)200 : (size_t)1};
-    if (c->cfg.ace_fs_on) {
-      CK(dalloc(c->d_ace_e12b, m));
-      CK(dalloc(c->d_ace_fs, 2 * m));
-    }
-    for (int k = 0; k < 4; ++k) {
-      if (*bufs[k]) cudaFree(*bufs[k]);
-      *bufs[k] = nullptr;
-      CK(cudaMalloc(bufs[k], rb * per[k] * (size_t)m));
-    }
-  }
   size_t need_tmp = scan_tmp_bytes(std::max<int64_t>(c->n_cells + 1, m + 1)) / sizeof(int) + 1;
   if (need_tmp > c->scan_tmp_cap) {
     c->scan_tmp_cap = need_tmp;
@@ -293,11 +319,23 @@ ap_status build_checked(ap_ctx* c, const double* d_x, const int32_t* d_species, 
   return AP_OK;
 }
 
-ap_status build_ace_checked(ap_ctx* c, const double* d_x, const int* d_queue, cudaStream_t s) {
+// ACE rows of a queue whose length is the device scalar d_count (a field of
+// c->d_sc), with the ACE storage sized for that length first and the pair records for
+// the longest row after; grows the row capacity once on overflow.  Synchronises.
+ap_status build_ace_checked(ap_ctx* c, const double* d_x, const int* d_queue, const int* d_count, cudaStream_t s) {
+  const size_t off = (size_t)((const char*)d_count - (const char*)c->d_sc);
+  if (off + sizeof(int) > sizeof(DevScalars)) return fail(c, AP_ERR_ARG, "queue length outside the device scalars");
   for (int attempt = 0; attempt < 2; ++attempt) {
     ap_status st = clear_err(c, s);
     if (st) return st;
-    launch_build_ace(c, d_x, d_queue, &c->d_sc->n_precise, s);
+    CK(cudaMemsetAsync(&c->d_sc->ace_row_max, 0, sizeof(int), s));
+    st = read_scalars(c, s);
+    if (st) return st;
+    int m = 0;
+    std::memcpy(&m, (const char*)c->h_sc + off, sizeof(int));
+    st = ensure_ace_queue(c, m);
+    if (st) return st;
+    launch_build_ace(c, d_x, d_queue, d_count, s);
     CK(cudaGetLastError());
     st = read_scalars(c, s);
     if (st) return st;
@@ -307,7 +345,9 @@ ap_status build_ace_checked(ap_ctx* c, const double* d_x, const int* d_queue, cu
       if (st) return st;
       continue;
     }
-    return check_err_bits(c);
+    st = check_err_bits(c);
+    if (st) return st;
+    return ensure_ace_records(c, c->h_sc->ace_row_max);
   }
   return AP_OK;
 }
@@ -464,17 +504,19 @@ ap_status ensure_th(ap_ctx* c) {
 // part over K = {Delta lambda != 0} with weights -Delta lambda (which also gives E^p
 // of K for Delta V), then the EAM part with weights Delta lambda.  Runs before the
 // ACE rows of the new precise queue are built.
-void th_difference(ap_ctx* c, const double* d_x, cudaStream_t s) {
+ap_status th_difference(ap_ctx* c, const double* d_x, cudaStream_t s) {
   const int n = (int)c->n;
   launch_th_delta(c, c->d_th_lamc, c->d_lam_int, s);
   c->kernels += scan_exclusive(c->d_flag, c->d_scan, n, c->d_scan_tmp, s) + 1;
   k_compact_q<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_flag, c->d_scan, c->d_th_qk, &c->d_sc->n_th_k);
-  cudaMemsetAsync(c->d_th_df, 0, sizeof(double) * 3 * (size_t)n, s);
-  cudaMemsetAsync(c->d_th_ep, 0, sizeof(double) * (size_t)n, s);
-  launch_build_ace(c, d_x, c->d_th_qk, &c->d_sc->n_th_k, s);
+  CK(cudaMemsetAsync(c->d_th_df, 0, sizeof(double) * 3 * (size_t)n, s));
+  CK(cudaMemsetAsync(c->d_th_ep, 0, sizeof(double) * (size_t)n, s));
+  ap_status st = build_ace_checked(c, d_x, c->d_th_qk, &c->d_sc->n_th_k, s);
+  if (st) return st;
   launch_ace(c, nullptr, c->d_th_qk, c->d_th_ep, true, s, c->d_th_w, &c->d_sc->n_th_k);
   launch_ace_finalize(c, c->d_th_df, s);
   launch_eam(c, c->d_th_dlam, nullptr, c->d_th_df, true, s);
+  return AP_OK;
 }
 
 // Delta E of every mobile atom from F^d (interatomic forces only) and the queue of
@@ -673,8 +715,8 @@ ap_status ap_neighbor_total(ap_ctx* c, int32_t which, int64_t* h_total) {
   return AP_OK;
 }
 
-ap_status ap_classify(ap_ctx* c, int64_t n, const double* d_x, const uint8_t* d_changeable, double* d_lam,
-                      int32_t* d_precise_idx, int64_t* d_n_precise, void* stream) {
+ap_status ap_classify(ap_ctx* c, int64_t n, const double* d_x, const uint8_t* d_changeable, int32_t sample_now,
+                      double* d_lam, int32_t* d_precise_idx, int64_t* d_n_precise, void* stream) {
   if (!c) return AP_ERR_ARG;
   if (!c->built || n != c->n) return fail(c, AP_ERR_STATE, "ap_classify needs ap_build_neighbors on the same atoms");
   if (n > 0 && (!d_x || !d_lam || !d_precise_idx)) return fail(c, AP_ERR_ARG, "null argument");
@@ -682,6 +724,18 @@ ap_status ap_classify(ap_ctx* c, int64_t n, const double* d_x, const uint8_t* d_
   if (n == 0) {
     if (d_n_precise) CK(cudaMemsetAsync(d_n_precise, 0, sizeof(int64_t), s));
     CK(cudaMemsetAsync(&c->d_sc->n_precise, 0, sizeof(int), s));
+    return AP_OK;
+  }
+  if (!sample_now) {   // no new sample: the lambda of the last update and its queue
+    if (!c->lam_ready || !c->hist_started)
+      return fail(c, AP_ERR_STATE, "ap_classify with sample_now = 0 needs an earlier classification");
+    const int nn = (int)n;
+    CK(cudaMemcpyAsync(d_lam, c->d_lam_prev, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    k_flag_lam<<<(nn + 255) / 256, 256, 0, s>>>(nn, d_lam, c->d_flag);
+    scan_exclusive(c->d_flag, c->d_scan, nn, c->d_scan_tmp, s);
+    k_compact_q64<<<(nn + 255) / 256, 256, 0, s>>>(
+        nn, c->d_flag, c->d_scan, d_precise_idx, d_n_precise ? (long long*)d_n_precise : &c->d_sc->n_precise64);
+    CK(cudaGetLastError());
     return AP_OK;
   }
   ap_status st = prep_detector(c);
@@ -736,14 +790,22 @@ ap_status ap_get_lambda_state(ap_ctx* c, double* d_csp, double* d_csp_avg, doubl
 }
 
 ap_status ap_eval_eam(ap_ctx* c, int64_t n, const double* d_x, const double* d_lam, double* d_e_fast, double* d_f,
-                      void* stream) {
+                      float* d_feat, void* stream) {
   if (!c) return AP_ERR_ARG;
   if (!c->built || n != c->n) return fail(c, AP_ERR_STATE, "ap_eval_eam needs ap_build_neighbors on the same atoms");
   if (n == 0) return AP_OK;
   if (!d_x || !d_e_fast || !d_f) return fail(c, AP_ERR_ARG, "null argument");
+  if (d_feat && c->cfg.eam_type != AP_EAM_ANALYTIC)
+    return fail(c, AP_ERR_ARG, "selector features need eam_type AP_EAM_ANALYTIC");
   cudaStream_t s = S(stream);
   launch_shadow(c, d_x, s);
   launch_eam(c, d_lam, d_e_fast, d_f, true, s);
+  if (d_feat) {   // the selector's EAM-level features from the same rows and shadows
+    ap_status st = ensure_sel_feat(c, n);
+    if (st) return st;
+    launch_csp(c, d_x, nullptr, s);
+    launch_sel_features(c, d_feat, s);
+  }
   CK(cudaGetLastError());
   return AP_OK;
 }
@@ -758,7 +820,7 @@ ap_status ap_eval_ace(ap_ctx* c, int64_t n, const double* d_x, const double* d_l
   launch_shadow(c, d_x, s);
   k_set_count<<<1, 1, 0, s>>>((const long long*)d_n_precise, (int)n, &c->d_sc->n_precise, &c->d_sc->n_precise64);
   k_copy_queue<<<c->num_sms * 4, 256, 0, s>>>(d_precise_idx, &c->d_sc->n_precise, (int)n, c->d_precise, c->d_sc);
-  ap_status st = build_ace_checked(c, d_x, c->d_precise, s);
+  ap_status st = build_ace_checked(c, d_x, c->d_precise, &c->d_sc->n_precise, s);
   if (st) return st;
   CK(cudaMemsetAsync(d_e_prec, 0, sizeof(double) * (size_t)n, s));
   launch_ace(c, d_lam, c->d_precise, d_e_prec, d_f != nullptr, s);
@@ -812,7 +874,7 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
     } else {
       classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s, true);
     }
-    st = build_ace_checked(c, d_x, c->d_precise, s);
+    st = build_ace_checked(c, d_x, c->d_precise, &c->d_sc->n_precise, s);
     if (st) return st;
     CK(cudaMemsetAsync(c->d_eprec, 0, sizeof(double) * (size_t)n, s));
     launch_eam(c, c->d_lam_int, c->d_efast, d_f, false, s);
@@ -842,8 +904,14 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
         PhaseTimer t(c, s, AP_PHASE_NEIGHBORS);
         k_check_skin<<<1, 1, 0, s>>>(c->d_sc, skin_lim2);
         c->kernels += 1;
+        // an error so far (skin, non-finite position) ends the call here
+        st = read_scalars(c, s);
+        if (st) return st;
+        st = check_err_bits(c);
+        if (st) return st;
         launch_wrap_positions(c, d_x, s);
-        build_async(c, d_x, nullptr, s);
+        st = build_checked(c, d_x, nullptr, s);   // grows the EAM rows if one overflows
+        if (st) return st;
       }
       {
         PhaseTimer t(c, s, AP_PHASE_CLASSIFY);
@@ -855,11 +923,14 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
       }
       if (lam_step && thermo) {
         PhaseTimer t(c, s, AP_PHASE_THERMOSTAT);
-        th_difference(c, d_x, s);
+        st = th_difference(c, d_x, s);
+        if (st) return st;
       }
       {
         PhaseTimer t(c, s, AP_PHASE_CLASSIFY);
-        launch_build_ace(c, d_x, c->d_precise, &c->d_sc->n_precise, s);
+        // the new queue's ACE rows, with its storage sized first (synchronises)
+        st = build_ace_checked(c, d_x, c->d_precise, &c->d_sc->n_precise, s);
+        if (st) return st;
       }
     } else {
       PhaseTimer t(c, s, AP_PHASE_NEIGHBORS);

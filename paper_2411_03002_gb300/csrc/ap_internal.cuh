@@ -78,6 +78,7 @@ struct DevScalars {
   int work_counter;   // persistent-kernel work counter
   int work_counter2;  // second persistent-kernel work counter (right after work_counter)
   int n_csp_slow;     // atoms handed from the FP32 CSP kernel to the exact one
+  int ace_row_max;    // longest ACE row of the last ACE row build
   unsigned long long row_total;   // ap_neighbor_total's result
   unsigned int max_disp2_bits;  // float bits of the largest squared displacement
   long long n_precise64;
@@ -182,10 +183,11 @@ struct ap_ctx {
   int* d_cnt_eam = nullptr;      // [n]
   int* d_lim_eam = nullptr;      // [n] the row build's in-range count, then (after each EAM density
                                  //     pass) one past the last entry found inside r_c
-  int* d_nbr_ace = nullptr;      // [n][cap_ace] rows in queue order
+  int* d_nbr_ace = nullptr;      // [ace_q_cap][cap_ace] rows in queue order
   int* d_off_ace = nullptr;
-  int* d_cnt_ace = nullptr;
-  int64_t ace_rows_cap = 0;
+  int* d_cnt_ace = nullptr;      // [ace_q_cap]
+  int64_t ace_q_cap = 0;         // queue positions held by the ACE rows and the ACE scratch below
+  int ace_rec_cap = 0;           // pair-record slots per queue position (>= the longest ACE row)
 
   // lambda state (FP64)
   double* d_csp = nullptr;       // sample
@@ -218,17 +220,17 @@ struct ap_ctx {
   bool restart_pending = false;  // lambda state imported; next ap_step reuses it
   float* d_W32 = nullptr;        // [W (320) | M2 (320) | C1 (8)]
   double* d_W64 = nullptr;
-  // ACE scratch per precise-queue position (sized for n atoms, working precision)
-  void* d_ace_list = nullptr;       // [n][192] in-range (d_x, d_y, d_z, j) records, working precision
-  int* d_ace_nin = nullptr;         // [n]
-  void* d_ace_a48 = nullptr;        // [n][48]
-  void* d_ace_dA = nullptr;         // [n][200]
-  double* d_ace_e12 = nullptr;      // [n]
-  void* d_ace_de3 = nullptr;        // [n][48]
-  double* d_ace_e3 = nullptr;       // [n]
-  void* d_ace_dAb = nullptr;        // [n][200] (Finnis-Sinclair form)
-  double* d_ace_e12b = nullptr;     // [n]
-  double* d_ace_fs = nullptr;       // [n][2]
+  // ACE scratch per precise-queue position q < ace_q_cap (working precision)
+  void* d_ace_list = nullptr;       // [q][ace_rec_cap] in-range (d_x, d_y, d_z, j) records
+  int* d_ace_nin = nullptr;         // [q]
+  void* d_ace_a48 = nullptr;        // [q][48]
+  void* d_ace_dA = nullptr;         // [q][200]
+  double* d_ace_e12 = nullptr;      // [q]
+  void* d_ace_de3 = nullptr;        // [q][48]
+  double* d_ace_e3 = nullptr;       // [q]
+  void* d_ace_dAb = nullptr;        // [q][200] (Finnis-Sinclair form)
+  double* d_ace_e12b = nullptr;     // [q]
+  double* d_ace_fs = nullptr;       // [q][2]
 
   // scan scratch
   int* d_scan_tmp = nullptr;

@@ -364,7 +364,7 @@ __device__ inline float4 make_r4(float a, float b, float c, float d) { return ma
 __device__ inline double4_32a make_r4(double a, double b, double c, double d) { return make_double4_32a(a, b, c, d); }
 __device__ inline int unpack_j(double v) { return (int)__double_as_longlong(v); }
 
-constexpr int kListCap = 192;   // neighbours inside ace_rc kept per precise atom (FCC bulk: 134)
+constexpr int kListCap = 192;   // in-range records per precise atom cached in shared memory (FCC bulk: 134)
 #ifndef AP_ACE3_WARPS
 #define AP_ACE3_WARPS 6
 #endif
@@ -406,7 +406,8 @@ struct AceArgs {
   double* e_prec;
   float4* facc32;
   double* facc64;
-  typename V<R>::R4* list4;   // [q][kListCap] in-range (d, j) records in row order (kernel 1 -> 3)
+  typename V<R>::R4* list4;   // [q][rec] in-range (d, j) records in row order (kernel 1 -> 3)
+  int rec;                    // record slots per queue position (>= every ACE row's length)
   int* nin;          // [q] their number
   R* a48;            // [q][48] A entries with n <= 2, l <= 3 (input of nu = 3)
   R* dA;             // [q][200] dE/dA of nu = 1, 2
@@ -461,6 +462,7 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
   const int m = *a.count;
   const int kq = lane & 7, grp = lane >> 3;
   const unsigned lt_mask = (1u << lane) - 1u;
+  unsigned long long cnt_pairs = 0, cnt_atoms = 0, cnt_mma = 0;   // profiling counts of this warp
   while (true) {
     int q = 0;
     if (lane == 0) q = atomicAdd(a.counter, 1);
@@ -486,23 +488,16 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
         in = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < a.rc2;
       }
       const unsigned mask = __ballot_sync(0xffffffffu, in);
-      const int pos = nin + __popc(mask & lt_mask);
-      if (in && pos < kListCap) {
-        R* e = &list[4 * pos];
-        e[0] = d[0];
-        e[1] = d[1];
-        e[2] = d[2];
-        e[3] = pack_j(j, R(0));
-        a.list4[(size_t)q * kListCap + pos] = make_r4(d[0], d[1], d[2], e[3]);
+      const int pos = nin + __popc(mask & lt_mask);   // < c <= rec
+      if (in) {
+        const auto rec = make_r4(d[0], d[1], d[2], pack_j(j, R(0)));
+        a.list4[(size_t)q * a.rec + pos] = rec;
+        if (pos < kListCap) *reinterpret_cast<typename V<R>::R4*>(&list[4 * pos]) = rec;
       }
       nin += __popc(mask);
     }
-    if (nin > kListCap) {
-      if (lane == 0) atomicOr(&a.stats->err, kErrCapacity);
-      nin = kListCap;
-    }
     if (lane == 0) a.nin[q] = nin;
-    __syncwarp();
+    __syncwarp();   // also orders this warp's record stores before the reads of stage A
 
     // ---------------- stage A: G_klm = sum_j g_k Y_lm over the compacted neighbours,
     // then A = (1/N0) W . G and nu = 1, 2: E12 and dE12/dA
@@ -529,7 +524,7 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
         const int slot = base + lane;
         float g[8], Y[25];
         if (slot < nin) {
-          auto en = ld4<R>(&list[4 * slot]);
+          const auto en = slot < kListCap ? ld4<R>(&list[4 * slot]) : a.list4[(size_t)q * a.rec + slot];
           float r2 = en.x * en.x + en.y * en.y + en.z * en.z;
           float ir = rsqrt_(r2);
           radial<float, false>(r2 * ir, a.inv_rc, a.mode, g, nullptr);
@@ -630,7 +625,7 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
         const int slot = base + lane;
         R g[8], Y[25];
         if (slot < nin) {
-          auto en = ld4<R>(&list[4 * slot]);
+          const auto en = slot < kListCap ? ld4<R>(&list[4 * slot]) : a.list4[(size_t)q * a.rec + slot];
           R r2 = en.x * en.x + en.y * en.y + en.z * en.z;
           R ir = rsqrt_(r2);
           radial<R, false>(r2 * ir, a.inv_rc, a.mode, g, nullptr);
@@ -703,14 +698,17 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
       }
     }
     const double E = warp_sum<double>((double)e);
-    if (lane == 0) {
-      a.e12[q] = E;
-      atomicAdd(&a.stats->ace_pairs, (unsigned long long)nin);
-      atomicAdd(&a.stats->ace_atoms, 1ull);
-      // tensor-core tiles: 6 per k-step of 8 neighbours, 15 per lm_mix
-      if (sizeof(R) == 4) atomicAdd(&a.stats->ace_mma, (unsigned long long)(6 * ((nin + 7) / 8) + (a.fs_on ? 45 : 30)));
-    }
+    if (lane == 0) a.e12[q] = E;
+    cnt_pairs += nin;
+    cnt_atoms += 1;
+    // tensor-core tiles: 6 per k-step of 8 neighbours, 15 per lm_mix
+    if (sizeof(R) == 4) cnt_mma += 6 * ((nin + 7) / 8) + (a.fs_on ? 45 : 30);
     __syncwarp();
+  }
+  if (lane == 0 && cnt_atoms > 0) {   // the warp's counts, added once
+    atomicAdd(&a.stats->ace_pairs, cnt_pairs);
+    atomicAdd(&a.stats->ace_atoms, cnt_atoms);
+    if (sizeof(R) == 4) atomicAdd(&a.stats->ace_mma, cnt_mma);
   }
 }
 
@@ -832,7 +830,7 @@ __global__ void __launch_bounds__(kWarps3<R> * 32, sizeof(R) == 4 ? AP_ACE3_MINB
     R pix = R(0), piy = R(0), piz = R(0);
     // the pair records kernel 1 kept (displacement and j, coalesced), the lane's next
     // one loaded an iteration ahead
-    const typename V<R>::R4* lst = a.list4 + (size_t)q * kListCap;
+    const typename V<R>::R4* lst = a.list4 + (size_t)q * a.rec;
     typename V<R>::R4 e_n = make_r4(R(0), R(0), R(0), R(0));
     if (lane < nin) e_n = lst[lane];
     for (int base = 0; base < nin; base += 32) {
@@ -947,6 +945,7 @@ void run_ace(ap_ctx* c, const double* d_lam, const double* d_wgt, const int* d_q
   a.mode = c->cfg.fcut_mode;
   a.e_prec = d_e_prec;
   a.list4 = reinterpret_cast<typename V<R>::R4*>(c->d_ace_list);
+  a.rec = c->ace_rec_cap;
   a.nin = c->d_ace_nin;
   a.a48 = reinterpret_cast<R*>(c->d_ace_a48);
   a.dA = reinterpret_cast<R*>(c->d_ace_dA);

@@ -127,9 +127,10 @@ __global__ void k_eam_static_force(int n, const double* __restrict__ x, StaticBo
 std::mutex g_mu;
 void* g_ptr[128] = {};
 
-ap_status scratch_address(double** out) {
+ap_status scratch_address(double** out, int* dev_out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return AP_ERR_CUDA;
+  *dev_out = dev;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_ptr[dev]) {
     void* p = nullptr;
@@ -163,9 +164,15 @@ extern "C" ap_status ap_eval_eam_static(const ap_config* h_cfg, int64_t n, const
   StaticEam p{c.eam_beta, c.eam_beta / c.eam_r0, c.eam_alpha, c.eam_A, c.eam_D, c.eam_rp, c.eam_rc,
               c.eam_rc * c.eam_rc, 1.0 / c.eam_h};
   double* scratch = nullptr;
-  ap_status st = scratch_address(&scratch);
+  int dev = 0;
+  ap_status st = scratch_address(&scratch, &dev);
   if (st != AP_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (s) {   // the scratch address is the current device's, so the stream must run there too
+    int sdev = -1;
+    if (cudaStreamGetDevice(s, &sdev) == cudaSuccess && sdev != dev) return AP_ERR_ARG;
+    cudaGetLastError();
+  }
   const int threads = 128, blocks = (int)((n + threads - 1) / threads);
   k_eam_static_density<<<blocks, threads, 0, s>>>((int)n, d_x, b, p, d_lam, scratch);
   k_eam_static_force<<<blocks, threads, 0, s>>>((int)n, d_x, b, p, scratch, d_e_fast, d_f);

@@ -446,6 +446,7 @@ __global__ void __launch_bounds__(256) k_build_ace(const int* __restrict__ queue
                                  off ? off + (size_t)q * cap : nullptr);
     if ((threadIdx.x & 31) == 0) {
       cnt[q] = c < cap ? c : cap;
+      atomicMax(&sc->ace_row_max, c < cap ? c : cap);
       if (c > cap) {
         atomicMax(&sc->need_ace, c);
         atomicOr(&sc->err, kErrCapacity);

@@ -83,7 +83,7 @@ def test_config_validation_rejects_bad_values():
 def test_null_context_calls_fail_cleanly():
     lib = N.lib()
     assert lib.ap_build_neighbors(None, 0, None, None, None, None) == 1
-    assert lib.ap_classify(None, 0, None, None, None, None, None, None) == 1
+    assert lib.ap_classify(None, 0, None, None, 1, None, None, None, None) == 1
     assert lib.ap_step(None, 0, None, None, None, None, None, None, 0, None, None) == 1
     assert lib.ap_last_error(None) == b"null context"
 

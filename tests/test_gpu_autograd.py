@@ -86,11 +86,18 @@ def test_batch_of_64_cells_in_one_launch():
     e = energy(x, lam, ctx, batch=(offs.tolist(), [c.box for c in cells]))
     e.backward()
     f = -x.grad.cpu().numpy()
+    # per-cell energies: the site energies of the same context on the same rows
+    idx, cnt = ctx.precise_queue(lam)
+    ef, _ = ctx.eval_eam(x.detach(), lam)
+    ep, _ = ctx.eval_ace(x.detach(), lam, idx, cnt, forces=False)
+    e_atom = ctx.blend_forces(lam, ef, ep)[0].cpu().numpy()
     ace = O.ACE(I.ace_params(0))
-    e_sum = 0.0
-    for k in (0, 31, 63):
-        c = cells[k]
+    e_sum, n_sum = 0.0, 0
+    for k, c in enumerate(cells):         # every cell: forces from backward, the cell's energy
         e_o, f_o, _, _ = O.hybrid(c.x, c.box, c.lam, I.eam_params(0), ace)
         d = np.linalg.norm(f[offs[k]:offs[k + 1]] - f_o, axis=1)
         assert d.max() <= 1e-3, (k, d.max())
-    assert np.isfinite(e.item())
+        assert abs(e_atom[offs[k]:offs[k + 1]].sum() - e_o.sum()) / c.n <= 1e-6, k
+        e_sum += e_o.sum()
+        n_sum += c.n
+    assert abs(e.item() - e_sum) / n_sum <= 1e-6

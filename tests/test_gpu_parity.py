@@ -127,6 +127,37 @@ def test_classify_history_sequence_bit_exact():
         lam_o, *_ = O.classify(ost, x, w.box, hyb)
         assert np.array_equal(lam.cpu().numpy(), lam_o), it
         x = x + 0.04 * g.standard_normal(x.shape)
+        # without a sample (sample_now = 0): the last update's lambda and queue, at moved
+        # positions, and the histories untouched (the next update still matches the oracle)
+        ctx.build_neighbors(T(x), w.box)
+        lam2, q2, cnt2 = ctx.classify(T(x), sample_now=False)
+        assert np.array_equal(lam2.cpu().numpy(), lam_o), it
+        n2 = int(cnt2.item())
+        assert n2 == int(cnt.item()) and np.array_equal(q2[:n2].cpu().numpy(), np.nonzero(lam_o < 1.0)[0])
+
+
+def test_classify_without_sample_needs_an_update():
+    w = I.config_c1()
+    ctx = ctx_for(w, ap.PREC_MIXED)
+    ctx.build_neighbors(T(w.x), w.box)
+    with pytest.raises(ap.ApError) as e:
+        ctx.classify(T(w.x), sample_now=False)
+    assert e.value.status == 6          # AP_ERR_STATE
+
+
+def test_eval_eam_features_equal_sel_features():
+    """ap_eval_eam's optional feature output is the selector's 24 features of every atom,
+    the same values ap_sel_features gives (same kernels, all atoms changeable)."""
+    w = I.config_c2()
+    ctx = ctx_for(w, ap.PREC_MIXED)
+    x = T(w.x)
+    ctx.build_neighbors(x, w.box)
+    feat = torch.empty((w.n, 24), dtype=torch.float32, device=DEV)
+    ef, f = ctx.eval_eam(x, feat=feat)
+    ref = ctx.sel_features(x)
+    assert torch.equal(feat, ref)
+    ef2, f2 = ctx.eval_eam(x)
+    assert torch.equal(ef, ef2) and torch.equal(f, f2)
 
 
 # ------------------------------------------------------------------ potentials
@@ -212,13 +243,14 @@ def test_batched_cells_one_launch():
     ef, f = ctx.eval_eam(T(x), T(lam))
     ep, f = ctx.eval_ace(T(x), T(lam), T(q, torch.int32), torch.tensor([len(q)], dtype=torch.int64, device=DEV),
                          f=f)
-    f = f.cpu().numpy()
+    e_atom, _ = ctx.blend_forces(T(lam), ef, ep)
+    f, e_atom = f.cpu().numpy(), e_atom.cpu().numpy()
     ace = O.ACE(I.ace_params(0))
-    for k in (0, 17, 63):
-        c = cells[k]
+    for k, c in enumerate(cells):         # every cell: forces and the cell's energy
         e_o, f_o, _, _ = O.hybrid(c.x, c.box, c.lam, I.eam_params(0), ace)
         ok, worst = force_ok(f[offs[k]:offs[k + 1]], f_o, ap.PREC_MIXED)
         assert ok, (k, worst)
+        assert abs(e_atom[offs[k]:offs[k + 1]].sum() - e_o.sum()) / c.n <= 1e-6, k
 
 
 # ------------------------------------------------------------------ dynamics
