@@ -276,6 +276,49 @@ def reference_arm(args, ws, rank):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def c2_record(dev, nsteps: int = 200):
+    """The 32,000-atom adaptive-MD slab (20^3 FCC cells, x/y periodic, a 0.3 A-disordered
+    hemisphere of 15 A under the top surface, Hyb1, lambda every 10 steps, lists rebuilt every
+    5 steps) for 200 MD steps of 1 fs from 300 K, in FP64 and in mixed precision from the same
+    start: rates, total-energy drift and the largest difference between the two precisions'
+    final forces and positions.  The oracle comparison of the same runs' final forces is a test
+    (tests/test_gpu_md.py)."""
+    import torch
+    import paper_2411_03002_gb300 as ap
+    w = I.config_c2()
+    out = {"workload": "FCC slab 20^3 cells (32,000 atoms), x/y periodic, 0.3 A-disordered 15 A hemisphere, "
+                       "Hyb1, lambda every 10 steps, %d MD steps of 1 fs from 300 K" % nsteps}
+    final = {}
+    for pname, p in (("fp64", ap.PREC_FP64), ("mixed", ap.PREC_MIXED)):
+        cfg = ap.make_config(I.eam_params(0), I.ace_for_config(2), w.hyb, precision=p, dt=w.dt, lambda_every=10,
+                             rebuild_every=5)
+        c = ap.Context(cfg)
+        x, v = torch.as_tensor(w.x, device=dev).clone(), torch.as_tensor(w.v, device=dev).clone()
+        f = torch.zeros_like(x)
+        lam = torch.empty(w.n, dtype=torch.float64, device=dev)
+        m = torch.as_tensor(w.mass, device=dev)
+        c.build_neighbors(x, w.box)
+        s0 = c.step(x, v, f, m, None, lam, 0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(torch.cuda.current_stream())
+        s1 = c.step(x, v, f, m, None, lam, nsteps)
+        b.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b)
+        out[pname] = {"atom_steps_s": w.n * nsteps / (t / 1e3), "precise_fraction": s1.n_precise / w.n,
+                      "drift_eV_per_atom": (s1.e_pot + s1.e_kin - s0.e_pot - s0.e_kin) / w.n}
+        final[pname] = (x.clone(), f.clone())
+        c.close()
+        del c
+    (x64, f64), (x32, f32) = final["fp64"], final["mixed"]
+    out["mixed_vs_fp64"] = {
+        "force_max_meV_A": float(torch.linalg.vector_norm(f32 - f64, dim=1).max().item() * 1e3),
+        "force_rms_meV_A": float(torch.sqrt(((f32 - f64) ** 2).mean()).item() * 1e3),
+        "position_p99_A": float(torch.quantile(torch.linalg.vector_norm(x32 - x64, dim=1), 0.99).item())}
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_2411_03002_gb300 as ap
@@ -311,12 +354,15 @@ def run_ours(args, ws, rank, local):
             torch.cuda.synchronize()
 
     peaks = measured_peaks(local)
+    free0 = torch.cuda.mem_get_info(local)[0]
     ctx = new_ctx(hyb, detector=ap.DETECT_SELECTOR if args.detector == "selector" else ap.DETECT_CSP)
     x, v, f, mass, fixed, lam = tensors()
     ctx.build_neighbors(x, w.box)
     stats = ctx.step(x, v, f, mass, fixed, lam, 0)
     for _ in range(args.warmup):
         stats = ctx.step(x, v, f, mass, fixed, lam, MD_PER_STEP)
+    stats_start = stats
+    footprint_gb = (free0 - torch.cuda.mem_get_info(local)[0]) / 1e9   # library scratch + the run's own state
     barrier()
     ctx.profile_enable(True)
     clocks = Clocks(local)
@@ -364,32 +410,80 @@ def run_ours(args, ws, rank, local):
     h2d = 3 * w.n * 3 * 8
     d2h = 3 * w.n * 3 * 8 + w.n * 8
 
+    drift = (stats.e_pot + stats.e_kin - stats_start.e_pot - stats_start.e_kin) / w.n
+
+    def timed_mode(make, steps):
+        """One mode of the comparison on the same workload and GPU: a fresh context, one
+        warm-up bench step, then `steps` timed bench steps with their own clock record."""
+        c = make()
+        x2, v2, f2, m2, fx2, l2 = tensors()
+        c.build_neighbors(x2, w.box)
+        c.step(x2, v2, f2, m2, fx2, l2, 0)
+        s0 = c.step(x2, v2, f2, m2, fx2, l2, MD_PER_STEP)
+        torch.cuda.synchronize()
+        ck2 = Clocks(local)
+        ck2.start()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            s1 = c.step(x2, v2, f2, m2, fx2, l2, MD_PER_STEP)
+        b.record(stream)
+        torch.cuda.synchronize()
+        clk = ck2.stop()
+        t = a.elapsed_time(b)
+        out = {"atom_steps_s": w.n * MD_PER_STEP * steps / (t / 1e3), "ms_per_step": t / steps, "steps": steps,
+               "precise_fraction": s1.n_precise / w.n,
+               "drift_eV_per_atom": (s1.e_pot + s1.e_kin - s0.e_pot - s0.e_kin) / w.n, "clocks": clk}
+        if s1.th_corrected or s1.th_refused:
+            out["thermostat"] = {"corrections": s1.th_corrected, "refused": s1.th_refused,
+                                 "corrected_energy_eV": s1.th_energy}
+        c.close()
+        del c, x2, v2, f2, m2, fx2, l2
+        torch.cuda.empty_cache()
+        return out
+
+    def rms_max(d):
+        return {"rms_meV_A": float(torch.sqrt((d * d).mean()).item() * 1e3) if d.numel() else None,
+                "max_meV_A": float(torch.linalg.vector_norm(d, dim=1).max().item() * 1e3) if d.numel() else None,
+                "atoms": int(d.shape[0])}
+
     extras = {}
     cpu = None
     if rank == 0 and not args.no_extras:
         lam0 = ctx.get_lambda_state()["lam0"]
-        detected = torch.nonzero(lam0 < 1.0).flatten()
+        detected = lam0 < 1.0
         xs, lams = x.clone(), lam.clone()
         ctx.close()
         del ctx
         torch.cuda.empty_cache()
-        # force error on detected atoms: adaptive forces vs full ACE, same positions (FP32 path)
-        ev = new_ctx(hyb)
-        ev.build_neighbors(xs, w.box)
-        q = torch.nonzero(lams < 1.0).flatten().to(torch.int32)
-        nq = torch.tensor([q.numel()], dtype=torch.int64, device=dev)
-        _, fh_ = ev.eval_eam(xs, lams)
-        _, fh_ = ev.eval_ace(xs, lams, q, nq, f=fh_)
-        z = torch.zeros_like(lams)
+        # force error against full ACE at the timed run's final positions and lambda, in both
+        # precisions: on the detected set (the paper's defect and surface atoms), on {lambda = 0}
+        # and on every precise atom; full EAM (lambda = 1 everywhere) on the detected set
         allq = torch.arange(w.n, dtype=torch.int32, device=dev)
         na = torch.tensor([w.n], dtype=torch.int64, device=dev)
-        _, fa_ = ev.eval_eam(xs, z)
-        _, fa_ = ev.eval_ace(xs, z, allq, na, f=fa_)
-        d = (fh_ - fa_)[detected]
-        extras["force_err_rms_meV_A_detected"] = float(torch.sqrt((d * d).mean()).item() * 1e3)
-        extras["force_err_max_meV_A_detected"] = float(d.abs().max().item() * 1e3)
-        # atoms whose full-ACE and full-EAM forces differ by more than the selector's label threshold
-        _, fe_ = ev.eval_eam(xs, torch.ones_like(lams))
+        q = torch.nonzero(lams < 1.0).flatten().to(torch.int32)
+        nq = torch.tensor([q.numel()], dtype=torch.int64, device=dev)
+        z = torch.zeros_like(lams)
+        ferr = {}
+        for pname, p in (("mixed", ap.PREC_MIXED), ("fp64", ap.PREC_FP64)):
+            ev = new_ctx(hyb, p=p)
+            ev.build_neighbors(xs, w.box)
+            _, fh_ = ev.eval_eam(xs, lams)
+            _, fh_ = ev.eval_ace(xs, lams, q, nq, f=fh_)
+            _, fa_ = ev.eval_eam(xs, z)
+            _, fa_ = ev.eval_ace(xs, z, allq, na, f=fa_)
+            _, fe_ = ev.eval_eam(xs, torch.ones_like(lams))
+            ferr[pname] = {"adaptive_vs_full_ace": {"detected": rms_max((fh_ - fa_)[detected]),
+                                                    "lambda0": rms_max((fh_ - fa_)[lams == 0.0]),
+                                                    "precise": rms_max((fh_ - fa_)[lams < 1.0])},
+                           "full_eam_vs_full_ace": {"detected": rms_max((fe_ - fa_)[detected])}}
+            ev.close()
+            if pname == "mixed":
+                fh_m, fa_m, fe_m = fh_, fa_, fe_
+            del ev, fh_, fa_, fe_
+            torch.cuda.empty_cache()
+        extras["force_error"] = ferr
+        fh_, fa_, fe_ = fh_m, fa_m, fe_m
         mobile = torch.as_tensor(w.fixed, device=dev) == 0
         # scored region: mobile atoms with no fixed (always-EAM) atom inside the ACE cutoff,
         # since no detector can remove the error that the fixed layers contribute
@@ -397,8 +491,6 @@ def run_ours(args, ws, rank, local):
         scored = mobile & (torch.as_tensor(w.x[:, 2], device=dev) > z_fixed + float(acep.rc))
         pos = (torch.linalg.vector_norm(fa_ - fe_, dim=1) > float(sel["tau"])) & scored
         dp = (fh_ - fa_)[pos]
-        ev.close()
-        del ev
         # the same positions classified by the selector instead of CSP
         es = new_ctx(hyb, detector=ap.DETECT_SELECTOR)
         es.build_neighbors(xs, w.box)
@@ -415,38 +507,26 @@ def run_ours(args, ws, rank, local):
             "csp_precise_fraction": float((lams < 1.0).float().mean().item()),
         }
         es.close()
-        del es, fs_, fa_, fe_, fh_
+        del es, fs_, fa_, fe_, fh_, fh_m, fa_m, fe_m
         torch.cuda.empty_cache()
-        # full-ACE, full-EAM and selector-driven adaptive MD on the same GPU, same workload, same code path
-        for mode in ("full-ace", "full-eam", "selector", "thermostat"):
-            c2 = (new_ctx(hyb, detector=ap.DETECT_SELECTOR) if mode == "selector"
-                  else new_ctx(hyb, thermostat=True) if mode == "thermostat"
-                  else new_ctx(hyb_for(mode, w.hyb)))
-            x2, v2, f2, m2, fx2, l2 = tensors()
-            c2.build_neighbors(x2, w.box)
-            c2.step(x2, v2, f2, m2, fx2, l2, 0)
-            c2.step(x2, v2, f2, m2, fx2, l2, MD_PER_STEP)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            k2 = 2
-            for _ in range(k2):
-                c2.step(x2, v2, f2, m2, fx2, l2, MD_PER_STEP)
-            b.record(stream)
-            torch.cuda.synchronize()
-            rate = w.n * MD_PER_STEP * k2 / (a.elapsed_time(b) / 1e3)
-            if mode == "selector":
-                extras["selector"]["atom_steps_s"] = rate
-            elif mode == "thermostat":
-                st2 = c2.step(x2, v2, f2, m2, fx2, l2, 0)
-                extras["thermostat"] = {"atom_steps_s": rate, "corrections": st2.th_corrected,
-                                        "refused": st2.th_refused, "corrected_energy_eV": st2.th_energy}
-            else:
-                extras[mode.replace("-", "_") + "_atom_steps_s"] = rate
-            c2.close()
-            del c2, x2, v2, f2, m2, fx2, l2
-            torch.cuda.empty_cache()
-        extras["speedup_vs_full_ace"] = value / ws / extras["full_ace_atom_steps_s"]
+        # the comparison of the paper's nanoindentation run: adaptive (mixed, the timed run above;
+        # FP64), full ACE and full EAM, plus the selector detector and the local thermostat, on the
+        # same GPU and workload, each timed over the same number of bench steps
+        modes = {"adaptive_mixed": {"atom_steps_s": value / ws, "ms_per_step": ms / args.steps,
+                                    "steps": args.steps, "precise_fraction": stats.n_precise / w.n,
+                                    "drift_eV_per_atom": drift,
+            "memory": {"device_gb": footprint_gb, "what": "device memory taken by the context and the run's x, v, f, "
+                                                        "mass, fixed, lambda after warm-up (cudaMemGetInfo)"}, "clocks": ck}}
+        for name, make in (("adaptive_fp64", lambda: new_ctx(hyb, p=ap.PREC_FP64)),
+                           ("full_ace", lambda: new_ctx(hyb_for("full-ace", w.hyb))),
+                           ("full_eam", lambda: new_ctx(hyb_for("full-eam", w.hyb))),
+                           ("adaptive_selector", lambda: new_ctx(hyb, detector=ap.DETECT_SELECTOR)),
+                           ("adaptive_thermostat", lambda: new_ctx(hyb, thermostat=True))):
+            modes[name] = timed_mode(make, args.steps)
+        extras["modes"] = modes
+        extras["selector"]["atom_steps_s"] = modes["adaptive_selector"]["atom_steps_s"]
+        extras["speedup_vs_full_ace"] = value / ws / modes["full_ace"]["atom_steps_s"]
+        extras["c2"] = c2_record(dev)
         if ws == 1:
             n_s, times, cores = oracle_sample(w.hyb, reps=1)
             cpu = {"value": n_s / times[0], "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
@@ -467,6 +547,7 @@ def run_ours(args, ws, rank, local):
                        else "FP64", "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "precise_fraction": stats.n_precise / w.n, "n_precise": stats.n_precise, "n_detected": stats.n_detected,
+            "drift_eV_per_atom": drift,
             "e2e": {"value": atom_steps / (ms_e2e / 1e3), "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": prof["kernels"],

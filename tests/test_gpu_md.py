@@ -7,9 +7,12 @@ The 0.3 A-disordered hemisphere melts in the first ~50 fs (atoms move ~0.05 A/fs
 there, with EAM as with ACE), so the lists are rebuilt every 5 steps to keep
 every displacement between rebuilds below skin/2 = 0.5 A.
 * Adaptive run (Hyb1, lambda every 10 steps) for 200 steps in FP64 and in mixed
-  precision from the same start: both stay finite, the precise fraction stays in
-  a sane range, and the final FP64 forces match the oracle on sampled atoms
-  (same tolerance as the other FP64 parity tests), the mixed ones within 1 meV/A.
+  precision from the same start (the bench's c2 record): both stay finite, the
+  precise fraction stays in a sane range, and the final forces of all 32,000 atoms
+  match the oracle evaluated on the whole slab at the GPU's final positions and
+  lambda (FP64: the per-atom FP64 bar of the other parity tests; mixed: 1 meV/A);
+  the energy drift of the two runs (without the local thermostat, lambda changes
+  move the energy) agrees within 1e-5 eV/atom.
 """
 import dataclasses
 
@@ -72,23 +75,19 @@ def test_adaptive_runs_fp64_and_mixed(adaptive_runs):
 def test_final_forces_match_oracle(adaptive_runs, which):
     w, r64, r32 = adaptive_runs
     s0, s1, x, f, lam = r64 if which == "fp64" else r32
-    ace = O.ACE(I.ace_for_config(2))
-    p = I.eam_params(0)
-    g = np.random.Generator(np.random.PCG64(I.seed_for(2, 9)))
-    L = w.box.hi - w.box.lo
-    inner = np.nonzero((x[:, 0] > 20) & (x[:, 0] < L[0] - 20) & (x[:, 1] > 20) & (x[:, 1] < L[1] - 20))[0]
-    pick = np.concatenate([g.choice(inner[lam[inner] < 1.0], 8, replace=False),
-                           g.choice(inner[lam[inner] == 1.0], 4, replace=False)])
-    worst = 0.0
-    for i in pick:
-        d = x - x[i]
-        sel = np.nonzero((d * d).sum(1) < 16.0 ** 2)[0]
-        xc = x[sel]
-        box = I.Box(lo=xc.min(0) - 20, hi=xc.max(0) + 20, periodic=np.array([False] * 3))
-        k0 = int(np.nonzero(sel == i)[0][0])
-        _, fo, _, _ = O.hybrid(xc, box, lam[sel], p, ace)
-        err = np.linalg.norm(f[i] - fo[k0])
-        if which == "fp64":
-            assert err <= 1e-5 * (np.linalg.norm(fo[k0]) + 0.01), (i, err)
-        worst = max(worst, err)
-    assert worst <= 1e-3, worst
+    _, fo, _, _ = O.hybrid(x, w.box, lam, I.eam_params(0), O.ACE(I.ace_for_config(2)))
+    err = np.linalg.norm(f - fo, axis=1)
+    print(f"c2 {which}: max |dF| {err.max() * 1e3:.3g} meV/A, rms {np.sqrt((err ** 2).mean()) * 1e3:.3g} meV/A, "
+          f"drift {((s1.e_pot + s1.e_kin) - (s0.e_pot + s0.e_kin)) / w.n:.3g} eV/atom, "
+          f"precise {s1.n_precise / w.n:.3f}")
+    if which == "fp64":
+        lim = 1e-5 * (np.linalg.norm(fo, axis=1) + 0.01)
+        assert np.all(err <= lim), (err / lim).max()
+    assert err.max() <= 1e-3, err.max()
+
+
+def test_drift_of_the_two_precisions_agrees(adaptive_runs):
+    w, r64, r32 = adaptive_runs
+    d = [((s1.e_pot + s1.e_kin) - (s0.e_pot + s0.e_kin)) / w.n for s0, s1, *_ in (r64, r32)]
+    assert all(np.isfinite(d))
+    assert abs(d[0] - d[1]) < 1e-5, d
