@@ -18,6 +18,7 @@ step on one GPU per system); value = atoms x steps over all ranks / max time.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -56,12 +57,13 @@ ACE_FLOP_PER_PAIR = ADJ_FLOP_PER_PAIR + BASIS_FLOP_PER_PAIR
 ACE_FLOP_PER_ATOM = ADJ_FLOP_PER_ATOM + BASIS_FLOP_PER_ATOM + 11400
 # DRAM bytes (read + write) per launch on this workload, from ncu captures of the
 # current kernels on the 500k-atom case (60,000 precise atoms), scaled to 4,000,000 atoms
-# and 240,000 precise atoms (profiles/k_ace_adjoint_slab50_mixed.md,
-# profiles/k_eam_force_slab50_mixed.md):
-#   k_ace_adjoint  185.6 MB read (mostly the basis kernel's pair records) + 0.7 MB written;
+# and 240,000 precise atoms (profiles/k_ace_basis_slab50_mixed.md,
+# profiles/k_ace_adjoint_slab50_mixed.md, profiles/k_eam_force_slab50_mixed.md):
+#   k_ace_basis    45.3 MB read + 122.9 MB written (the pair records, 16 B per pair);
+#   k_ace_adjoint  185.6 MB read (mostly the basis kernel's pair records) + 3.8 MB written;
 #   k_eam_force    146.1 MB read + 6.5 MB written.
-ADJ_TRAFFIC_BYTES = 186.3e6 * 240000 / 60000
-BASIS_TRAFFIC_BYTES = None      # k_ace_basis changed (tensor cores) since its last DRAM capture
+ADJ_TRAFFIC_BYTES = 189.4e6 * 240000 / 60000
+BASIS_TRAFFIC_BYTES = 168.2e6 * 240000 / 60000
 EAM_FORCE_TRAFFIC_BYTES = 152.6e6 * 4000000 / 500000
 # FP32 SIMT peak from unit counts: SMs (read from the device) x 128 FP32 lanes x 2 flop x the
 # maximum SM clock; reported for context beside the measured FFMA peak (ap_probe_peak), which
@@ -131,6 +133,17 @@ def kernel_rooflines(ctx, prof, n, hbm_gbs, hbm_src, peaks):
     return out
 
 
+def curve_at(points, kx, x, ky):
+    """ky at kx = x, interpolated linearly along the points ordered by precise fraction (the
+    first crossing); None when x lies outside the range the points cover."""
+    pts = sorted(points, key=lambda p: p["precise_fraction"])
+    for a, b in zip(pts, pts[1:]):
+        if (a[kx] - x) * (b[kx] - x) <= 0 and a[kx] != b[kx]:
+            t = (x - a[kx]) / (b[kx] - a[kx])
+            return a[ky] + t * (b[ky] - a[ky])
+    return None
+
+
 def dominant_kernel(rooflines):
     """The instrumented kernel with the most measured time in the timed region."""
     return max(rooflines, key=lambda k: rooflines[k]["ms_total"])
@@ -158,6 +171,8 @@ def parse():
     p.add_argument("--skin", type=float, default=1.0, help="neighbour-list skin (A); lists are rebuilt every "
                    "lambda update, so skin/2 bounds the displacement over 10 MD steps")
     p.add_argument("--thermostat", action="store_true", help="local thermostat (Appendix C) in the timed run")
+    p.add_argument("--deterministic", action="store_true",
+                   help="fixed-point ACE force reduction (bitwise reproducible) in the timed run")
     p.add_argument("--detector", default="csp", choices=["csp", "selector"],
                    help="detector behind lambda_0 in the timed run (centro-symmetry or the stored selector)")
     return p.parse_args()
@@ -334,10 +349,13 @@ def run_ours(args, ws, rank, local):
 
     sel = np.load(os.path.join(ROOT, "paper_2411_03002_gb300", "selector_cu.npz"))
 
-    def new_ctx(h, p=prec, detector=ap.DETECT_CSP, thermostat=False):
+    def new_ctx(h, p=prec, detector=ap.DETECT_CSP, thermostat=False, p_lo=None, p_hi=None, deterministic=False):
         c = ap.Context(ap.make_config(eam, acep, h, precision=p, indenter=w.indenter, lambda_every=MD_PER_STEP,
-                                      dt=w.dt, skin=args.skin, detector=detector, sel_p_lo=float(sel["p_lo"]),
-                                      sel_p_hi=float(sel["p_hi"]), thermostat=thermostat or args.thermostat))
+                                      dt=w.dt, skin=args.skin, detector=detector,
+                                      sel_p_lo=float(sel["p_lo"]) if p_lo is None else p_lo,
+                                      sel_p_hi=float(sel["p_hi"]) if p_hi is None else p_hi,
+                                      thermostat=thermostat or args.thermostat,
+                                      deterministic=deterministic or args.deterministic))
         if detector == ap.DETECT_SELECTOR:
             c.sel_set_model(sel["params"], sel["mu"], sel["inv_sigma"])
         return c
@@ -491,23 +509,46 @@ def run_ours(args, ws, rank, local):
         scored = mobile & (torch.as_tensor(w.x[:, 2], device=dev) > z_fixed + float(acep.rc))
         pos = (torch.linalg.vector_norm(fa_ - fe_, dim=1) > float(sel["tau"])) & scored
         dp = (fh_ - fa_)[pos]
-        # the same positions classified by the selector instead of CSP
-        es = new_ctx(hyb, detector=ap.DETECT_SELECTOR)
-        es.build_neighbors(xs, w.box)
-        lam_s, q_s, n_s = es.classify(xs, mobile.to(torch.uint8))
-        _, fs_ = es.eval_eam(xs, lam_s)
-        _, fs_ = es.eval_ace(xs, lam_s, q_s, n_s, f=fs_)
-        ds = (fs_ - fa_)[pos]
+        # the same positions classified by the selector instead of CSP, and both detectors over
+        # a set of switching zones: precise fraction against the force error on the atoms whose
+        # full-ACE and full-EAM forces differ by more than the selector's label threshold
+        def detector_point(detector, h, p_lo, p_hi):
+            es = new_ctx(h, detector=detector, p_lo=p_lo, p_hi=p_hi)
+            es.build_neighbors(xs, w.box)
+            lam_s, q_s, n_s = es.classify(xs, mobile.to(torch.uint8))
+            _, fs_ = es.eval_eam(xs, lam_s)
+            _, fs_ = es.eval_ace(xs, lam_s, q_s, n_s, f=fs_)
+            ds = (fs_ - fa_)[pos]
+            out = {"r_lo": h.r_lo, "r_hi": h.r_hi, "precise_fraction": float((lam_s < 1.0).float().mean().item()),
+                   "force_err_rms_meV_A_label_positive": float(torch.sqrt((ds * ds).mean()).item() * 1e3)}
+            es.close()
+            del es, fs_
+            return out
+        pareto = {"csp": [], "selector": []}
+        for r_lo, r_hi in ((8.0, 20.0), (6.0, 14.0), (5.0, 12.0), (4.0, 10.0), (4.0, 8.0), (3.0, 6.0)):
+            hz = dataclasses.replace(hyb, r_lo=r_lo, r_hi=r_hi)
+            pareto["csp"].append(detector_point(ap.DETECT_CSP, hz, 0.0, 0.0))
+            pareto["selector"].append(dict(detector_point(ap.DETECT_SELECTOR, hz, 0.9, 0.95), p_lo=0.9, p_hi=0.95))
+        deployed = detector_point(ap.DETECT_SELECTOR, hyb, float(sel["p_lo"]), float(sel["p_hi"]))
+        csp_ref = pareto["csp"][0]                       # the timed run's detector and zone
+        err_key = "force_err_rms_meV_A_label_positive"
         extras["selector"] = {
             "model": "paper_2411_03002_gb300/selector_cu.npz (p_lo %.2f, p_hi %.2f)" % (sel["p_lo"], sel["p_hi"]),
             "label_positive_fraction_of_scored": float((pos.sum() / scored.sum()).item()),
-            "precise_fraction": float((lam_s < 1.0).float().mean().item()),
-            "force_err_rms_meV_A_label_positive": float(torch.sqrt((ds * ds).mean()).item() * 1e3),
+            "precise_fraction": deployed["precise_fraction"],
+            "force_err_rms_meV_A_label_positive": deployed["force_err_rms_meV_A_label_positive"],
             "csp_force_err_rms_meV_A_label_positive": float(torch.sqrt((dp * dp).mean()).item() * 1e3),
             "csp_precise_fraction": float((lams < 1.0).float().mean().item()),
+            "matched": {"csp_hyb2": csp_ref,
+                        "selector_error_at_csp_cost": curve_at(pareto["selector"], "precise_fraction",
+                                                               csp_ref["precise_fraction"], err_key),
+                        "selector_cost_at_csp_error": curve_at(pareto["selector"], err_key, csp_ref[err_key],
+                                                               "precise_fraction"),
+                        "csp_error_at_deployed_selector_cost": curve_at(pareto["csp"], "precise_fraction",
+                                                                        deployed["precise_fraction"], err_key)},
+            "pareto": pareto,
         }
-        es.close()
-        del es, fs_, fa_, fe_, fh_, fh_m, fa_m, fe_m
+        del fa_, fe_, fh_, fh_m, fa_m, fe_m
         torch.cuda.empty_cache()
         # the comparison of the paper's nanoindentation run: adaptive (mixed, the timed run above;
         # FP64), full ACE and full EAM, plus the selector detector and the local thermostat, on the
@@ -521,6 +562,7 @@ def run_ours(args, ws, rank, local):
                            ("full_ace", lambda: new_ctx(hyb_for("full-ace", w.hyb))),
                            ("full_eam", lambda: new_ctx(hyb_for("full-eam", w.hyb))),
                            ("adaptive_selector", lambda: new_ctx(hyb, detector=ap.DETECT_SELECTOR)),
+                           ("adaptive_deterministic", lambda: new_ctx(hyb, deterministic=True)),
                            ("adaptive_thermostat", lambda: new_ctx(hyb, thermostat=True))):
             modes[name] = timed_mode(make, args.steps)
         extras["modes"] = modes
@@ -541,7 +583,8 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": f"nanoindentation-shaped FCC slab {args.ncell}^3 cells ({w.n} atoms), Hyb2 "
                                    f"(r_lambda 8/20 A), {args.mode}, {args.precision} precision"
                                    + (", selector detector" if args.detector == "selector" else "")
-                                   + (", local thermostat" if args.thermostat else ""),
+                                   + (", local thermostat" if args.thermostat else "")
+                                   + (", fixed-point ACE forces" if args.deterministic else ""),
                        "atoms": w.n, "md_steps_per_step": MD_PER_STEP, "lambda_every": MD_PER_STEP,
                        "precision": "FP32 potentials, FP64 integration and energy sums" if prec == ap.PREC_MIXED
                        else "FP64", "l2": "inputs larger than L2 (no flush)",

@@ -74,3 +74,13 @@ def test_tensor_pipe_use_of_the_basis_kernel():
     assert t["frac"] == pytest.approx(t["achieved"] / 303.0) and t["mma_tiles_per_launch"] == 3.0e7
     r0 = bench.kernel_rooflines(FakeCtx(1, 2), prof(12.0, 11.0, 10.0), 100, 6785.9, "test", PEAKS)
     assert "tensor" not in r0["k_ace_basis"]
+
+
+def test_curve_interpolation_at_equal_cost_and_error():
+    """The selector/CSP comparison reads one detector's curve at the other's precise fraction
+    (or error) by linear interpolation along the curve; outside its range there is no value."""
+    k = "force_err_rms_meV_A_label_positive"
+    pts = [{"precise_fraction": p, k: e} for p, e in ((0.04, 5.0), (0.06, 3.0), (0.08, 1.0))]
+    assert bench.curve_at(pts, "precise_fraction", 0.05, k) == pytest.approx(4.0)
+    assert bench.curve_at(pts, k, 2.0, "precise_fraction") == pytest.approx(0.07)
+    assert bench.curve_at(pts, "precise_fraction", 0.10, k) is None
