@@ -555,9 +555,7 @@ def run_ours(args, ws, rank, local):
         # same GPU and workload, each timed over the same number of bench steps
         modes = {"adaptive_mixed": {"atom_steps_s": value / ws, "ms_per_step": ms / args.steps,
                                     "steps": args.steps, "precise_fraction": stats.n_precise / w.n,
-                                    "drift_eV_per_atom": drift,
-            "memory": {"device_gb": footprint_gb, "what": "device memory taken by the context and the run's x, v, f, "
-                                                        "mass, fixed, lambda after warm-up (cudaMemGetInfo)"}, "clocks": ck}}
+                                    "drift_eV_per_atom": drift, "clocks": ck}}
         for name, make in (("adaptive_fp64", lambda: new_ctx(hyb, p=ap.PREC_FP64)),
                            ("full_ace", lambda: new_ctx(hyb_for("full-ace", w.hyb))),
                            ("full_eam", lambda: new_ctx(hyb_for("full-eam", w.hyb))),
@@ -590,6 +588,8 @@ def run_ours(args, ws, rank, local):
                        else "FP64", "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "precise_fraction": stats.n_precise / w.n, "n_precise": stats.n_precise, "n_detected": stats.n_detected,
+            "memory": {"device_gb": footprint_gb, "what": "device memory taken by the context and the run's x, v, f, "
+                                                        "mass, fixed, lambda after warm-up (cudaMemGetInfo)"},
             "drift_eV_per_atom": drift,
             "e2e": {"value": atom_steps / (ms_e2e / 1e3), "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

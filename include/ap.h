@@ -158,6 +158,14 @@ typedef struct {
    * selector detector and ap_eval_eam_static accept AP_EAM_ANALYTIC only. */
   int32_t eam_type;
   double eam_mishin[29];
+  /* ACE force reduction.  0: each neighbour pair's contribution is scattered with
+   * floating-point atomics (FP32 vector atomics in mixed precision), so the summation
+   * order, and with it the last bits of the forces, varies from run to run.  1: each
+   * contribution is rounded to a multiple of 2^-36 eV/A (an error of at most 2^-37 per
+   * contribution) and summed with 64-bit integer atomics, which are exact and
+   * independent of the order: forces, and ap_step trajectories, are bitwise
+   * reproducible on one GPU model.  Accumulated forces must stay below 2^27 eV/A. */
+  int32_t ace_deterministic;
 } ap_config;
 
 typedef struct ap_ctx ap_ctx;

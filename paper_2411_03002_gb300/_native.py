@@ -38,7 +38,7 @@ class ApConfig(ctypes.Structure):
                    ("ind_c0", F64 * 3), ("ind_v", F64 * 3), ("ind_R", F64), ("ind_k", F64),
                    ("rebuild_every", I32), ("detector", I32), ("sel_p_lo", F64), ("sel_p_hi", F64),
                    ("thermostat_on", I32), ("ace_fs_on", I32), ("ace_fs_eps", F64), ("ace_c2", F64 * 512),
-                   ("eam_type", I32), ("eam_mishin", F64 * 29)])
+                   ("eam_type", I32), ("eam_mishin", F64 * 29), ("ace_deterministic", I32)])
 
 
 class ApStepStats(ctypes.Structure):

@@ -42,7 +42,7 @@ def make_box(lo, hi, periodic) -> ApBox:
 def make_config(eam, ace, hyb, precision: int = N.PREC_MIXED, skin: float = 1.0, dt: float = 1.0,
                 indenter=None, cap_eam: int = 0, cap_ace: int = 0, lambda_every: Optional[int] = None,
                 rebuild_every: int = 0, detector: int = N.DETECT_CSP, sel_p_lo: float = 0.5,
-                sel_p_hi: float = 0.9, thermostat: bool = False) -> ApConfig:
+                sel_p_hi: float = 0.9, thermostat: bool = False, deterministic: bool = False) -> ApConfig:
     """Fill an ap_config from parameter objects with the attribute names of
     the EAM (beta, alpha, A, D, rp, r0, rc, h), ACE (W, c, rc, n0) and switching
     (csp_lo, csp_hi, r_lo, r_hi, dlam_min, n_csp_avg, n_lam_avg, fcut_mode,
@@ -100,6 +100,7 @@ def make_config(eam, ace, hyb, precision: int = N.PREC_MIXED, skin: float = 1.0,
             c.ind_v[k] = float(indenter.velocity[k])
         c.ind_R = float(indenter.radius)
         c.ind_k = float(indenter.k)
+    c.ace_deterministic = 1 if deterministic else 0
     return c
 
 

@@ -212,6 +212,7 @@ struct ap_ctx {
   double* d_xi = nullptr;        // [n] xi(rho)
   float4* d_facc32 = nullptr;    // [n] ACE force accumulator (mixed)
   double* d_facc64 = nullptr;    // [n][3] ACE force accumulator (FP64)
+  unsigned long long* d_faccfix = nullptr;   // [n][3] fixed-point ACE force accumulator (ace_deterministic)
   double* d_efast = nullptr;     // [n] internal (ap_step)
   double* d_eprec = nullptr;     // [n] internal (ap_step)
   double* d_eatom = nullptr;     // [n] internal (ap_step)
