@@ -225,8 +225,19 @@ __device__ inline void pair_disp(const SysInfo& S, const typename V<R>::S4& si, 
   }
 }
 
+// Fixed-point force accumulation (ace_deterministic): contributions rounded to multiples
+// of 2^-36 eV/A, summed with exact, order-independent 64-bit integer atomics.
+constexpr double kFixScale = 68719476736.0;   // 2^36
+__device__ inline unsigned long long to_fix(double v) { return (unsigned long long)llrint(v * kFixScale); }
+
 template <typename R>
-__device__ inline void add_force(float4* facc32, double* facc64, int j, R sx, R sy, R sz) {
+__device__ inline void add_force(float4* facc32, double* facc64, unsigned long long* fix, int j, R sx, R sy, R sz) {
+  if (fix) {
+    atomicAdd(&fix[3 * j + 0], to_fix((double)sx));
+    atomicAdd(&fix[3 * j + 1], to_fix((double)sy));
+    atomicAdd(&fix[3 * j + 2], to_fix((double)sz));
+    return;
+  }
   if constexpr (sizeof(R) == 4) {
     atomicAdd(&facc32[j], make_float4(sx, sy, sz, 0.f));
   } else {
@@ -406,6 +417,7 @@ struct AceArgs {
   double* e_prec;
   float4* facc32;
   double* facc64;
+  unsigned long long* faccfix;   // fixed-point accumulator [n][3], or NULL (float atomics)
   typename V<R>::R4* list4;   // [q][rec] in-range (d, j) records in row order (kernel 1 -> 3)
   int rec;                    // record slots per queue position (>= every ACE row's length)
   int* nin;          // [q] their number
@@ -474,16 +486,23 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
     const int c = a.cnt[q];
     const size_t row = (size_t)q * a.cap;
 
-    // ---------------- pass 0: compact the row entries inside ace_rc
+    // ---------------- pass 0: compact the row entries inside ace_rc.  The dependent loads
+    // (row entry, then its shadow) run ahead of their use: the entry two batches ahead,
+    // the shadow one batch ahead.
     int nin = 0;
+    int j_a = lane < c ? a.nbr[row + lane] : 0;
+    auto s_a = lane < c ? a.sh[j_a] : si;
+    int j_b = lane + 32 < c ? a.nbr[row + lane + 32] : 0;
     for (int base = 0; base < c; base += 32) {
       const int slot = base + lane;
+      const int j = j_a;
+      const auto sj = s_a;
+      j_a = j_b;
+      if (slot + 32 < c) s_a = a.sh[j_a];
+      j_b = slot + 64 < c ? a.nbr[row + slot + 64] : 0;
       bool in = false;
       R d[3] = {R(0), R(0), R(0)};
-      int j = 0;
       if (slot < c) {
-        j = a.nbr[row + slot];
-        auto sj = a.sh[j];
         pair_disp<R>(S, si, sj, a.off, row + slot, d);
         in = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < a.rc2;
       }
@@ -858,12 +877,12 @@ __global__ void __launch_bounds__(kWarps3<R> * 32, sizeof(R) == 4 ? AP_ACE3_MINB
       pix += px;
       piy += py;
       piz += pz;
-      add_force<R>(a.facc32, a.facc64, j, -wgt * px, -wgt * py, -wgt * pz);
+      add_force<R>(a.facc32, a.facc64, a.faccfix, j, -wgt * px, -wgt * py, -wgt * pz);
     }
     pix = warp_sum<R>(pix);
     piy = warp_sum<R>(piy);
     piz = warp_sum<R>(piz);
-    if (lane == 0) add_force<R>(a.facc32, a.facc64, i, wgt * pix, wgt * piy, wgt * piz);
+    if (lane == 0) add_force<R>(a.facc32, a.facc64, a.faccfix, i, wgt * pix, wgt * piy, wgt * piz);
     __syncwarp();
   }
 }
@@ -876,6 +895,13 @@ __global__ void k_ace_finalize32(int n, const float4* __restrict__ acc, double* 
   f[3 * i + 0] += (double)v.x;
   f[3 * i + 1] += (double)v.y;
   f[3 * i + 2] += (double)v.z;
+}
+
+__global__ void k_ace_finalize_fix(int n, const unsigned long long* __restrict__ acc, double* __restrict__ f) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * n) return;
+  const long long v = (long long)acc[i];
+  if (v != 0) f[i] += (double)v * (1.0 / kFixScale);
 }
 
 __global__ void k_ace_finalize64(int n, const double* __restrict__ acc, double* __restrict__ f) {
@@ -930,6 +956,7 @@ void run_ace(ap_ctx* c, const double* d_lam, const double* d_wgt, const int* d_q
   a.cap = c->cap_ace;
   a.lam = d_lam;
   a.wgt = d_wgt;
+  a.faccfix = c->cfg.ace_deterministic ? c->d_faccfix : nullptr;
   a.M2 = a.W + 320;   // the parameter block is [W (320) | M2 (320) | C1 (8) | M2b (320) | C1b (8)]
   a.C1 = a.W + 640;
   a.M2b = a.W + 648;
@@ -967,7 +994,9 @@ void run_ace(ap_ctx* c, const double* d_lam, const double* d_wgt, const int* d_q
                    : (fs ? k_ace_adjoint<R, false, true> : k_ace_adjoint<R, false, false>);
   if (!b3[pi][forces][fs]) b3[pi][forces][fs] = resident_blocks(k3, kWarps3<R> * 32, s3);
   if (forces) {
-    if constexpr (sizeof(R) == 4)
+    if (a.faccfix)
+      cudaMemsetAsync(c->d_faccfix, 0, sizeof(unsigned long long) * 3 * (size_t)c->n, s);
+    else if constexpr (sizeof(R) == 4)
       cudaMemsetAsync(c->d_facc32, 0, sizeof(float4) * (size_t)c->n, s);
     else
       cudaMemsetAsync(c->d_facc64, 0, sizeof(double) * 3 * (size_t)c->n, s);
@@ -1021,7 +1050,9 @@ void launch_ace(ap_ctx* c, const double* d_lam, const int* d_queue, double* d_e_
 
 void launch_ace_finalize(ap_ctx* c, double* d_f, cudaStream_t s) {
   c->kernels += 1;
-  if (c->cfg.precision == AP_PREC_FP64)
+  if (c->cfg.ace_deterministic)
+    k_ace_finalize_fix<<<(int)((3 * c->n + 255) / 256), 256, 0, s>>>((int)c->n, c->d_faccfix, d_f);
+  else if (c->cfg.precision == AP_PREC_FP64)
     k_ace_finalize64<<<(int)((3 * c->n + 255) / 256), 256, 0, s>>>((int)c->n, c->d_facc64, d_f);
   else
     k_ace_finalize32<<<(int)((c->n + 255) / 256), 256, 0, s>>>((int)c->n, c->d_facc32, d_f);
