@@ -66,6 +66,7 @@ SIGNATURES = [
     ("ap_build_neighbors_batch", I32, [P, I32, P, P, P, P, P]),
     ("ap_get_neighbors", I32, [P, I32, P, P, P, I64, P]),
     ("ap_neighbor_total", I32, [P, I32, P]),
+    ("ap_spatial_order", I32, [P, P, P]),
     ("ap_classify", I32, [P, I64, P, P, I32, P, P, P, P]),
     ("ap_reset_lambda", I32, [P]),
     ("ap_precise_queue", I32, [P, I64, P, P, P, P]),

@@ -210,6 +210,13 @@ class Context:
         self._ck(self.lib.ap_neighbor_total(self.h, which, ctypes.byref(t)))
         return t.value
 
+    def spatial_order(self, stream=None) -> torch.Tensor:
+        """The atoms in the cell order of the last build (int32 [n]): x[order], v[order], ...
+        put neighbours close in memory (ap_spatial_order)."""
+        order = torch.empty(max(self.n, 1), dtype=torch.int32, device="cuda")
+        self._ck(self.lib.ap_spatial_order(self.h, _ptr(order), _stream(stream)))
+        return order[:self.n]
+
     def get_neighbors(self, which: int = 0, cap: int = 320):
         """(cnt [rows], idx [rows, cap], shift [rows, cap, 3]) as CUDA int32 tensors."""
         rows = ctypes.c_int64()

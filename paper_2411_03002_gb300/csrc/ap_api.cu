@@ -699,6 +699,15 @@ ap_status ap_get_neighbors(ap_ctx* c, int32_t which, int32_t* d_cnt, int32_t* d_
   return AP_OK;
 }
 
+ap_status ap_spatial_order(ap_ctx* c, int32_t* d_order, void* stream) {
+  if (!c) return AP_ERR_ARG;
+  if (!c->built) return fail(c, AP_ERR_STATE, "no neighbour build yet");
+  if (!d_order) return fail(c, AP_ERR_ARG, "null order");
+  if (c->n > 0)
+    CK(cudaMemcpyAsync(d_order, c->d_cell_atoms, sizeof(int) * (size_t)c->n, cudaMemcpyDeviceToDevice, S(stream)));
+  return AP_OK;
+}
+
 ap_status ap_neighbor_total(ap_ctx* c, int32_t which, int64_t* h_total) {
   if (!c) return AP_ERR_ARG;
   if (!h_total) return fail(c, AP_ERR_ARG, "null argument");
