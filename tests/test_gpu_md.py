@@ -50,8 +50,24 @@ def test_full_ace_nve_is_stable_fp64():
     s0, s1, x, f, lam = run(w, hyb, ap.PREC_FP64, 200, lambda_every=10 ** 6)
     assert np.all(lam == 0.0)
     drift = abs((s1.e_pot + s1.e_kin) - (s0.e_pot + s0.e_kin)) / w.n
+    print(f"full-ACE NVE drift {drift:.3g} eV/atom over 200 steps")
     assert np.isfinite(s1.e_pot) and drift < 1e-4, drift
     assert s1.max_disp < 0.5
+
+
+def test_full_ace_nve_thermal_slab_drift_below_1e5_fp64():
+    """The same slab without the disordered hemisphere (FCC at its lattice sites, the 300 K
+    velocities of the workload): full ACE at fixed lambda in FP64 conserves the energy to
+    the integrator's pin, |E(200 fs) - E(0)|/N < 1e-5 eV/atom.  (With the hemisphere, whose
+    0.3 A disorder melts in the first ~50 fs, the test above allows 1e-4.)"""
+    w0 = I.config_c2()
+    w = dataclasses.replace(w0, x=I.fcc_lattice(20, 20, 20))
+    hyb = dataclasses.replace(w.hyb, csp_lo=-2.0, csp_hi=-1.0)
+    s0, s1, x, f, lam = run(w, hyb, ap.PREC_FP64, 200, lambda_every=10 ** 6, rebuild_every=10)
+    assert np.all(lam == 0.0)
+    drift = abs((s1.e_pot + s1.e_kin) - (s0.e_pot + s0.e_kin)) / w.n
+    print(f"full-ACE NVE thermal slab drift {drift:.3g} eV/atom over 200 steps")
+    assert drift < 1e-5, drift
 
 
 @pytest.fixture(scope="module")
