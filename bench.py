@@ -168,8 +168,11 @@ def parse():
     p.add_argument("--mode", default="adaptive", choices=["adaptive", "full-ace", "full-eam"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-extras", action="store_true", help="skip full-ACE/full-EAM, error and CPU baseline legs")
-    p.add_argument("--skin", type=float, default=1.0, help="neighbour-list skin (A); lists are rebuilt every "
-                   "lambda update, so skin/2 bounds the displacement over 10 MD steps")
+    p.add_argument("--skin", type=float, default=1.0, help="neighbour-list skin (A)")
+    p.add_argument("--rebuild", default="skin", choices=["lambda", "skin"],
+                   help="list rebuilds in the timed run: at every lambda update, or on the skin criterion "
+                        "(checked after every drift; a lambda update keeps the lists while no atom has moved "
+                        "more than skin/4)")
     p.add_argument("--thermostat", action="store_true", help="local thermostat (Appendix C) in the timed run")
     p.add_argument("--deterministic", action="store_true",
                    help="fixed-point ACE force reduction (bitwise reproducible) in the timed run")
@@ -349,9 +352,12 @@ def run_ours(args, ws, rank, local):
 
     sel = np.load(os.path.join(ROOT, "paper_2411_03002_gb300", "selector_cu.npz"))
 
-    def new_ctx(h, p=prec, detector=ap.DETECT_CSP, thermostat=False, p_lo=None, p_hi=None, deterministic=False):
+    def new_ctx(h, p=prec, detector=ap.DETECT_CSP, thermostat=False, p_lo=None, p_hi=None, deterministic=False,
+                rebuild=None):
+        rebuild = args.rebuild if rebuild is None else rebuild
         c = ap.Context(ap.make_config(eam, acep, h, precision=p, indenter=w.indenter, lambda_every=MD_PER_STEP,
                                       dt=w.dt, skin=args.skin, detector=detector,
+                                      rebuild_every=ap.REBUILD_SKIN if rebuild == "skin" else 0,
                                       sel_p_lo=float(sel["p_lo"]) if p_lo is None else p_lo,
                                       sel_p_hi=float(sel["p_hi"]) if p_hi is None else p_hi,
                                       thermostat=thermostat or args.thermostat,
@@ -450,7 +456,8 @@ def run_ours(args, ws, rank, local):
         clk = ck2.stop()
         t = a.elapsed_time(b)
         out = {"atom_steps_s": w.n * MD_PER_STEP * steps / (t / 1e3), "ms_per_step": t / steps, "steps": steps,
-               "precise_fraction": s1.n_precise / w.n,
+               "precise_fraction": s1.n_precise / w.n, "rebuilds": s1.rebuilds - s0.rebuilds,
+               "kept_updates": s1.kept - s0.kept,
                "drift_eV_per_atom": (s1.e_pot + s1.e_kin - s0.e_pot - s0.e_kin) / w.n, "clocks": clk}
         if s1.th_corrected or s1.th_refused:
             out["thermostat"] = {"corrections": s1.th_corrected, "refused": s1.th_refused,
@@ -555,12 +562,16 @@ def run_ours(args, ws, rank, local):
         # same GPU and workload, each timed over the same number of bench steps
         modes = {"adaptive_mixed": {"atom_steps_s": value / ws, "ms_per_step": ms / args.steps,
                                     "steps": args.steps, "precise_fraction": stats.n_precise / w.n,
+                                    "rebuilds": stats.rebuilds - stats_start.rebuilds,
+                                    "kept_updates": stats.kept - stats_start.kept,
                                     "drift_eV_per_atom": drift, "clocks": ck}}
+        other_rebuild = "lambda" if args.rebuild == "skin" else "skin"
         for name, make in (("adaptive_fp64", lambda: new_ctx(hyb, p=ap.PREC_FP64)),
                            ("full_ace", lambda: new_ctx(hyb_for("full-ace", w.hyb))),
                            ("full_eam", lambda: new_ctx(hyb_for("full-eam", w.hyb))),
                            ("adaptive_selector", lambda: new_ctx(hyb, detector=ap.DETECT_SELECTOR)),
                            ("adaptive_deterministic", lambda: new_ctx(hyb, deterministic=True)),
+                           ("adaptive_rebuild_" + other_rebuild, lambda: new_ctx(hyb, rebuild=other_rebuild)),
                            ("adaptive_thermostat", lambda: new_ctx(hyb, thermostat=True))):
             modes[name] = timed_mode(make, args.steps)
         extras["modes"] = modes
@@ -582,7 +593,8 @@ def run_ours(args, ws, rank, local):
                                    f"(r_lambda 8/20 A), {args.mode}, {args.precision} precision"
                                    + (", selector detector" if args.detector == "selector" else "")
                                    + (", local thermostat" if args.thermostat else "")
-                                   + (", fixed-point ACE forces" if args.deterministic else ""),
+                                   + (", fixed-point ACE forces" if args.deterministic else "")
+                                   + (", lists rebuilt on the skin criterion" if args.rebuild == "skin" else ""),
                        "atoms": w.n, "md_steps_per_step": MD_PER_STEP, "lambda_every": MD_PER_STEP,
                        "precision": "FP32 potentials, FP64 integration and energy sums" if prec == ap.PREC_MIXED
                        else "FP64", "l2": "inputs larger than L2 (no flush)",
@@ -591,6 +603,8 @@ def run_ours(args, ws, rank, local):
             "memory": {"device_gb": footprint_gb, "what": "device memory taken by the context and the run's x, v, f, "
                                                         "mass, fixed, lambda after warm-up (cudaMemGetInfo)"},
             "drift_eV_per_atom": drift,
+            "lists": {"rebuild": args.rebuild, "rebuilds": stats.rebuilds - stats_start.rebuilds,
+                      "kept_updates": stats.kept - stats_start.kept, "lambda_updates": args.steps},
             "e2e": {"value": atom_steps / (ms_e2e / 1e3), "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": prof["kernels"],

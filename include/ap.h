@@ -62,6 +62,8 @@ typedef int32_t ap_status;
 #define AP_EAM_ANALYTIC 0   /* eam_type: the analytic synthetic EAM (eam_beta .. eam_h)     */
 #define AP_EAM_MISHIN 1     /* eam_type: Mishin EAM2 copper (Appendix E), eam_mishin[]      */
 
+#define AP_REBUILD_SKIN (-1) /* rebuild_every: rebuild on the skin criterion (see ap_config) */
+
 #define AP_FCUT_PRINTED 0   /* f_cut(x) = 1 - 1.875x + 1.25x^3 - 0.375x^5 as printed    */
 #define AP_FCUT_C2 1        /* C2-symmetric reading 0.5*p(2x-1)                         */
 
@@ -110,7 +112,20 @@ typedef struct {
   int32_t indenter_on;       /* 1: spherical indenter F = k (R - r)^2 (x - c)/r, r < R */
   double ind_c0[3], ind_v[3], ind_R, ind_k;   /* centre at t=0 (A), velocity (A/fs), R (A), k (eV/A^3) */
   int32_t rebuild_every;     /* neighbour rebuild period (steps); 0 = lambda_every.  Every
-                                lambda update also rebuilds, so the CSP sees fresh rows. */
+                                lambda update also rebuilds, so the CSP sees fresh rows.
+                                AP_REBUILD_SKIN: ap_step reads the largest displacement
+                                since the last build after every drift (a stream sync
+                                per step) and rebuilds when it exceeds skin/2; a lambda
+                                update keeps the lists while it is at most skin/4 and
+                                takes the CSP from them where they decide it (12
+                                candidates inside r_search - 2 x that displacement; any
+                                atom that fails this makes the update rebuild after
+                                all).  Lambda and the forces equal those of a rebuild
+                                at the update.  Lists are kept only with
+                                AP_DETECT_CSP, without the local thermostat, and when
+                                every periodic dimension of every system holds >= 7
+                                cells or the offsets are stored; otherwise each update
+                                rebuilds (the per-step check stays). */
   /* Detector behind lambda_0 (Appendix B allows any detector whose f_cut argument
    * is 0 for precise and 1 for fast atoms).  AP_DETECT_SELECTOR pushes the
    * selector's p_i in [0,1] into the history in place of CSP_i and uses
@@ -183,6 +198,7 @@ typedef struct {
   int64_t th_corrected;      /* local-thermostat corrections applied so far */
   int64_t th_refused;        /* corrections refused for a negative radicand so far */
   double th_energy;          /* sum of the corrected Delta E so far (eV) */
+  int64_t kept;              /* lambda updates that kept the lists (AP_REBUILD_SKIN) so far */
 } ap_step_stats;
 
 /* ----------------------------------------------------------------- lifetime */
@@ -339,9 +355,10 @@ ap_status ap_blend_forces(ap_ctx* ctx, int64_t n, const double* d_lam, const dou
  * d_lam [n] FP64 out.  h_stats (may be NULL) is filled at the end.  The call
  * synchronises the stream at its end and at every rebuild: there it checks the
  * error bits so far (an error ends the call), grows the EAM rows if one overflowed,
- * and reads the new precise queue's length to size the ACE storage for it.
+ * and reads the new precise queue's length to size the ACE storage for it.  With
+ * rebuild_every = AP_REBUILD_SKIN it also synchronises after every drift.
  * Errors: as above plus AP_ERR_SKIN (an atom moved more than skin/2 before a
- * rebuild) and AP_ERR_NONFINITE. */
+ * rebuild; never with AP_REBUILD_SKIN) and AP_ERR_NONFINITE. */
 ap_status ap_step(ap_ctx* ctx, int64_t n, double* d_x, double* d_v, double* d_f, const double* d_mass,
                   const uint8_t* d_fixed, double* d_lam, int64_t nsteps, ap_step_stats* h_stats, void* stream);
 

@@ -17,6 +17,7 @@ ERRORS = {1: "AP_ERR_ARG", 2: "AP_ERR_CUDA", 3: "AP_ERR_CAPACITY", 4: "AP_ERR_NO
 PREC_FP64 = 0
 PREC_MIXED = 1
 DETECT_CSP = 0
+REBUILD_SKIN = -1
 DETECT_SELECTOR = 1
 EAM_ANALYTIC = 0
 EAM_MISHIN = 1
@@ -44,7 +45,7 @@ class ApConfig(ctypes.Structure):
 class ApStepStats(ctypes.Structure):
     _fields_ = [("step", I64), ("n_precise", I64), ("n_detected", I64), ("rebuilds", I64), ("e_pot", F64),
                 ("e_kin", F64), ("max_disp", F64), ("error_bits", I32), ("th_corrected", I64), ("th_refused", I64),
-                ("th_energy", F64)]
+                ("th_energy", F64), ("kept", I64)]
 
 
 class ApError(RuntimeError):

@@ -62,7 +62,7 @@ ap_status validate(const ap_config& g, std::string& why) {
   if (g.ace_nc < 0 || g.ace_nc > 512) return bad("ace_nc out of range");
   if (g.cap_eam < 0 || g.cap_ace < 0 || g.cap_eam > 4096 || g.cap_ace > 4096) return bad("row capacity out of range");
   if (g.lambda_every < 1) return bad("lambda_every must be >= 1");
-  if (g.rebuild_every < 0) return bad("rebuild_every must be >= 0");
+  if (g.rebuild_every < AP_REBUILD_SKIN) return bad("rebuild_every must be >= 0 or AP_REBUILD_SKIN");
   if (g.detector != AP_DETECT_CSP && g.detector != AP_DETECT_SELECTOR) return bad("unknown detector");
   if (g.detector == AP_DETECT_SELECTOR && !(g.sel_p_lo >= 0 && g.sel_p_hi > g.sel_p_lo))
     return bad("need 0 <= sel_p_lo < sel_p_hi");
@@ -81,7 +81,12 @@ ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box
   std::vector<SysInfo> sys(n_sys);
   int base = 0;
   bool stored = false;
-  int spread[3] = {0, 0, 0};
+  int spread[3] = {0, 0, 0}, spread_stale[3] = {0, 0, 0};
+  // Lists kept past a lambda update (skin criterion) take ACE rows from cells up to skin/4
+  // old and reaching ace_rc + skin + skin/2: pair cell offsets up to
+  // ceil((ace_rc + 2 skin)/h).  Without stored offsets they are recovered from the wrapped
+  // cells, which needs 2 offset + 1 cells in every periodic dimension.
+  bool wide = true;
   for (int s = 0; s < n_sys; ++s) {
     SysInfo& I = sys[s];
     std::memset(&I, 0, sizeof(I));
@@ -101,6 +106,11 @@ ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box
       int sp = (int)std::ceil(g.r_hi / I.h[d]);
       if (!I.periodic[d]) sp = std::min(sp, nc);
       spread[d] = std::max(spread[d], sp);
+      int sps = (int)std::ceil((g.r_hi + g.skin) / I.h[d]);   // atoms up to skin/2 from their cells
+      if (!I.periodic[d]) sps = std::min(sps, nc);
+      spread_stale[d] = std::max(spread_stale[d], sps);
+      const int reach = (int)std::ceil((g.ace_rc + 2.0 * g.skin) / I.h[d]);
+      if (I.periodic[d] && nc < 2 * reach + 1) wide = false;
     }
     I.cell_base = base;
     base += I.nc[0] * I.nc[1] * I.nc[2];
@@ -114,7 +124,11 @@ ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box
   c->n_sys = n_sys;
   c->n_cells = base;
   c->stored_off = stored;
-  for (int d = 0; d < 3; ++d) c->sten_spread[d] = spread[d];
+  for (int d = 0; d < 3; ++d) {
+    c->sten_spread[d] = spread[d];
+    c->sten_spread_stale[d] = spread_stale[d];
+  }
+  c->stale_ok = stored || wide;
   CK(dalloc(c->d_sys, n_sys));
   CK(cudaMemcpy(c->d_sys, sys.data(), sizeof(SysInfo) * n_sys, cudaMemcpyHostToDevice));
   dfree(c->d_atom_sys);
@@ -216,6 +230,7 @@ ap_status ensure_capacity(ap_ctx* c, int64_t n) {
   CK(dalloc(c->d_vscale, m));
   CK(dalloc(c->d_cnt_eam, m));
   CK(dalloc(c->d_lim_eam, m));
+  if (c->cfg.rebuild_every == AP_REBUILD_SKIN) CK(dalloc(c->d_split_eam, m));
   ap_status st = alloc_rows(c, true, true);
   if (st) return st;
   CK(dalloc(c->d_csp, m));
@@ -290,7 +305,11 @@ void build_async(ap_ctx* c, const double* d_x, const int32_t* d_species, cudaStr
   launch_cell_sort(c, s);
   launch_shadow(c, d_x, s);
   launch_build_eam(c, d_x, s);
+  if (c->d_split_eam)   // the split of the rows, for a CSP on them after the atoms have moved
+    cudaMemcpyAsync(c->d_split_eam, c->d_lim_eam, sizeof(int) * (size_t)c->n, cudaMemcpyDeviceToDevice, s);
   c->lim_valid = false;
+  c->cells_stale = false;
+  c->stale_m = 0.0;
   cudaMemcpyAsync(c->d_xbuild, d_x, sizeof(double) * 3 * (size_t)c->n, cudaMemcpyDeviceToDevice, s);
   cudaMemsetAsync(&c->d_sc->max_disp2_bits, 0, sizeof(unsigned int), s);
   c->rebuilds++;
@@ -537,10 +556,11 @@ ap_status prep_detector(ap_ctx* c) {
   return ensure_sel_feat(c, c->n);
 }
 
-// fresh_rows: the EAM rows were built at d_x in this call (ap_step).
+// fresh_rows: the EAM rows were built at d_x in this call (ap_step); csp_done: d_csp
+// already holds the CSP at d_x.
 void classify_async(ap_ctx* c, const double* d_x, const uint8_t* d_ch, double* d_lam, int* d_queue,
-                    int64_t* d_nq64, cudaStream_t s, bool fresh_rows = false) {
-  launch_csp(c, d_x, d_ch, s, fresh_rows);
+                    int64_t* d_nq64, cudaStream_t s, bool fresh_rows = false, bool csp_done = false) {
+  if (!csp_done) launch_csp(c, d_x, d_ch, s, fresh_rows);
   if (c->cfg.detector == AP_DETECT_SELECTOR) {
     launch_sel_features(c, c->d_sel_feat, s);
     launch_sel_mlp(c, c->n, c->d_sel_feat, nullptr, nullptr, c->d_sel_score, nullptr, nullptr, nullptr, s);
@@ -600,7 +620,7 @@ void ap_destroy(ap_ctx* c) {
   cudaDeviceSynchronize();
   void* ptrs[] = {c->d_sys, c->d_atom_sys, c->d_cell, c->d_cunw, c->d_cell_start, c->d_cell_count, c->d_cell_atoms,
                   c->d_slot, c->d_sh32, c->d_sh32c, c->d_sh64, c->d_xbuild, c->d_vscale, c->d_nbr_eam, c->d_off_eam, c->d_cnt_eam,
-                  c->d_lim_eam, c->d_nbr_ace, c->d_off_ace, c->d_cnt_ace, c->d_csp, c->d_csp_slow, c->d_csp_avg, c->d_lam0, c->d_lam_min,
+                  c->d_lim_eam, c->d_split_eam, c->d_nbr_ace, c->d_off_ace, c->d_cnt_ace, c->d_csp, c->d_csp_slow, c->d_csp_avg, c->d_lam0, c->d_lam_min,
                   c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected,
                   c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_faccfix, c->d_efast, c->d_eprec,
                   c->d_eatom, c->d_eext, c->d_changeable, c->d_W32, c->d_W64, c->d_ace_list, c->d_ace_nin,
@@ -897,6 +917,10 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
   st = clear_err(c, s);
   if (st) return st;
   const float skin_lim2 = (float)(0.25 * g.skin * g.skin);
+  // Skin criterion: the lists are checked after every drift; a lambda update keeps them
+  // (stale cells and rows) where the detector and the box allow it.
+  const bool skin_rule = g.rebuild_every == AP_REBUILD_SKIN;
+  const bool keep_ok = skin_rule && c->stale_ok && g.detector == AP_DETECT_CSP && !thermo;
   if (nsteps > 0) {
     PhaseTimer t(c, s, AP_PHASE_OTHER);
     launch_vscale(c, d_mass, s);   // the half-kick factors of this call's masses
@@ -908,27 +932,67 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
       launch_vv_first(c, d_x, d_v, d_f, d_mass, d_fixed, s);
     }
     const bool lam_step = c->step % g.lambda_every == 0;
-    const int rb = g.rebuild_every > 0 ? g.rebuild_every : g.lambda_every;
-    if (lam_step || c->step % rb == 0) {
-      {
+    bool build = false, keep = false;
+    double m = 0.0;   // the largest displacement since the last build (skin criterion)
+    if (skin_rule) {
+      PhaseTimer t(c, s, AP_PHASE_NEIGHBORS);
+      st = read_scalars(c, s);   // an error so far (non-finite position) ends the call here
+      if (st) return st;
+      st = check_err_bits(c);
+      if (st) return st;
+      float d2;
+      std::memcpy(&d2, &c->h_sc->max_disp2_bits, sizeof(float));
+      // FP32 squared sum of FP64 differences: a few ulp of headroom
+      m = std::sqrt((double)d2) * (1.0 + 1e-5) + 1e-6;
+      build = m > 0.5 * g.skin;
+      keep = lam_step && !build && keep_ok && m <= 0.25 * g.skin;
+      build = build || (lam_step && !keep);
+    } else {
+      const int rb = g.rebuild_every > 0 ? g.rebuild_every : g.lambda_every;
+      build = lam_step || c->step % rb == 0;
+    }
+    if (build || lam_step) {
+      if (build) {
         PhaseTimer t(c, s, AP_PHASE_NEIGHBORS);
-        k_check_skin<<<1, 1, 0, s>>>(c->d_sc, skin_lim2);
-        c->kernels += 1;
-        // an error so far (skin, non-finite position) ends the call here
-        st = read_scalars(c, s);
-        if (st) return st;
-        st = check_err_bits(c);
-        if (st) return st;
+        if (!skin_rule) {
+          k_check_skin<<<1, 1, 0, s>>>(c->d_sc, skin_lim2);
+          c->kernels += 1;
+          // an error so far (skin, non-finite position) ends the call here
+          st = read_scalars(c, s);
+          if (st) return st;
+          st = check_err_bits(c);
+          if (st) return st;
+        }
         launch_wrap_positions(c, d_x, s);
         st = build_checked(c, d_x, nullptr, s);   // grows the EAM rows if one overflows
         if (st) return st;
+      }
+      bool csp_done = false;
+      if (keep) {   // CSP from the kept rows; any atom they cannot decide sends the update to a rebuild
+        PhaseTimer t(c, s, AP_PHASE_CLASSIFY);
+        launch_shadow(c, d_x, s);
+        launch_csp(c, d_x, ch, s, false, m);
+        st = read_scalars(c, s);
+        if (st) return st;
+        if (c->h_sc->n_stale_bad == 0) {
+          c->cells_stale = true;
+          c->stale_m = m;
+          c->kept++;
+          csp_done = true;
+        } else {
+          PhaseTimer t2(c, s, AP_PHASE_NEIGHBORS);
+          launch_wrap_positions(c, d_x, s);
+          st = build_checked(c, d_x, nullptr, s);
+          if (st) return st;
+          keep = false;
+        }
       }
       {
         PhaseTimer t(c, s, AP_PHASE_CLASSIFY);
         if (lam_step) {
           if (thermo)
             CK(cudaMemcpyAsync(c->d_th_lamc, c->d_lam_int, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
-          classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s, true);
+          classify_async(c, d_x, ch, c->d_lam_int, c->d_precise, nullptr, s, !keep, csp_done);
         }
       }
       if (lam_step && thermo) {
@@ -1000,6 +1064,7 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
     h_stats->th_corrected = (int64_t)c->h_sc->th_n;
     h_stats->th_refused = (int64_t)c->h_sc->th_bad;
     h_stats->th_energy = c->h_sc->th_e;
+    h_stats->kept = c->kept;
   }
   return check_err_bits(c);
 }

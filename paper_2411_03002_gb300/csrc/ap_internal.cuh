@@ -79,6 +79,7 @@ struct DevScalars {
   int work_counter2;  // second persistent-kernel work counter (right after work_counter)
   int n_csp_slow;     // atoms handed from the FP32 CSP kernel to the exact one
   int ace_row_max;    // longest ACE row of the last ACE row build
+  int n_stale_bad;    // atoms whose CSP the rows of an earlier build cannot decide (stale rows)
   unsigned long long row_total;   // ap_neighbor_total's result
   unsigned int max_disp2_bits;  // float bits of the largest squared displacement
   long long n_precise64;
@@ -156,6 +157,10 @@ struct ap_ctx {
   bool lim_valid = false;        // d_lim_eam holds the prefixes of an EAM pass on the current rows
   float split_rpf2 = 0.f;        // r_c^2 (FP32) at which the EAM rows were split
   int sten_spread[3] = {0, 0, 0};
+  int sten_spread_stale[3] = {0, 0, 0};   // the spread's stencil with cells up to skin/2 old
+  bool cells_stale = false;      // the atoms moved since the cell build (ap_step skipped a rebuild)
+  double stale_m = 0.0;          // with cells_stale: the largest displacement since the cell build
+  bool stale_ok = false;         // rows and cells may be kept past a lambda update (pair offsets unwrap)
 
   // capacity
   int64_t n_cap = 0;             // per-atom arrays sized for this many atoms
@@ -165,6 +170,7 @@ struct ap_ctx {
   bool built = false;
   bool lam_ready = false;        // a classification exists for the current n
   int64_t rebuilds = 0;
+  int64_t kept = 0;              // lambda updates that kept the lists (skin criterion)
 
   // per-atom state (device)
   int* d_cell = nullptr;         // global cell id (wrapped)
@@ -183,6 +189,8 @@ struct ap_ctx {
   int* d_cnt_eam = nullptr;      // [n]
   int* d_lim_eam = nullptr;      // [n] the row build's in-range count, then (after each EAM density
                                  //     pass) one past the last entry found inside r_c
+  int* d_split_eam = nullptr;    // [n] the row build's in-range count, kept until the next build
+                                 //     (rebuild_every = AP_REBUILD_SKIN only)
   int* d_nbr_ace = nullptr;      // [ace_q_cap][cap_ace] rows in queue order
   int* d_off_ace = nullptr;
   int* d_cnt_ace = nullptr;      // [ace_q_cap]
@@ -315,8 +323,12 @@ int prof_mark(ap_ctx* c, cudaStream_t s);
 void prof_add(ap_ctx* c, int phase, int start, int end);
 
 // k_classify.cu
-// fresh_rows: the EAM rows were built at d_x (the CSP may stop after their in-range part)
-void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s, bool fresh_rows = false);
+// fresh_rows: the EAM rows were built at d_x (the CSP may stop after their in-range part);
+// stale_disp > 0: the rows are older than d_x, every atom having moved at most stale_disp
+// since the build; atoms whose selection the rows cannot guarantee are counted in
+// DevScalars::n_stale_bad.
+void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s, bool fresh_rows = false,
+                double stale_disp = 0.0);
 void launch_lambda0(ap_ctx* c, const uint8_t* d_ch, const double* d_score, double lo, double hi, cudaStream_t s);
 void launch_spread(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s);
 void launch_lambda_final(ap_ctx* c, const uint8_t* d_ch, double* d_lam, int* d_queue, int64_t* d_nq64,

@@ -132,7 +132,8 @@ __device__ __forceinline__ void csp_atom(int i, const double* __restrict__ x, co
                                          const int* __restrict__ nbr, const int* __restrict__ off,
                                          const int* __restrict__ cnt, int cap, float rsf2, double rs2,
                                          double* __restrict__ csp, int* __restrict__ slow, int* __restrict__ n_slow,
-                                         const int* __restrict__ nin = nullptr, float rpf2 = 0.f) {
+                                         const int* __restrict__ nin = nullptr, float rpf2 = 0.f,
+                                         float stale2 = 0.f, int* __restrict__ n_stale = nullptr) {
   static_assert(kNN <= 255, "neighbour slots are packed in 8 bits");
   if (ch && !ch[i]) {
     csp[i] = 0.0;
@@ -194,6 +195,12 @@ __device__ __forceinline__ void csp_atom(int i, const double* __restrict__ x, co
       }
     }
   }
+  // Rows older than the positions (stale2 > 0): every atom outside the row lies beyond
+  // r_search - 2 m (m the largest displacement since the build), stale2 = that radius
+  // squared.  The row's selection is exact when 12 candidates lie inside it with a
+  // guard band; otherwise (a nearly isolated atom) the atom is counted and the caller
+  // rebuilds the rows and computes the CSP again.
+  if (stale2 > 0.f && !(n_in >= kNN && tr[kNN - 1] + 2.f * kBand < stale2)) atomicAdd(n_stale, 1);
   if (n_in < kNN) {
     csp[i] = INFINITY;
     return;
@@ -351,10 +358,12 @@ __global__ void __launch_bounds__(128) k_csp(int n, const double* __restrict__ x
                                                 const int* __restrict__ nbr, const int* __restrict__ off,
                                                 const int* __restrict__ cnt, int cap, float rsf2, double rs2,
                                                 double* __restrict__ csp, int* __restrict__ slow,
-                                                int* __restrict__ n_slow, const int* __restrict__ nin, float rpf2) {
+                                                int* __restrict__ n_slow, const int* __restrict__ nin, float rpf2,
+                                                float stale2, int* __restrict__ n_stale) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n)
-    csp_atom<true>(i, x, ch, sys, atom_sys, s32, cunw, nbr, off, cnt, cap, rsf2, rs2, csp, slow, n_slow, nin, rpf2);
+    csp_atom<true>(i, x, ch, sys, atom_sys, s32, cunw, nbr, off, cnt, cap, rsf2, rs2, csp, slow, n_slow, nin, rpf2,
+                   stale2, n_stale);
 }
 
 __global__ void __launch_bounds__(128) k_csp_exact(const double* __restrict__ x, const uint8_t* __restrict__ ch,
@@ -363,10 +372,12 @@ __global__ void __launch_bounds__(128) k_csp_exact(const double* __restrict__ x,
                                                    const int* __restrict__ nbr, const int* __restrict__ off,
                                                    const int* __restrict__ cnt, int cap, float rsf2, double rs2,
                                                    double* __restrict__ csp, const int* __restrict__ slow,
-                                                   const int* __restrict__ n_slow) {
+                                                   const int* __restrict__ n_slow, float stale2,
+                                                   int* __restrict__ n_stale) {
   const int m = *n_slow;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x)
-    csp_atom<false>(slow[t], x, ch, sys, atom_sys, s32, cunw, nbr, off, cnt, cap, rsf2, rs2, csp, nullptr, nullptr);
+    csp_atom<false>(slow[t], x, ch, sys, atom_sys, s32, cunw, nbr, off, cnt, cap, rsf2, rs2, csp, nullptr, nullptr,
+                    nullptr, 0.f, stale2, n_stale);
 }
 
 // Canonical moving average over a ring buffer [ns][n]: oldest -> newest, then / ns.
@@ -433,7 +444,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
     const uint8_t* __restrict__ ch, const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
     const float4* __restrict__ s32, const int4* __restrict__ cunw, const int* __restrict__ cstart,
     const int* __restrict__ catoms, const double* __restrict__ lam0, double r_lo, double r_hi, int mode, int sx,
-    int sy, int sz, double* __restrict__ lam_min) {
+    int sy, int sz, double* __restrict__ lam_min, float margin) {
   // per warp: inclusive prefix of candidate counts, first catoms slot, stencil offset
   __shared__ int s_pre[kSpreadWarps][32], s_beg[kSpreadWarps][32], s_t[kSpreadWarps][32], s_img[kSpreadWarps][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -441,6 +452,8 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
   const int m = *n_det;
   const double rh2 = __dmul_rn(r_hi, r_hi);
   const float rhf2 = (float)rh2;
+  // cells older than the positions (atoms up to `margin` from their cells): prune beyond r_hi + margin
+  const float rprune = (float)r_hi + margin, prune2 = rprune * rprune;
   const double width = __dsub_rn(r_hi, r_lo);
   const float r_lo_f = (float)r_lo, inv_w_f = (float)(1.0 / width);
   const int wx = 2 * sx + 1, wy = 2 * sy + 1, wz = 2 * sz + 1;
@@ -474,7 +487,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
           const float gx = fmaxf(0.f, fmaxf((float)dx * S.hf[0] - si.x, si.x - (float)(dx + 1) * S.hf[0]));
           const float gy = fmaxf(0.f, fmaxf((float)dy * S.hf[1] - si.y, si.y - (float)(dy + 1) * S.hf[1]));
           const float gz = fmaxf(0.f, fmaxf((float)dz * S.hf[2] - si.z, si.z - (float)(dz + 1) * S.hf[2]));
-          if (gx * gx + gy * gy + gz * gz <= rhf2 + kBand) {
+          if (gx * gx + gy * gy + gz * gz <= prune2 + kBand) {
             const int cid = S.cell_base + (tc[2] * S.nc[1] + tc[1]) * S.nc[0] + tc[0];
             beg = cstart[cid];
             cnt = cstart[cid + 1] - beg;
@@ -579,20 +592,35 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s, bool fresh_rows) {
+void launch_csp(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s, bool fresh_rows,
+                double stale_disp) {
   double r = c->cfg.eam_rc + c->cfg.skin;
   double rs2 = r * r;
   const int* off = c->stored_off ? c->d_off_eam : nullptr;
   int* n_slow = &c->d_sc->n_csp_slow;
   cudaMemsetAsync(n_slow, 0, sizeof(int), s);
+  // Rows older than the positions: stale2 = the radius inside which they are complete.
+  // The build's split still bounds the skin part from below: its entries were beyond r_c
+  // at the build and are now beyond r_c - 2 m, the radius the in-range part is tested
+  // against before the skin part is skipped.
+  float stale2 = 0.f;
+  const int* nin = fresh_rows ? c->d_lim_eam : nullptr;
+  float rpf2 = c->split_rpf2;
+  if (stale_disp > 0.0) {
+    const double rin = r - 2.0 * stale_disp;
+    stale2 = rin > 0.0 ? (float)(rin * rin) : 1e-30f;
+    cudaMemsetAsync(&c->d_sc->n_stale_bad, 0, sizeof(int), s);
+    const double rp = std::sqrt((double)c->split_rpf2) - 2.0 * stale_disp;
+    nin = c->d_split_eam;
+    rpf2 = rp > 0.0 ? (float)(rp * rp) : 0.f;
+  }
   k_csp<<<nblk(c->n, 128), 128, 0, s>>>((int)c->n, d_x, d_ch, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
                                               c->d_nbr_eam, off, c->d_cnt_eam, c->cap_eam, (float)rs2, rs2, c->d_csp,
-                                              c->d_csp_slow, n_slow, fresh_rows ? c->d_lim_eam : nullptr,
-                                              c->split_rpf2);
+                                              c->d_csp_slow, n_slow, nin, rpf2, stale2, &c->d_sc->n_stale_bad);
   // the handed-over atoms (a small fraction), grid-stride over the device-side count
   k_csp_exact<<<c->num_sms * 4, 128, 0, s>>>(d_x, d_ch, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw, c->d_nbr_eam,
                                              off, c->d_cnt_eam, c->cap_eam, (float)rs2, rs2, c->d_csp,
-                                             c->d_csp_slow, n_slow);
+                                             c->d_csp_slow, n_slow, stale2, &c->d_sc->n_stale_bad);
   c->kernels += 2;
 }
 
@@ -612,10 +640,11 @@ void launch_lambda0(ap_ctx* c, const uint8_t* d_ch, const double* d_score, doubl
 
 void launch_spread(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream_t s) {
   int grid = c->num_sms * 8;
+  const int* st = c->cells_stale ? c->sten_spread_stale : c->sten_spread;
+  const float margin = c->cells_stale ? (float)c->stale_m : 0.f;
   k_spread<<<grid, kSpreadWarps * 32, 0, s>>>(c->d_detected, &c->d_sc->n_detected, d_x, d_ch, c->d_sys, c->d_atom_sys, c->d_sh32,
                                 c->d_cunw, c->d_cell_start, c->d_cell_atoms, c->d_lam0, c->cfg.r_lo, c->cfg.r_hi,
-                                c->cfg.fcut_mode, c->sten_spread[0], c->sten_spread[1], c->sten_spread[2],
-                                c->d_lam_min);
+                                c->cfg.fcut_mode, st[0], st[1], st[2], c->d_lam_min, margin);
   c->kernels += 1;
 }
 

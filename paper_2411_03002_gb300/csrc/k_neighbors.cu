@@ -2,6 +2,9 @@
 // the paper delegates to LAMMPS).  Row i of a list holds every image (j, s) with
 // |x_j + s L - x_i|^2 < r_list^2, decided by that FP64 expression; an FP32
 // cell-relative pre-filter only skips candidates that are clearly in or out.
+#include <algorithm>
+#include <cmath>
+
 #include "ap_internal.cuh"
 
 namespace ap {
@@ -194,26 +197,29 @@ __device__ inline bool exact_within(const double* __restrict__ x, const SysInfo&
   return r2 < rc2;
 }
 
-// One warp builds one row (used for the long ACE rows): lanes take stencil cells (5x5x5 around atom i, pruned
-// by the cell-box distance), iterate their cells' atoms in lock-step and append
-// accepted (j, offset) with ballot compaction.  Entry order: (cell round, atom
-// slot, lane) -- deterministic.  Returns the full count (may exceed cap).
+// One warp builds one row (used for the long ACE rows): lanes take stencil cells
+// ((2 sten + 1)^3 around atom i's cell, pruned by the cell-box distance), iterate their
+// cells' atoms in lock-step and append accepted (j, offset) with ballot compaction.
+// Entry order: (cell round, atom slot, lane) -- deterministic.  Returns the full count
+// (may exceed cap).  With cells older than the positions (atoms moved up to `margin`
+// since the cell build), a cell is pruned only beyond r + margin, and the stencil
+// must reach r + 2 margin.
 __device__ inline int build_row_warp(int i, const double* __restrict__ x, const SysInfo& S,
                                      const float4* __restrict__ s32, const int4* __restrict__ cunw,
                                      const int* __restrict__ cstart, const int* __restrict__ catoms, float rcf2,
                                      double rc2, float band, int cap, int* __restrict__ row,
-                                     int* __restrict__ offrow) {
+                                     int* __restrict__ offrow, int sten, float margin) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const float4 si = s32[i];
   const int4 ci = cunw[i];
   const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
-  const float rmax2 = rcf2 + band;
-  constexpr int W = 2 * kStencil + 1;
+  const float rprune = sqrtf(rcf2) + margin, prune2 = rprune * rprune + band;
+  const int W = 2 * sten + 1;
   int cnt = 0;
   for (int t0 = 0; t0 < W * W * W; t0 += 32) {
     const int t = t0 + lane;
-    const int dx = t % W - kStencil, dy = (t / W) % W - kStencil, dz = t / (W * W) - kStencil;
+    const int dx = t % W - sten, dy = (t / W) % W - sten, dz = t / (W * W) - sten;
     int tc[3] = {cw[0] + dx, cw[1] + dy, cw[2] + dz};
     int img[3] = {0, 0, 0};
     bool valid = t < W * W * W;
@@ -229,7 +235,7 @@ __device__ inline int build_row_warp(int i, const double* __restrict__ x, const 
       const float gx = fmaxf(0.f, fmaxf((float)dx * S.hf[0] - si.x, si.x - (float)(dx + 1) * S.hf[0]));
       const float gy = fmaxf(0.f, fmaxf((float)dy * S.hf[1] - si.y, si.y - (float)(dy + 1) * S.hf[1]));
       const float gz = fmaxf(0.f, fmaxf((float)dz * S.hf[2] - si.z, si.z - (float)(dz + 1) * S.hf[2]));
-      valid = gx * gx + gy * gy + gz * gz <= rmax2;
+      valid = gx * gx + gy * gy + gz * gz <= prune2;
     }
     int b = 0, len = 0;
     if (valid) {
@@ -436,14 +442,14 @@ __global__ void __launch_bounds__(256) k_build_ace(const int* __restrict__ queue
                                                    const int4* __restrict__ cunw, const int* __restrict__ cstart,
                                                    const int* __restrict__ catoms, float rcf2, double rc2,
                                                    float band, int cap, int* __restrict__ nbr, int* __restrict__ off,
-                                                   int* __restrict__ cnt, DevScalars* sc) {
+                                                   int* __restrict__ cnt, DevScalars* sc, int sten, float margin) {
   const int m = *nq;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < m; q += warps) {
     const int i = queue[q];
     const SysInfo& S = sys_of(sys, atom_sys, i);
     const int c = build_row_warp(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, band, cap, nbr + (size_t)q * cap,
-                                 off ? off + (size_t)q * cap : nullptr);
+                                 off ? off + (size_t)q * cap : nullptr, sten, margin);
     if ((threadIdx.x & 31) == 0) {
       cnt[q] = c < cap ? c : cap;
       atomicMax(&sc->ace_row_max, c < cap ? c : cap);
@@ -570,11 +576,24 @@ void launch_build_eam(ap_ctx* c, const double* d_x, cudaStream_t s) {
 
 void launch_build_ace(ap_ctx* c, const double* d_x, const int* d_queue, const int* d_nq, cudaStream_t s) {
   double r = c->cfg.ace_rc + c->cfg.skin;
+  // Cells older than the positions (ap_step kept the EAM lists past a lambda update): the
+  // atoms moved up to m = stale_m since the cell build.  The rows then reach 2 m further,
+  // so that they stay complete while no atom moves more than skin/2 from its position at
+  // the cell build (the EAM lists' own condition), and the stencil reaches r + 2 m.
+  int sten = kStencil;
+  float margin = 0.f;
+  if (c->cells_stale) {
+    margin = (float)c->stale_m;
+    r += 2.0 * c->stale_m;
+    for (const SysInfo& S : c->h_sys)
+      for (int d = 0; d < 3; ++d) sten = std::max(sten, (int)std::ceil((r + 2.0 * c->stale_m) / S.h[d]));
+  }
   double rc2 = r * r;
   int grid = c->num_sms * 8;
   k_build_ace<<<grid, 256, 0, s>>>(d_queue, d_nq, d_x, c->d_sys, c->d_atom_sys, c->d_sh32, c->d_cunw,
                                    c->d_cell_start, c->d_cell_atoms, (float)rc2, rc2, kBand, c->cap_ace,
-                                   c->d_nbr_ace, c->stored_off ? c->d_off_ace : nullptr, c->d_cnt_ace, c->d_sc);
+                                   c->d_nbr_ace, c->stored_off ? c->d_off_ace : nullptr, c->d_cnt_ace, c->d_sc, sten,
+                                   margin);
   c->kernels += 1;
 }
 

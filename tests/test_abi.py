@@ -78,6 +78,10 @@ def test_config_validation_rejects_bad_values():
     h = ctypes.c_void_p()
     assert N.lib().ap_create(ctypes.byref(cfg), ctypes.byref(h)) == 1   # AP_ERR_ARG before any device call
     assert N.lib().ap_create(None, ctypes.byref(h)) == 1
+    # rebuild_every: a period >= 0 or the skin criterion (-1), nothing below
+    cfg = api.make_config(I.EAM_NOMINAL, I.ace_params(0), I.HybridParams(), rebuild_every=-2)
+    assert N.lib().ap_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+    assert N.REBUILD_SKIN == -1
 
 
 def test_null_context_calls_fail_cleanly():

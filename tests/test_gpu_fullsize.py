@@ -1,12 +1,15 @@
 """Parity at the full benchmark size, through the timed region's path (needs a GPU).
 
 The 4,000,000-atom nanoindentation-shaped slab is prepared and integrated exactly as
-bench.py times it (mixed precision, Hyb2, lambda and the lists updated every 10 MD
-steps, indenter, fixed bottom layers): ap_step(0) prepares, then ap_step runs 10, 10
-and 5 MD steps.  The lambda updates at steps 10 and 20 push the second and third
-CSP and lambda_min samples into the 11-sample windows (Eqs. csp_2_i, lambda_3_i) and
-rebuild the rows; the forces at step 25 are evaluated on rows built at step 20 with
-the atoms moved since (the EAM force pass walks the prefix the density pass found).
+bench.py times it (mixed precision, Hyb2, lambda updated every 10 MD steps, the lists
+on the skin criterion, indenter, fixed bottom layers): ap_step(0) prepares, then
+ap_step runs 10, 10 and 5 MD steps.  The lambda updates at steps 10 and 20 push the
+second and third CSP and lambda_min samples into the 11-sample windows (Eqs. csp_2_i,
+lambda_3_i).  At 300 K no atom moves skin/4 = 0.25 A in 10 fs, so the update at step 10
+keeps the lists of step 0: its CSP comes from rows 10 steps older than the positions,
+its spread from old cells, and its ACE rows are built from those cells; the forces at
+step 25 are evaluated on rows older still (the EAM force pass walks the prefix the
+density pass found).
 
 About 1,000 sampled atoms are checked against the oracle run on local clusters with
 the GPU's own positions at each step:
@@ -49,7 +52,7 @@ def _open_box(xc):
 def run():
     w = I.config_c5(100, hyb=I.HYB2)
     cfg = ap.make_config(I.eam_params(0), I.ace_for_config(5), w.hyb, precision=ap.PREC_MIXED, indenter=w.indenter,
-                         lambda_every=10, dt=w.dt)
+                         lambda_every=10, dt=w.dt, rebuild_every=ap.REBUILD_SKIN)
     ctx = ap.Context(cfg)
     dev = "cuda"
     x = torch.as_tensor(w.x, device=dev).clone()
@@ -119,6 +122,12 @@ def test_sample_count_and_strata(run, plan):
     for name, m in (("detected", lam0 < 1.0), ("lambda=0", lam == 0.0), ("interior", (lam > 0) & (lam < 1)),
                     ("lambda=1", lam == 1.0), ("fixed", fixed != 0)):
         assert m.sum() >= 50, name
+
+
+def test_updates_kept_the_lists(run):
+    st = run["stats"]
+    print(f"4M run: kept {st.kept} of 2 updates, rebuilds {st.rebuilds}, max displacement {st.max_disp:.3f} A")
+    assert st.kept >= 1 and st.error_bits == 0
 
 
 def test_precise_fraction_in_expected_range(run):
