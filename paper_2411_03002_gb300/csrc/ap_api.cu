@@ -226,7 +226,7 @@ ap_status ensure_capacity(ap_ctx* c, int64_t n) {
   CK(dalloc(c->d_sh32, m));
   CK(dalloc(c->d_sh32c, m));
   CK(dalloc(c->d_sh64, m));
-  CK(dalloc(c->d_xbuild, 3 * m));
+  CK(dalloc(c->d_sh32b, m));
   CK(dalloc(c->d_vscale, m));
   CK(dalloc(c->d_cnt_eam, m));
   CK(dalloc(c->d_lim_eam, m));
@@ -310,7 +310,7 @@ void build_async(ap_ctx* c, const double* d_x, const int32_t* d_species, cudaStr
   c->lim_valid = false;
   c->cells_stale = false;
   c->stale_m = 0.0;
-  cudaMemcpyAsync(c->d_xbuild, d_x, sizeof(double) * 3 * (size_t)c->n, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(c->d_sh32b, c->d_sh32, sizeof(float4) * (size_t)c->n, cudaMemcpyDeviceToDevice, s);
   cudaMemsetAsync(&c->d_sc->max_disp2_bits, 0, sizeof(unsigned int), s);
   c->rebuilds++;
 }
@@ -619,7 +619,7 @@ void ap_destroy(ap_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   void* ptrs[] = {c->d_sys, c->d_atom_sys, c->d_cell, c->d_cunw, c->d_cell_start, c->d_cell_count, c->d_cell_atoms,
-                  c->d_slot, c->d_sh32, c->d_sh32c, c->d_sh64, c->d_xbuild, c->d_vscale, c->d_nbr_eam, c->d_off_eam, c->d_cnt_eam,
+                  c->d_slot, c->d_sh32, c->d_sh32c, c->d_sh64, c->d_sh32b, c->d_vscale, c->d_nbr_eam, c->d_off_eam, c->d_cnt_eam,
                   c->d_lim_eam, c->d_split_eam, c->d_nbr_ace, c->d_off_ace, c->d_cnt_ace, c->d_csp, c->d_csp_slow, c->d_csp_avg, c->d_lam0, c->d_lam_min,
                   c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected,
                   c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_faccfix, c->d_efast, c->d_eprec,
@@ -942,8 +942,8 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
       if (st) return st;
       float d2;
       std::memcpy(&d2, &c->h_sc->max_disp2_bits, sizeof(float));
-      // FP32 squared sum of FP64 differences: a few ulp of headroom
-      m = std::sqrt((double)d2) * (1.0 + 1e-5) + 1e-6;
+      // from FP32 shadows (a few 1e-7 A per component): headroom
+      m = std::sqrt((double)d2) * (1.0 + 1e-5) + 1e-5;
       build = m > 0.5 * g.skin;
       keep = lam_step && !build && keep_ok && m <= 0.25 * g.skin;
       build = build || (lam_step && !keep);
@@ -970,8 +970,7 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
       bool csp_done = false;
       if (keep) {   // CSP from the kept rows; any atom they cannot decide sends the update to a rebuild
         PhaseTimer t(c, s, AP_PHASE_CLASSIFY);
-        launch_shadow(c, d_x, s);
-        launch_csp(c, d_x, ch, s, false, m);
+        launch_csp(c, d_x, ch, s, false, m);   // the drift wrote the shadows of d_x
         st = read_scalars(c, s);
         if (st) return st;
         if (c->h_sc->n_stale_bad == 0) {
@@ -1006,9 +1005,6 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
         st = build_ace_checked(c, d_x, c->d_precise, &c->d_sc->n_precise, s);
         if (st) return st;
       }
-    } else {
-      PhaseTimer t(c, s, AP_PHASE_NEIGHBORS);
-      launch_shadow(c, d_x, s);
     }
     {
       PhaseTimer t(c, s, AP_PHASE_EAM);

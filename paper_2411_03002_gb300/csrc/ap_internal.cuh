@@ -34,6 +34,16 @@ __host__ __device__ inline int cell_x(int c) { return c & 1023; }
 __host__ __device__ inline int cell_y(int c) { return (c >> 10) & 1023; }
 __host__ __device__ inline int cell_z(int c) { return (c >> 20) & 1023; }
 
+#ifdef __CUDACC__
+// Cell-relative shadow s = (x - lo) - c h of a position in its unwrapped cell c, with one
+// rounding for the product and the difference (FP64; the FP32 shadow rounds s).
+__device__ inline void cell_shadow(const SysInfo& S, const int4& c, const double x[3], double s[3]) {
+  s[0] = fma(-(double)c.x, S.h[0], x[0] - S.lo[0]);
+  s[1] = fma(-(double)c.y, S.h[1], x[1] - S.lo[1]);
+  s[2] = fma(-(double)c.z, S.h[2], x[2] - S.lo[2]);
+}
+#endif
+
 // Stored per-entry cell offsets k (small boxes): 8 bits per component, biased by 128.
 __host__ __device__ inline int pack_off(int kx, int ky, int kz) { return (kx + 128) | ((ky + 128) << 8) | ((kz + 128) << 16); }
 __host__ __device__ inline int off_x(int p) { return (p & 255) - 128; }
@@ -182,7 +192,7 @@ struct ap_ctx {
   float4* d_sh32 = nullptr;      // FP32 cell-relative shadow
   float4* d_sh32c = nullptr;     // the same in cell order (the EAM row build's candidate stream)
   double4_32a* d_sh64 = nullptr;     // FP64 cell-relative shadow
-  double* d_xbuild = nullptr;    // [n][3] positions at the last build
+  float4* d_sh32b = nullptr;     // [n] the FP32 shadows at the last build (displacement check)
   double* d_vscale = nullptr;    // [n] 0.5 dt ACC / m_i of the current ap_step call
   int* d_nbr_eam = nullptr;      // [n][cap_eam]
   int* d_off_eam = nullptr;      // [n][cap_eam] (stored offsets only)

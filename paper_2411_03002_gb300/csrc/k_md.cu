@@ -19,27 +19,46 @@ __global__ void k_vscale(int n, const double* __restrict__ mass, double dt, doub
   if (i < n) vs[i] = 0.5 * dt * kAcc / mass[i];
 }
 
+// Half kick and drift, and the new positions' cell-relative shadows (the k_shadow
+// arithmetic, relative to the cells of the last build).  The displacement since the
+// build (skin check) is the difference of the FP32 shadow and the build's shadow s32b:
+// both are relative to the same cell, so it is exact to a few 1e-7 A.
 __global__ void k_vv_first(int n, double* __restrict__ x, double* __restrict__ v, const double* __restrict__ f,
                            const double* __restrict__ vs, const uint8_t* __restrict__ fixed, double dt,
-                           const double* __restrict__ xb, DevScalars* sc) {
+                           const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
+                           const int4* __restrict__ cunw, float4* __restrict__ s32, double4_32a* __restrict__ s64,
+                           const float4* __restrict__ s32b, DevScalars* sc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   float d2 = 0.f;
   if (i < n) {
-    if (fixed && fixed[i]) {
+    double xx[3];
+    const bool mobile = !(fixed && fixed[i]);
+    if (!mobile) {
       v[3 * i + 0] = v[3 * i + 1] = v[3 * i + 2] = 0.0;
+      for (int a = 0; a < 3; ++a) xx[a] = x[3 * i + a];
     } else {
       const double s = vs[i];
       bool bad = false;
       for (int a = 0; a < 3; ++a) {
         double vv = v[3 * i + a] + s * f[3 * i + a];
-        double xx = x[3 * i + a] + dt * vv;
+        xx[a] = x[3 * i + a] + dt * vv;
         v[3 * i + a] = vv;
-        x[3 * i + a] = xx;
-        bad |= !isfinite(xx);
-        const float e = (float)(xx - xb[3 * i + a]);   // displacement since the build (skin check)
-        d2 += e * e;
+        x[3 * i + a] = xx[a];
+        bad |= !isfinite(xx[a]);
       }
       if (bad) atomicOr(&sc->err, kErrNonfinite);
+    }
+    const SysInfo& S = sys[atom_sys ? atom_sys[i] : 0];
+    const int4 c = cunw[i];
+    double sh[3];
+    cell_shadow(S, c, xx, sh);
+    const float4 s4 = make_float4((float)sh[0], (float)sh[1], (float)sh[2], __int_as_float(c.w));
+    s32[i] = s4;
+    if (s64) s64[i] = make_double4_32a(sh[0], sh[1], sh[2], (double)c.w);
+    if (mobile) {
+      const float4 b = s32b[i];
+      const float ex = s4.x - b.x, ey = s4.y - b.y, ez = s4.z - b.z;
+      d2 = ex * ex + ey * ey + ez * ez;
     }
   }
 #pragma unroll
@@ -148,7 +167,9 @@ void launch_vscale(ap_ctx* c, const double* d_mass, cudaStream_t s) {
 void launch_vv_first(ap_ctx* c, double* d_x, double* d_v, const double* d_f, const double* d_mass,
                      const uint8_t* d_fixed, cudaStream_t s) {
   (void)d_mass;   // the half-kick factors come from launch_vscale
-  k_vv_first<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, d_v, d_f, c->d_vscale, d_fixed, c->cfg.dt, c->d_xbuild,
+  k_vv_first<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, d_v, d_f, c->d_vscale, d_fixed, c->cfg.dt, c->d_sys,
+                                             c->d_atom_sys, c->d_cunw, c->d_sh32,
+                                             c->cfg.precision == AP_PREC_FP64 ? c->d_sh64 : nullptr, c->d_sh32b,
                                              c->d_sc);
   c->kernels += 1;
 }

@@ -153,13 +153,12 @@ __global__ void k_shadow(int n, const double* __restrict__ x, const SysInfo* __r
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const SysInfo& S = sys_of(sys, atom_sys, i);
-  int4 c = cunw[i];
-  // (x - lo) - c h with one rounding for the product and the difference
-  double s0 = fma(-(double)c.x, S.h[0], x[3 * i + 0] - S.lo[0]);
-  double s1 = fma(-(double)c.y, S.h[1], x[3 * i + 1] - S.lo[1]);
-  double s2 = fma(-(double)c.z, S.h[2], x[3 * i + 2] - S.lo[2]);
-  s32[i] = make_float4((float)s0, (float)s1, (float)s2, __int_as_float(c.w));
-  if (s64) s64[i] = make_double4_32a(s0, s1, s2, (double)c.w);
+  const int4 c = cunw[i];
+  const double xi[3] = {x[3 * i + 0], x[3 * i + 1], x[3 * i + 2]};
+  double sh[3];
+  cell_shadow(S, c, xi, sh);
+  s32[i] = make_float4((float)sh[0], (float)sh[1], (float)sh[2], __int_as_float(c.w));
+  if (s64) s64[i] = make_double4_32a(sh[0], sh[1], sh[2], (double)c.w);
 }
 
 __global__ void k_wrap(int n, double* __restrict__ x, const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys) {
@@ -197,32 +196,35 @@ __device__ inline bool exact_within(const double* __restrict__ x, const SysInfo&
   return r2 < rc2;
 }
 
-// One warp builds one row (used for the long ACE rows): lanes take stencil cells
-// ((2 sten + 1)^3 around atom i's cell, pruned by the cell-box distance), iterate their
-// cells' atoms in lock-step and append accepted (j, offset) with ballot compaction.
-// Entry order: (cell round, atom slot, lane) -- deterministic.  Returns the full count
-// (may exceed cap).  With cells older than the positions (atoms moved up to `margin`
-// since the cell build), a cell is pruned only beyond r + margin, and the stencil
-// must reach r + 2 margin.
+// One warp builds one row (used for the long ACE rows).  The lanes test the stencil cells
+// ((2 sten + 1)^3 around atom i's cell) 32 at a time against the cell-box distance and
+// queue the cells that pass in a per-warp shared-memory buffer; each full batch of 32
+// queued cells is walked with one cell per lane, the lanes iterating their cells' atoms in
+// lock-step, and accepted (j, offset) are appended with ballot compaction.  Entry order:
+// (batch, atom slot, lane) -- deterministic.  Returns the full count (may exceed cap).
+// With cells older than the positions (atoms moved up to `margin` since the cell build),
+// a cell is pruned only beyond r + margin, and the stencil must reach r + 2 margin.
+// buf: this warp's 64-entry shared-memory queue (first atom slot, count, cell offset,
+// image).
 __device__ inline int build_row_warp(int i, const double* __restrict__ x, const SysInfo& S,
                                      const float4* __restrict__ s32, const int4* __restrict__ cunw,
                                      const int* __restrict__ cstart, const int* __restrict__ catoms, float rcf2,
                                      double rc2, float band, int cap, int* __restrict__ row,
-                                     int* __restrict__ offrow, int sten, float margin) {
+                                     int* __restrict__ offrow, int sten, float margin, int4* buf) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const float4 si = s32[i];
   const int4 ci = cunw[i];
   const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
   const float rprune = sqrtf(rcf2) + margin, prune2 = rprune * rprune + band;
-  const int W = 2 * sten + 1;
-  int cnt = 0;
-  for (int t0 = 0; t0 < W * W * W; t0 += 32) {
+  const int W = 2 * sten + 1, ncell = W * W * W;
+  int cnt = 0, queued = 0;
+  for (int t0 = 0; t0 < ncell; t0 += 32) {
     const int t = t0 + lane;
     const int dx = t % W - sten, dy = (t / W) % W - sten, dz = t / (W * W) - sten;
     int tc[3] = {cw[0] + dx, cw[1] + dy, cw[2] + dz};
     int img[3] = {0, 0, 0};
-    bool valid = t < W * W * W;
+    bool valid = t < ncell;
     for (int d = 0; d < 3 && valid; ++d) {
       if (S.periodic[d]) {
         img[d] = floor_div(tc[d], S.nc[d]);
@@ -243,34 +245,51 @@ __device__ inline int build_row_warp(int i, const double* __restrict__ x, const 
       b = cstart[cid];
       len = cstart[cid + 1] - b;
     }
-    const int maxlen = __reduce_max_sync(0xffffffffu, len);
-    const float ox = (float)dx * S.hf[0] - si.x;
-    const float oy = (float)dy * S.hf[1] - si.y;
-    const float oz = (float)dz * S.hf[2] - si.z;
-    const bool self_cell = dx == 0 && dy == 0 && dz == 0;
-    for (int k = 0; k < maxlen; ++k) {
-      bool take = false;
-      int j = 0;
-      if (k < len) {
-        j = catoms[b + k];
-        if (!(j == i && self_cell)) {
-          const float4 sj = s32[j];
-          const float ddx = ox + sj.x, ddy = oy + sj.y, ddz = oz + sj.z;
-          const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
-          if (r2f < rcf2 - band) {
-            take = true;
-          } else if (r2f <= rcf2 + band) {
-            take = exact_within(x, S, i, j, ci, cunw[j], img, rc2);
+    const unsigned vm = __ballot_sync(0xffffffffu, len > 0);
+    if (len > 0) buf[queued + __popc(vm & lt)] = make_int4(b, len, pack_off(dx, dy, dz), pack_off(img[0], img[1], img[2]));
+    queued += __popc(vm);
+    __syncwarp();
+    // walk a full batch, or what is left after the last stencil cell
+    const bool last = t0 + 32 >= ncell;
+    while (queued >= 32 || (last && queued > 0)) {
+      const int take_n = queued < 32 ? queued : 32;
+      int4 e = make_int4(0, 0, 0, 0);
+      if (lane < take_n) e = buf[lane];
+      __syncwarp();
+      if (lane + 32 < queued) buf[lane] = buf[lane + 32];   // the rest moves to the front
+      queued -= take_n;
+      __syncwarp();
+      const int ox_i = off_x(e.z), oy_i = off_y(e.z), oz_i = off_z(e.z);
+      const int im[3] = {off_x(e.w), off_y(e.w), off_z(e.w)};
+      const float ox = (float)ox_i * S.hf[0] - si.x;
+      const float oy = (float)oy_i * S.hf[1] - si.y;
+      const float oz = (float)oz_i * S.hf[2] - si.z;
+      const bool self_cell = ox_i == 0 && oy_i == 0 && oz_i == 0;
+      const int maxlen = __reduce_max_sync(0xffffffffu, e.y);
+      for (int k = 0; k < maxlen; ++k) {
+        bool take = false;
+        int j = 0;
+        if (k < e.y) {
+          j = catoms[e.x + k];
+          if (!(j == i && self_cell)) {
+            const float4 sj = s32[j];
+            const float ddx = ox + sj.x, ddy = oy + sj.y, ddz = oz + sj.z;
+            const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
+            if (r2f < rcf2 - band) {
+              take = true;
+            } else if (r2f <= rcf2 + band) {
+              take = exact_within(x, S, i, j, ci, cunw[j], im, rc2);
+            }
           }
         }
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        const int pos = cnt + __popc(m & lt);
+        if (take && pos < cap) {
+          row[pos] = j;
+          if (offrow) offrow[pos] = e.z;
+        }
+        cnt += __popc(m);
       }
-      const unsigned m = __ballot_sync(0xffffffffu, take);
-      const int pos = cnt + __popc(m & lt);
-      if (take && pos < cap) {
-        row[pos] = j;
-        if (offrow) offrow[pos] = pack_off(dx, dy, dz);
-      }
-      cnt += __popc(m);
     }
   }
   return cnt;
@@ -443,13 +462,15 @@ __global__ void __launch_bounds__(256) k_build_ace(const int* __restrict__ queue
                                                    const int* __restrict__ catoms, float rcf2, double rc2,
                                                    float band, int cap, int* __restrict__ nbr, int* __restrict__ off,
                                                    int* __restrict__ cnt, DevScalars* sc, int sten, float margin) {
+  __shared__ int4 s_buf[8][64];   // per warp: the stencil cells queued for the walk
+  const int wib = threadIdx.x >> 5;
   const int m = *nq;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < m; q += warps) {
     const int i = queue[q];
     const SysInfo& S = sys_of(sys, atom_sys, i);
     const int c = build_row_warp(i, x, S, s32, cunw, cstart, catoms, rcf2, rc2, band, cap, nbr + (size_t)q * cap,
-                                 off ? off + (size_t)q * cap : nullptr, sten, margin);
+                                 off ? off + (size_t)q * cap : nullptr, sten, margin, s_buf[wib]);
     if ((threadIdx.x & 31) == 0) {
       cnt[q] = c < cap ? c : cap;
       atomicMax(&sc->ace_row_max, c < cap ? c : cap);
