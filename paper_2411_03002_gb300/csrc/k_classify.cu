@@ -114,6 +114,10 @@ __device__ inline bool entry_less(const double* __restrict__ x, const SysInfo& S
 }
 
 // ------------------------------------------------------------------ CSP
+#ifndef AP_CSP_PREFETCH
+#define AP_CSP_PREFETCH 1   // software-pipelined row walk in the CSP selection (compile-time tuning)
+#endif
+
 // One thread per atom.  All selection arrays are indexed with compile-time
 // indices (fully unrolled insertion), so they live in registers.
 // FAST: every atom, FP32 selections only; an atom whose selection the FP32 values
@@ -155,13 +159,27 @@ __device__ __forceinline__ void csp_atom(int i, const double* __restrict__ x, co
   }
   int n_in = 0;
   int q_end = (FAST && nin) ? nin[i] : c;
+#if AP_CSP_PREFETCH
+  // loads run ahead of the selection: the next entry's shadow and the entry after it
+  int j_a = c > 0 ? nbr[row] : 0;
+  float4 s_a = s32[j_a];
+  int j_b = c > 1 ? nbr[row + 1] : 0;
+#endif
   for (int q = 0; q < c; ++q) {
     if (q == q_end) {   // end of the in-range part (FAST with nin only)
       if (tr[kNN] + 2.f * kBand < rpf2) break;
       q_end = c;
     }
+#if AP_CSP_PREFETCH
+    const int j = j_a;
+    const float4 sj = s_a;
+    j_a = j_b;
+    if (q + 1 < c) s_a = s32[j_a];
+    if (q + 2 < c) j_b = nbr[row + q + 2];
+#else
     const int j = nbr[row + q];
     const float4 sj = s32[j];
+#endif
     int k[3];
     entry_offset(off, row + q, S, ci.w, __float_as_int(sj.w), k);
     const float dx = (float)k[0] * S.hf[0] + sj.x - si.x;
