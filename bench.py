@@ -55,16 +55,15 @@ BASIS_FLOP_PER_ATOM = 7000
 # nu = 3 monomials (~11400).
 ACE_FLOP_PER_PAIR = ADJ_FLOP_PER_PAIR + BASIS_FLOP_PER_PAIR
 ACE_FLOP_PER_ATOM = ADJ_FLOP_PER_ATOM + BASIS_FLOP_PER_ATOM + 11400
-# DRAM bytes (read + write) per launch on this workload, from ncu captures of the
+# DRAM bytes (read + write) per launch on this workload, from an ncu capture of the
 # current kernels on the 500k-atom case (60,000 precise atoms), scaled to 4,000,000 atoms
-# and 240,000 precise atoms (profiles/k_ace_basis_slab50_mixed.md,
-# profiles/k_ace_adjoint_slab50_mixed.md, profiles/k_eam_force_slab50_mixed.md):
-#   k_ace_basis    45.3 MB read + 122.9 MB written (the pair records, 16 B per pair);
-#   k_ace_adjoint  185.6 MB read (mostly the basis kernel's pair records) + 3.8 MB written;
-#   k_eam_force    146.1 MB read + 6.5 MB written.
-ADJ_TRAFFIC_BYTES = 189.4e6 * 240000 / 60000
-BASIS_TRAFFIC_BYTES = 168.2e6 * 240000 / 60000
-EAM_FORCE_TRAFFIC_BYTES = 152.6e6 * 4000000 / 500000
+# and 240,000 precise atoms (profiles/dram_traffic_slab50_mixed.md):
+#   k_ace_basis    51.1 MB read + 120.6 MB written (the pair records, 16 B per pair);
+#   k_ace_adjoint  185.7 MB read (mostly the basis kernel's pair records) + 2.2 MB written;
+#   k_eam_force    146.0 MB read + 8.3 MB written.
+ADJ_TRAFFIC_BYTES = 187.9e6 * 240000 / 60000
+BASIS_TRAFFIC_BYTES = 171.8e6 * 240000 / 60000
+EAM_FORCE_TRAFFIC_BYTES = 154.3e6 * 4000000 / 500000
 # FP32 SIMT peak from unit counts: SMs (read from the device) x 128 FP32 lanes x 2 flop x the
 # maximum SM clock; reported for context beside the measured FFMA peak (ap_probe_peak), which
 # is the denominator of the ALU rooflines.
