@@ -167,11 +167,11 @@ def parse():
     p.add_argument("--mode", default="adaptive", choices=["adaptive", "full-ace", "full-eam"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--no-extras", action="store_true", help="skip full-ACE/full-EAM, error and CPU baseline legs")
-    p.add_argument("--skin", type=float, default=1.0, help="neighbour-list skin (A)")
+    p.add_argument("--skin", type=float, default=0.7, help="neighbour-list skin (A)")
     p.add_argument("--rebuild", default="skin", choices=["lambda", "skin"],
                    help="list rebuilds in the timed run: at every lambda update, or on the skin criterion "
                         "(checked after every drift; a lambda update keeps the lists while no atom has moved "
-                        "more than skin/4)")
+                        "more than 0.45 skin)")
     p.add_argument("--thermostat", action="store_true", help="local thermostat (Appendix C) in the timed run")
     p.add_argument("--deterministic", action="store_true",
                    help="fixed-point ACE force reduction (bitwise reproducible) in the timed run")

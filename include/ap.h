@@ -116,15 +116,16 @@ typedef struct {
                                 AP_REBUILD_SKIN: ap_step reads the largest displacement
                                 since the last build after every drift (a stream sync
                                 per step) and rebuilds when it exceeds skin/2; a lambda
-                                update keeps the lists while it is at most skin/4 and
-                                takes the CSP from them where they decide it (12
+                                update keeps the lists while it is at most 0.45 skin
+                                and takes the CSP from them where they decide it (12
                                 candidates inside r_search - 2 x that displacement; any
                                 atom that fails this makes the update rebuild after
                                 all).  Lambda and the forces equal those of a rebuild
                                 at the update.  Lists are kept only with
                                 AP_DETECT_CSP, without the local thermostat, and when
-                                every periodic dimension of every system holds >= 7
-                                cells or the offsets are stored; otherwise each update
+                                every periodic dimension of every system holds at least
+                                2 ceil((ace_rc + 2.8 skin)/h) + 1 cells (h the cell
+                                edge) or the offsets are stored; otherwise each update
                                 rebuilds (the per-step check stays). */
   /* Detector behind lambda_0 (Appendix B allows any detector whose f_cut argument
    * is 0 for precise and 1 for fast atoms).  AP_DETECT_SELECTOR pushes the

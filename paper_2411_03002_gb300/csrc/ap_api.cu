@@ -82,10 +82,10 @@ ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box
   int base = 0;
   bool stored = false;
   int spread[3] = {0, 0, 0}, spread_stale[3] = {0, 0, 0};
-  // Lists kept past a lambda update (skin criterion) take ACE rows from cells up to skin/4
-  // old and reaching ace_rc + skin + skin/2: pair cell offsets up to
-  // ceil((ace_rc + 2 skin)/h).  Without stored offsets they are recovered from the wrapped
-  // cells, which needs 2 offset + 1 cells in every periodic dimension.
+  // Lists kept past a lambda update (skin criterion) take ACE rows from cells up to
+  // m = kKeepFrac skin old, reaching ace_rc + skin + 2m: pair cell offsets up to
+  // ceil((ace_rc + skin + 4m)/h).  Without stored offsets they are recovered from the
+  // wrapped cells, which needs 2 offset + 1 cells in every periodic dimension.
   bool wide = true;
   for (int s = 0; s < n_sys; ++s) {
     SysInfo& I = sys[s];
@@ -109,7 +109,7 @@ ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box
       int sps = (int)std::ceil((g.r_hi + g.skin) / I.h[d]);   // atoms up to skin/2 from their cells
       if (!I.periodic[d]) sps = std::min(sps, nc);
       spread_stale[d] = std::max(spread_stale[d], sps);
-      const int reach = (int)std::ceil((g.ace_rc + 2.0 * g.skin) / I.h[d]);
+      const int reach = (int)std::ceil((g.ace_rc + (1.0 + 4.0 * kKeepFrac) * g.skin) / I.h[d]);
       if (I.periodic[d] && nc < 2 * reach + 1) wide = false;
     }
     I.cell_base = base;
@@ -945,7 +945,7 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
       // from FP32 shadows (a few 1e-7 A per component): headroom
       m = std::sqrt((double)d2) * (1.0 + 1e-5) + 1e-5;
       build = m > 0.5 * g.skin;
-      keep = lam_step && !build && keep_ok && m <= 0.25 * g.skin;
+      keep = lam_step && !build && keep_ok && m <= kKeepFrac * g.skin;
       build = build || (lam_step && !keep);
     } else {
       const int rb = g.rebuild_every > 0 ? g.rebuild_every : g.lambda_every;

@@ -26,6 +26,14 @@ struct SysInfo {
 };
 
 constexpr int kMaxCellsPerDim = 1023;
+// Skin criterion (rebuild_every = AP_REBUILD_SKIN): a lambda update keeps the lists while
+// the largest displacement since the build is at most this fraction of the skin
+// (compile-time tuning; at most 0.5, the lists' own limit).
+#ifndef AP_KEEP_FRAC
+#define AP_KEEP_FRAC 0.45
+#endif
+constexpr double kKeepFrac = AP_KEEP_FRAC;
+static_assert(kKeepFrac > 0.0 && kKeepFrac <= 0.5, "kept lists need m <= skin/2");
 constexpr int kStencil = 2;          // cell half-width of the EAM and ACE list stencils
 
 // Packed wrapped cell coordinates (10 bits each) carried in the shadow .w.

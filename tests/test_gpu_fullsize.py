@@ -2,10 +2,10 @@
 
 The 4,000,000-atom nanoindentation-shaped slab is prepared and integrated exactly as
 bench.py times it (mixed precision, Hyb2, lambda updated every 10 MD steps, the lists
-on the skin criterion, indenter, fixed bottom layers): ap_step(0) prepares, then
+on the skin criterion with the bench's 0.7 A skin, indenter, fixed bottom layers): ap_step(0) prepares, then
 ap_step runs 10, 10 and 5 MD steps.  The lambda updates at steps 10 and 20 push the
 second and third CSP and lambda_min samples into the 11-sample windows (Eqs. csp_2_i,
-lambda_3_i).  At 300 K no atom moves skin/4 = 0.25 A in 10 fs, so the update at step 10
+lambda_3_i).  At 300 K no atom moves 0.45 skin = 0.315 A in 10 fs, so the update at step 10
 keeps the lists of step 0: its CSP comes from rows 10 steps older than the positions,
 its spread from old cells, and its ACE rows are built from those cells; the forces at
 step 25 are evaluated on rows older still (the EAM force pass walks the prefix the
@@ -22,7 +22,7 @@ give detected atoms (lambda_0 < 1), other atoms with lambda = 0, interior lambda
 lambda = 1; 2 clusters above the fixed bottom layers give mobile and fixed atoms there.
 A classification cluster has radius 45 A around its centre, samples lie within 16 A
 of it: a sample's lambda depends on lambda_0 within r_hi = 20 A, whose CSP depends on
-neighbours within 6.5 A, so 16 + 20 + 6.5 leaves a 2.5 A margin to the cut.  Force
+neighbours within r_c + skin = 6.2 A, so 16 + 20 + 6.2 leaves a 2.8 A margin to the cut.  Force
 clusters have radius 32 A (EAM densities within 2 x 5.5 A, ACE site energies within
 7 A of a sample and their neighbours within 7 A: 16 + 14 A, plus 2 A for the motion
 over 25 steps), with lambda from the GPU (checked above).  Cluster centres keep
@@ -42,6 +42,7 @@ if torch.cuda.is_available():
 
 R_CLASSIFY, R_FORCE, R_SAMPLE = 45.0, 32.0, 16.0
 STEPS = (0, 10, 20, 25)            # MD step after each ap_step call
+SKIN = 0.7                         # the bench's neighbour-list skin (A)
 
 
 def _open_box(xc):
@@ -52,7 +53,7 @@ def _open_box(xc):
 def run():
     w = I.config_c5(100, hyb=I.HYB2)
     cfg = ap.make_config(I.eam_params(0), I.ace_for_config(5), w.hyb, precision=ap.PREC_MIXED, indenter=w.indenter,
-                         lambda_every=10, dt=w.dt, rebuild_every=ap.REBUILD_SKIN)
+                         lambda_every=10, dt=w.dt, skin=SKIN, rebuild_every=ap.REBUILD_SKIN)
     ctx = ap.Context(cfg)
     dev = "cuda"
     x = torch.as_tensor(w.x, device=dev).clone()
@@ -149,7 +150,8 @@ def test_lambda_bit_exact_at_steps_0_10_20(run, plan):
         st = O.LambdaState(len(sel), w.hyb.n_csp_avg, w.hyb.n_lam_avg)
         for step in (0, 10, 20):
             xc = snaps[step]["x"][sel]
-            lam_o, l0_o, csp_o, *_ = O.classify(st, xc, _open_box(xc), w.hyb, changeable=ch)
+            lam_o, l0_o, csp_o, *_ = O.classify(st, xc, _open_box(xc), w.hyb, changeable=ch,
+                                                r_search=I.eam_params(0).rc + SKIN)
             assert np.array_equal(csp_o[pos], snaps[step]["csp"][samples]), step
             assert np.array_equal(l0_o[pos], snaps[step]["lam0"][samples]), step
             assert np.array_equal(lam_o[pos], snaps[step]["lam"][samples]), step

@@ -2,7 +2,7 @@
 
 The lists are checked after every drift and rebuilt when an atom has moved more than
 skin/2 since the last build; a lambda update keeps them while no atom has moved more
-than skin/4, takes the CSP from the kept rows where they decide it and builds the new
+than 0.45 skin, takes the CSP from the kept rows where they decide it and builds the new
 ACE rows from the kept cells.  Every force and every lambda must be those of a run that
 rebuilds at each update:
 
