@@ -456,6 +456,9 @@ constexpr int kSpreadWarps = 8;
 #define AP_SPREAD_UNROLL 1   // unroll depth of the per-lane candidate loop (compile-time tuning)
 #endif
 constexpr int kSpreadUnroll = AP_SPREAD_UNROLL;
+#ifndef AP_SPREAD_QUEUE
+#define AP_SPREAD_QUEUE 1   // walk only the cells that can reach r_hi, 32 at a time (compile-time tuning)
+#endif
 
 __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
     const int* __restrict__ det, const int* __restrict__ n_det, const double* __restrict__ x,
@@ -465,7 +468,9 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
     int sy, int sz, double* __restrict__ lam_min, float margin) {
   // per warp: inclusive prefix of candidate counts, first catoms slot, stencil offset
   __shared__ int s_pre[kSpreadWarps][32], s_beg[kSpreadWarps][32], s_t[kSpreadWarps][32], s_img[kSpreadWarps][32];
+  __shared__ int4 s_q[kSpreadWarps][64];   // per warp: queued cells (first slot, count, stencil index, image)
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const int m = *n_det;
   const double rh2 = __dmul_rn(r_hi, r_hi);
@@ -484,36 +489,8 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
     const double one_minus = __dsub_rn(1.0, lam0[i]);
     const float one_minus_f = (float)one_minus;
     const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
-    for (int t0 = 0; t0 < ncell; t0 += 32) {
-      // this lane's cell of the chunk: kept if it exists and can reach r_hi
-      const int t = t0 + lane;
-      int cnt = 0, beg = 0, imgp = 0;
-      if (t < ncell) {
-        const int dx = t % wx - sx, dy = (t / wx) % wy - sy, dz = t / (wx * wy) - sz;
-        int tc[3] = {cw[0] + dx, cw[1] + dy, cw[2] + dz};
-        int img[3] = {0, 0, 0};
-        bool skip = false;
-        for (int a = 0; a < 3; ++a) {
-          if (S.periodic[a]) {
-            img[a] = floor_div(tc[a], S.nc[a]);
-            tc[a] -= img[a] * S.nc[a];
-          } else if (tc[a] < 0 || tc[a] >= S.nc[a]) {
-            skip = true;
-          }
-        }
-        if (!skip) {
-          const float gx = fmaxf(0.f, fmaxf((float)dx * S.hf[0] - si.x, si.x - (float)(dx + 1) * S.hf[0]));
-          const float gy = fmaxf(0.f, fmaxf((float)dy * S.hf[1] - si.y, si.y - (float)(dy + 1) * S.hf[1]));
-          const float gz = fmaxf(0.f, fmaxf((float)dz * S.hf[2] - si.z, si.z - (float)(dz + 1) * S.hf[2]));
-          if (gx * gx + gy * gy + gz * gz <= prune2 + kBand) {
-            const int cid = S.cell_base + (tc[2] * S.nc[1] + tc[1]) * S.nc[0] + tc[0];
-            beg = cstart[cid];
-            cnt = cstart[cid + 1] - beg;
-            // periodic image of the cell, 8 bits per component biased by 128
-            imgp = pack_off(img[0], img[1], img[2]);
-          }
-        }
-      }
+    // the scan of a batch of cells' atom counts and the stream of their candidates
+    auto walk = [&](int cnt, int beg, int t, int imgp) {
       int pre = cnt;   // inclusive warp scan of the counts
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -578,6 +555,57 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
         atomicMin((unsigned long long*)&lam_min[j], (unsigned long long)__double_as_longlong(v));
       }
       __syncwarp();
+    };
+    int queued = 0;
+    for (int t0 = 0; t0 < ncell; t0 += 32) {
+      // this lane's cell of the chunk: kept if it exists and can reach r_hi
+      const int t = t0 + lane;
+      int cnt = 0, beg = 0, imgp = 0;
+      if (t < ncell) {
+        const int dx = t % wx - sx, dy = (t / wx) % wy - sy, dz = t / (wx * wy) - sz;
+        int tc[3] = {cw[0] + dx, cw[1] + dy, cw[2] + dz};
+        int img[3] = {0, 0, 0};
+        bool skip = false;
+        for (int a = 0; a < 3; ++a) {
+          if (S.periodic[a]) {
+            img[a] = floor_div(tc[a], S.nc[a]);
+            tc[a] -= img[a] * S.nc[a];
+          } else if (tc[a] < 0 || tc[a] >= S.nc[a]) {
+            skip = true;
+          }
+        }
+        if (!skip) {
+          const float gx = fmaxf(0.f, fmaxf((float)dx * S.hf[0] - si.x, si.x - (float)(dx + 1) * S.hf[0]));
+          const float gy = fmaxf(0.f, fmaxf((float)dy * S.hf[1] - si.y, si.y - (float)(dy + 1) * S.hf[1]));
+          const float gz = fmaxf(0.f, fmaxf((float)dz * S.hf[2] - si.z, si.z - (float)(dz + 1) * S.hf[2]));
+          if (gx * gx + gy * gy + gz * gz <= prune2 + kBand) {
+            const int cid = S.cell_base + (tc[2] * S.nc[1] + tc[1]) * S.nc[0] + tc[0];
+            beg = cstart[cid];
+            cnt = cstart[cid + 1] - beg;
+            // periodic image of the cell, 8 bits per component biased by 128
+            imgp = pack_off(img[0], img[1], img[2]);
+          }
+        }
+      }
+#if AP_SPREAD_QUEUE
+      // queue the cells that can reach r_hi; walk them 32 at a time
+      const unsigned vm = __ballot_sync(0xffffffffu, cnt > 0);
+      if (cnt > 0) s_q[wib][queued + __popc(vm & lt)] = make_int4(beg, cnt, t, imgp);
+      queued += __popc(vm);
+      __syncwarp();
+      const bool last = t0 + 32 >= ncell;
+      while (queued >= 32 || (last && queued > 0)) {
+        const int take_n = queued < 32 ? queued : 32;
+        const int4 e = lane < take_n ? s_q[wib][lane] : make_int4(0, 0, 0, 0);
+        __syncwarp();
+        if (lane + 32 < queued) s_q[wib][lane] = s_q[wib][lane + 32];
+        queued -= take_n;
+        __syncwarp();
+        walk(e.y, e.x, e.z, e.w);
+      }
+#else
+      walk(cnt, beg, t, imgp);
+#endif
     }
   }
 }
