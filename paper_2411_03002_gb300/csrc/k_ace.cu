@@ -738,18 +738,41 @@ __global__ void __launch_bounds__(kWarps<R> * 32, sizeof(R) == 4 ? AP_ACE_MINB :
 // Finnis-Sinclair form (FS): a first pass gives the nu = 3 part of phi^(2), hence
 // phi^(2), F and F'; the gradient pass then uses the coefficients c1 + F' c2, and
 // E3 of phi^(1) is E3(c1 + F' c2) - F' E3(c2).
+#ifndef AP_NU3_MINB
+#define AP_NU3_MINB 0   // FP32: resident 128-thread blocks per SM the nu = 3 kernel is compiled for (0: no bound)
+#endif
+#if AP_NU3_MINB > 0
+#define AP_NU3_BOUNDS __launch_bounds__(sizeof(R) == 4 ? 128 : 64, sizeof(R) == 4 ? AP_NU3_MINB : 1)
+#else
+#define AP_NU3_BOUNDS __launch_bounds__(sizeof(R) == 4 ? 128 : 64)
+#endif
+#ifndef AP_NU3_VEC
+#define AP_NU3_VEC 1    // 4-wide loads of A and stores of dE3/dA
+#endif
 template <typename R, bool FS>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? 128 : 64) k_ace_nu3(AceArgs<R> a, const Nu3Coef<R> P,
+__global__ void AP_NU3_BOUNDS k_ace_nu3(AceArgs<R> a, const Nu3Coef<R> P,
                                                                        const Nu3Coef<R> Q) {
   const int m = *a.count;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
     R A[48], dA[48];
+#if AP_NU3_VEC
+    // 4-wide loads (the rows of a48 are 48 entries, a multiple of 4)
+    const auto* src = reinterpret_cast<const typename V<R>::R4*>(a.a48 + (size_t)q * 48);
+#pragma unroll
+    for (int v = 0; v < 12; ++v) {
+      const auto t = src[v];
+      A[4 * v] = t.x;
+      A[4 * v + 1] = t.y;
+      A[4 * v + 2] = t.z;
+      A[4 * v + 3] = t.w;
+    }
+#else
     const R* src = a.a48 + (size_t)q * 48;
 #pragma unroll
-    for (int v = 0; v < 48; ++v) {
-      A[v] = src[v];
-      dA[v] = R(0);
-    }
+    for (int v = 0; v < 48; ++v) A[v] = src[v];
+#endif
+#pragma unroll
+    for (int v = 0; v < 48; ++v) dA[v] = R(0);
     R fp = R(0);
     double e3b = 0.0, Fv = 0.0;
     if constexpr (FS) {
@@ -790,12 +813,17 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 128 : 64) k_ace_nu3(AceArgs<R
 #undef NU3_TERM
 #undef NU3_GROUP_END
     R e = R(0);
+#pragma unroll
+    for (int v = 0; v < 48; ++v) e = fma(A[v], dA[v], e);
+#if AP_NU3_VEC
+    auto* dst = reinterpret_cast<typename V<R>::R4*>(a.de3 + (size_t)q * 48);
+#pragma unroll
+    for (int v = 0; v < 12; ++v) dst[v] = make_r4(dA[4 * v], dA[4 * v + 1], dA[4 * v + 2], dA[4 * v + 3]);
+#else
     R* dst = a.de3 + (size_t)q * 48;
 #pragma unroll
-    for (int v = 0; v < 48; ++v) {
-      e = fma(A[v], dA[v], e);
-      dst[v] = dA[v];
-    }
+    for (int v = 0; v < 48; ++v) dst[v] = dA[v];
+#endif
     a.e3[q] = (double)e * (1.0 / 3.0) - (FS ? (double)fp * e3b : 0.0);
     if (FS) {
       a.fs[2 * (size_t)q] = Fv;
