@@ -79,6 +79,7 @@ ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box
   double rlist = std::max(g.eam_rc, g.ace_rc) + g.skin;
   double htarget = rlist / kStencil;
   std::vector<SysInfo> sys(n_sys);
+  std::vector<double> org;
   int base = 0;
   bool stored = false;
   int spread[3] = {0, 0, 0}, spread_stale[3] = {0, 0, 0};
@@ -114,6 +115,10 @@ ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box
     }
     I.cell_base = base;
     base += I.nc[0] * I.nc[1] * I.nc[2];
+    for (int d = 0; d < 3; ++d) {   // the cell origins lo + c h of the shadows
+      I.org[d] = (int)org.size();
+      for (int k = 0; k < I.nc[d]; ++k) org.push_back(std::fma((double)k, I.h[d], I.lo[d]));
+    }
   }
   bool same = (n_sys == c->n_sys) && c->h_offsets.size() == (size_t)n_sys + 1 &&
               std::equal(offsets, offsets + n_sys + 1, c->h_offsets.begin()) &&
@@ -131,6 +136,8 @@ ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box
   c->stale_ok = stored || wide;
   CK(dalloc(c->d_sys, n_sys));
   CK(cudaMemcpy(c->d_sys, sys.data(), sizeof(SysInfo) * n_sys, cudaMemcpyHostToDevice));
+  CK(dalloc(c->d_org, org.size()));
+  CK(cudaMemcpy(c->d_org, org.data(), sizeof(double) * org.size(), cudaMemcpyHostToDevice));
   dfree(c->d_atom_sys);
   int64_t n = offsets[n_sys];
   if (n_sys > 1 && n > 0) {
@@ -619,7 +626,7 @@ void ap_destroy(ap_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   void* ptrs[] = {c->d_sys, c->d_atom_sys, c->d_cell, c->d_cunw, c->d_cell_start, c->d_cell_count, c->d_cell_atoms,
-                  c->d_slot, c->d_sh32, c->d_sh32c, c->d_sh64, c->d_sh32b, c->d_vscale, c->d_nbr_eam, c->d_off_eam, c->d_cnt_eam,
+                  c->d_slot, c->d_sh32, c->d_sh32c, c->d_sh64, c->d_sh32b, c->d_org, c->d_vscale, c->d_nbr_eam, c->d_off_eam, c->d_cnt_eam,
                   c->d_lim_eam, c->d_split_eam, c->d_nbr_ace, c->d_off_ace, c->d_cnt_ace, c->d_csp, c->d_csp_slow, c->d_csp_avg, c->d_lam0, c->d_lam_min,
                   c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected,
                   c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_faccfix, c->d_efast, c->d_eprec,

@@ -22,7 +22,7 @@ struct SysInfo {
   int nc[3];         // cells per dimension (<= 1023)
   int periodic[3];
   int cell_base;     // first global cell id of this system
-  int pad;
+  int org[3];        // offsets of this system's cell origins lo + c h in the origin table, per dimension
 };
 
 constexpr int kMaxCellsPerDim = 1023;
@@ -43,12 +43,20 @@ __host__ __device__ inline int cell_y(int c) { return (c >> 10) & 1023; }
 __host__ __device__ inline int cell_z(int c) { return (c >> 20) & 1023; }
 
 #ifdef __CUDACC__
-// Cell-relative shadow s = (x - lo) - c h of a position in its unwrapped cell c, with one
-// rounding for the product and the difference (FP64; the FP32 shadow rounds s).
-__device__ inline void cell_shadow(const SysInfo& S, const int4& c, const double x[3], double s[3]) {
-  s[0] = fma(-(double)c.x, S.h[0], x[0] - S.lo[0]);
-  s[1] = fma(-(double)c.y, S.h[1], x[1] - S.lo[1]);
-  s[2] = fma(-(double)c.z, S.h[2], x[2] - S.lo[2]);
+// Cell-relative shadow s = x - o of a position in its unwrapped cell c, o = lo + c h the
+// cell's origin (FP64; the FP32 shadow rounds s).  The origins of the wrapped cells come
+// from a table (org, offsets S.org), so a shadow costs one FP64 subtraction per
+// component, FP64 arithmetic being slow on this GPU; an unwrapped cell adds whole periods.
+__device__ inline void cell_shadow(const SysInfo& S, const double* __restrict__ org, const int4& c,
+                                   const double x[3], double s[3]) {
+  const int cw[3] = {c.w & 1023, (c.w >> 10) & 1023, (c.w >> 20) & 1023};
+  const int cu[3] = {c.x, c.y, c.z};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double v = x[d] - org[S.org[d] + cw[d]];
+    if (cu[d] != cw[d]) v -= (double)((cu[d] - cw[d]) / S.nc[d]) * S.L[d];
+    s[d] = v;
+  }
 }
 #endif
 
@@ -201,6 +209,7 @@ struct ap_ctx {
   float4* d_sh32c = nullptr;     // the same in cell order (the EAM row build's candidate stream)
   double4_32a* d_sh64 = nullptr;     // FP64 cell-relative shadow
   float4* d_sh32b = nullptr;     // [n] the FP32 shadows at the last build (displacement check)
+  double* d_org = nullptr;       // cell origins lo + c h of every system and dimension (SysInfo::org)
   double* d_vscale = nullptr;    // [n] 0.5 dt ACC / m_i of the current ap_step call
   int* d_nbr_eam = nullptr;      // [n][cap_eam]
   int* d_off_eam = nullptr;      // [n][cap_eam] (stored offsets only)

@@ -26,7 +26,8 @@ __global__ void k_vscale(int n, const double* __restrict__ mass, double dt, doub
 __global__ void k_vv_first(int n, double* __restrict__ x, double* __restrict__ v, const double* __restrict__ f,
                            const double* __restrict__ vs, const uint8_t* __restrict__ fixed, double dt,
                            const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
-                           const int4* __restrict__ cunw, float4* __restrict__ s32, double4_32a* __restrict__ s64,
+                           const double* __restrict__ org, const int4* __restrict__ cunw, float4* __restrict__ s32,
+                           double4_32a* __restrict__ s64,
                            const float4* __restrict__ s32b, DevScalars* sc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   float d2 = 0.f;
@@ -44,14 +45,14 @@ __global__ void k_vv_first(int n, double* __restrict__ x, double* __restrict__ v
         xx[a] = x[3 * i + a] + dt * vv;
         v[3 * i + a] = vv;
         x[3 * i + a] = xx[a];
-        bad |= !isfinite(xx[a]);
+        bad |= (__double2hiint(xx[a]) & 0x7ff00000) == 0x7ff00000;   // inf or nan (exponent bits)
       }
       if (bad) atomicOr(&sc->err, kErrNonfinite);
     }
     const SysInfo& S = sys[atom_sys ? atom_sys[i] : 0];
     const int4 c = cunw[i];
     double sh[3];
-    cell_shadow(S, c, xx, sh);
+    cell_shadow(S, org, c, xx, sh);
     const float4 s4 = make_float4((float)sh[0], (float)sh[1], (float)sh[2], __int_as_float(c.w));
     s32[i] = s4;
     if (s64) s64[i] = make_double4_32a(sh[0], sh[1], sh[2], (double)c.w);
@@ -168,7 +169,7 @@ void launch_vv_first(ap_ctx* c, double* d_x, double* d_v, const double* d_f, con
                      const uint8_t* d_fixed, cudaStream_t s) {
   (void)d_mass;   // the half-kick factors come from launch_vscale
   k_vv_first<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, d_v, d_f, c->d_vscale, d_fixed, c->cfg.dt, c->d_sys,
-                                             c->d_atom_sys, c->d_cunw, c->d_sh32,
+                                             c->d_atom_sys, c->d_org, c->d_cunw, c->d_sh32,
                                              c->cfg.precision == AP_PREC_FP64 ? c->d_sh64 : nullptr, c->d_sh32b,
                                              c->d_sc);
   c->kernels += 1;

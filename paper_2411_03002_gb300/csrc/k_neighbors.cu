@@ -148,15 +148,15 @@ __global__ void k_cell_sort(int n_cells, const int* __restrict__ start, int* __r
 
 // Cell-relative coordinates s = (x - lo) - c_unw h; w = packed wrapped cell.
 __global__ void k_shadow(int n, const double* __restrict__ x, const SysInfo* __restrict__ sys,
-                         const int* __restrict__ atom_sys, const int4* __restrict__ cunw, float4* __restrict__ s32,
-                         double4_32a* __restrict__ s64) {
+                         const int* __restrict__ atom_sys, const double* __restrict__ org,
+                         const int4* __restrict__ cunw, float4* __restrict__ s32, double4_32a* __restrict__ s64) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const SysInfo& S = sys_of(sys, atom_sys, i);
   const int4 c = cunw[i];
   const double xi[3] = {x[3 * i + 0], x[3 * i + 1], x[3 * i + 2]};
   double sh[3];
-  cell_shadow(S, c, xi, sh);
+  cell_shadow(S, org, c, xi, sh);
   s32[i] = make_float4((float)sh[0], (float)sh[1], (float)sh[2], __int_as_float(c.w));
   if (s64) s64[i] = make_double4_32a(sh[0], sh[1], sh[2], (double)c.w);
 }
@@ -548,7 +548,7 @@ void launch_cell_sort(ap_ctx* c, cudaStream_t s) {
 }
 
 void launch_shadow(ap_ctx* c, const double* d_x, cudaStream_t s) {
-  k_shadow<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, c->d_sys, c->d_atom_sys, c->d_cunw, c->d_sh32,
+  k_shadow<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, c->d_sys, c->d_atom_sys, c->d_org, c->d_cunw, c->d_sh32,
                                            c->cfg.precision == AP_PREC_FP64 ? c->d_sh64 : nullptr);
   c->kernels += 1;
 }
