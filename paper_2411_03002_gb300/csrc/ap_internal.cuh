@@ -239,6 +239,7 @@ struct ap_ctx {
   int* d_flag = nullptr;         // [n] compaction flags
   int* d_scan = nullptr;         // [n + 1] scan output
   int* d_detected = nullptr;     // [n] detected queue
+  float* d_vmin_f = nullptr;     // [n] FP32 minima of the lambda spread's first pass
   int* d_precise = nullptr;      // [n] internal precise queue
   double* d_lam_int = nullptr;   // [n] internal lambda (ap_step)
 

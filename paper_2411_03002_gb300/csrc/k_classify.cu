@@ -62,7 +62,10 @@ __device__ inline void exact_disp(const double* __restrict__ x, const SysInfo& S
                                   const int4& cj, const int k[3], double d[3]) {
   int cu_i[3] = {ci.x, ci.y, ci.z}, cu_j[3] = {cj.x, cj.y, cj.z};
   for (int a = 0; a < 3; ++a) {
-    int sd = S.periodic[a] ? (k[a] - (cu_j[a] - cu_i[a])) / S.nc[a] : 0;
+    // whole periods between the pair's cell offset and its unwrapped cells (the integer
+    // division only where they differ)
+    const int t = k[a] - (cu_j[a] - cu_i[a]);
+    const int sd = (S.periodic[a] && t != 0) ? t / S.nc[a] : 0;
     // x_j + 0 L is x_j exactly: the FP64 multiply-add (slow on this GPU) only for images
     double shifted = sd == 0 ? x[3 * j + a] : __dadd_rn(x[3 * j + a], __dmul_rn((double)sd, S.L[a]));
     d[a] = __dsub_rn(shifted, x[3 * i + a]);
@@ -84,7 +87,10 @@ __device__ inline bool cand_less(double ra, int ja, const int* sa, double rb, in
 
 __device__ inline void image_of(const SysInfo& S, const int4& ci, const int4& cj, const int k[3], int s[3]) {
   int cu_i[3] = {ci.x, ci.y, ci.z}, cu_j[3] = {cj.x, cj.y, cj.z};
-  for (int a = 0; a < 3; ++a) s[a] = S.periodic[a] ? (k[a] - (cu_j[a] - cu_i[a])) / S.nc[a] : 0;
+  for (int a = 0; a < 3; ++a) {
+    const int t = k[a] - (cu_j[a] - cu_i[a]);
+    s[a] = (S.periodic[a] && t != 0) ? t / S.nc[a] : 0;
+  }
 }
 
 // Row position q of atom i's entry -> exact FP64 displacement.
@@ -460,12 +466,20 @@ constexpr int kSpreadUnroll = AP_SPREAD_UNROLL;
 #define AP_SPREAD_QUEUE 1   // walk only the cells that can reach r_hi, 32 at a time (compile-time tuning)
 #endif
 
+// Two passes over the same candidates.  PHASE 0 (FP32 only): vmin_f[j] = the smallest
+// FP32 estimate over the pairs surely inside r_hi (by more than the guard band).  PHASE 1:
+// the exact FP64 value of a pair only where it can set the final minimum: its estimate
+// (error < 1e-5) lies within 1e-4 of vmin_f[j] or the pair lies in the band around r_hi
+// (only then can it be inside while no surely-inside pair is), and it can still go below
+// the current lambda_min,j.  Exact evaluations (FP64 is slow on this GPU) then drop from
+// one per new running minimum to about one per atom.
+template <int PHASE>
 __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
     const int* __restrict__ det, const int* __restrict__ n_det, const double* __restrict__ x,
     const uint8_t* __restrict__ ch, const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
     const float4* __restrict__ s32, const int4* __restrict__ cunw, const int* __restrict__ cstart,
     const int* __restrict__ catoms, const double* __restrict__ lam0, double r_lo, double r_hi, int mode, int sx,
-    int sy, int sz, double* __restrict__ lam_min, float margin) {
+    int sy, int sz, double* __restrict__ lam_min, float margin, float* __restrict__ vmin_f) {
   // per warp: inclusive prefix of candidate counts, first catoms slot, stencil offset
   __shared__ int s_pre[kSpreadWarps][32], s_beg[kSpreadWarps][32], s_t[kSpreadWarps][32], s_img[kSpreadWarps][32];
   __shared__ int4 s_q[kSpreadWarps][64];   // per warp: queued cells (first slot, count, stencil index, image)
@@ -528,13 +542,18 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
         const float ddx = ox + sj.x, ddy = oy + sj.y, ddz = oz + sj.z;
         const float r2f = ddx * ddx + ddy * ddy + ddz * ddz;
         if (r2f > rhf2 + kBand) continue;
-        // FP32 estimate of the candidate value (error < 1e-5): if even its lower
-        // bound cannot go below the current lambda_min,j (which only decreases),
-        // the exact evaluation cannot change the final minimum; skip it.
-        {
-          const float vf = 1.f - one_minus_f * fcut_f((sqrtf(r2f) - r_lo_f) * inv_w_f, mode);
-          if ((double)vf - 1e-4 >= __ldcg(&lam_min[j])) continue;
+        // FP32 estimate of the candidate value (error < 1e-5)
+        const float vf = fmaxf(0.f, 1.f - one_minus_f * fcut_f((sqrtf(r2f) - r_lo_f) * inv_w_f, mode));
+        const bool inside = r2f < rhf2 - kBand;
+        if constexpr (PHASE == 0) {
+          if (inside && vf < __ldcg(&vmin_f[j])) atomicMin((unsigned int*)&vmin_f[j], __float_as_uint(vf));
+          continue;
         }
+        // if even its lower bound cannot go below the current lambda_min,j (which only
+        // decreases), or a surely-inside pair's estimate lies above the smallest one by
+        // more than twice the error, the exact value cannot be the final minimum
+        if ((double)vf - 1e-4 >= __ldcg(&lam_min[j])) continue;
+        if (inside && vf > __ldcg(&vmin_f[j]) + 1e-4f) continue;
         const int img[3] = {off_x(ip), off_y(ip), off_z(ip)};
         const int4 cj = cunw[j];
         double d[3];
@@ -688,10 +707,19 @@ void launch_spread(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream
   int grid = c->num_sms * 8;
   const int* st = c->cells_stale ? c->sten_spread_stale : c->sten_spread;
   const float margin = c->cells_stale ? (float)c->stale_m : 0.f;
-  k_spread<<<grid, kSpreadWarps * 32, 0, s>>>(c->d_detected, &c->d_sc->n_detected, d_x, d_ch, c->d_sys, c->d_atom_sys, c->d_sh32,
-                                c->d_cunw, c->d_cell_start, c->d_cell_atoms, c->d_lam0, c->cfg.r_lo, c->cfg.r_hi,
-                                c->cfg.fcut_mode, st[0], st[1], st[2], c->d_lam_min, margin);
-  c->kernels += 1;
+  // +3.4e38 in every float: the FP32 minima start above any estimate
+  cudaMemsetAsync(c->d_vmin_f, 0x7f, sizeof(float) * (size_t)c->n, s);
+  k_spread<0><<<grid, kSpreadWarps * 32, 0, s>>>(c->d_detected, &c->d_sc->n_detected, d_x, d_ch, c->d_sys,
+                                                 c->d_atom_sys, c->d_sh32, c->d_cunw, c->d_cell_start,
+                                                 c->d_cell_atoms, c->d_lam0, c->cfg.r_lo, c->cfg.r_hi,
+                                                 c->cfg.fcut_mode, st[0], st[1], st[2], c->d_lam_min, margin,
+                                                 c->d_vmin_f);
+  k_spread<1><<<grid, kSpreadWarps * 32, 0, s>>>(c->d_detected, &c->d_sc->n_detected, d_x, d_ch, c->d_sys,
+                                                 c->d_atom_sys, c->d_sh32, c->d_cunw, c->d_cell_start,
+                                                 c->d_cell_atoms, c->d_lam0, c->cfg.r_lo, c->cfg.r_hi,
+                                                 c->cfg.fcut_mode, st[0], st[1], st[2], c->d_lam_min, margin,
+                                                 c->d_vmin_f);
+  c->kernels += 2;
 }
 
 void launch_lambda_final(ap_ctx* c, const uint8_t* d_ch, double* d_lam, int* d_queue, int64_t* d_nq64,
