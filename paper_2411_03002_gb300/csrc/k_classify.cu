@@ -458,6 +458,30 @@ __global__ void k_compact(int n, const int* __restrict__ flag, const int* __rest
 // lanes share out (lane k takes candidates k, k + 32, ...; its cell is found by a
 // binary search over the 32 prefix sums), so lanes stay busy whatever the cells hold.
 constexpr int kSpreadWarps = 8;
+
+// The exact value 1 - (1 - lambda_0,i) f_cut((r_ij - r_lo)/(r_hi - r_lo)) of pair (i, j),
+// j in the stencil cell of periodic image img relative to i's wrapped cell cw_i; false if
+// r_ij >= r_hi.  Image relative to the input positions: s = img + nwrap_i - nwrap_j.
+__device__ inline bool spread_value(const double* __restrict__ x, const SysInfo& S, int i, int j, const int4& ci,
+                                    const int4& cj, const int img[3], double rh2, double r_lo, double width,
+                                    double one_minus, int mode, double& v) {
+  const int cwi[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
+  const int cwj[3] = {cell_x(cj.w), cell_y(cj.w), cell_z(cj.w)};
+  const int cu_i[3] = {ci.x, ci.y, ci.z}, cu_j[3] = {cj.x, cj.y, cj.z};
+  double d[3];
+  for (int q = 0; q < 3; ++q) {
+    int sd = 0;
+    if (S.periodic[q]) sd = img[q] + (cu_i[q] - cwi[q]) / S.nc[q] - (cu_j[q] - cwj[q]) / S.nc[q];
+    const double shifted = sd == 0 ? x[3 * j + q] : __dadd_rn(x[3 * j + q], __dmul_rn((double)sd, S.L[q]));
+    d[q] = __dsub_rn(shifted, x[3 * i + q]);
+  }
+  const double r2 = norm2_exact(d);
+  if (!(r2 < rh2)) return false;
+  const double r = __dsqrt_rn(r2);
+  const double f = fcut_exact(__ddiv_rn(__dsub_rn(r, r_lo), width), mode);
+  v = __dsub_rn(1.0, __dmul_rn(one_minus, f));
+  return true;
+}
 #ifndef AP_SPREAD_UNROLL
 #define AP_SPREAD_UNROLL 1   // unroll depth of the per-lane candidate loop (compile-time tuning)
 #endif
@@ -466,13 +490,14 @@ constexpr int kSpreadUnroll = AP_SPREAD_UNROLL;
 #define AP_SPREAD_QUEUE 1   // walk only the cells that can reach r_hi, 32 at a time (compile-time tuning)
 #endif
 
-// Two passes over the same candidates.  PHASE 0 (FP32 only): vmin_f[j] = the smallest
-// FP32 estimate over the pairs surely inside r_hi (by more than the guard band).  PHASE 1:
-// the exact FP64 value of a pair only where it can set the final minimum: its estimate
-// (error < 1e-5) lies within 1e-4 of vmin_f[j] or the pair lies in the band around r_hi
-// (only then can it be inside while no surely-inside pair is), and it can still go below
-// the current lambda_min,j.  Exact evaluations (FP64 is slow on this GPU) then drop from
-// one per new running minimum to about one per atom.
+// Two passes over the same candidates, since FP64 is slow on this GPU.  PHASE 0 (FP32): a
+// pair surely inside r_lo has f_cut = 1, so its exact value 1 - (1 - lambda_0,i) needs no
+// distance and goes straight into lambda_min,j; vmin_f[j] = the smallest FP32 estimate
+// (error < 1e-5) over the pairs surely inside r_hi.  PHASE 1: the exact value of the other
+// pairs only where it can set the final minimum: the estimate can go below the current
+// lambda_min,j and, for a pair surely inside r_hi, lies within 1e-4 of vmin_f[j] (a pair in
+// the guard band around r_hi is always evaluated).  Without the first pass every new
+// running minimum, and every pair inside r_lo (they tie), took an exact value.
 template <int PHASE>
 __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
     const int* __restrict__ det, const int* __restrict__ n_det, const double* __restrict__ x,
@@ -489,6 +514,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
   const int m = *n_det;
   const double rh2 = __dmul_rn(r_hi, r_hi);
   const float rhf2 = (float)rh2;
+  const float rlo2f = (float)__dmul_rn(r_lo, r_lo);
   // cells older than the positions (atoms up to `margin` from their cells): prune beyond r_hi + margin
   const float rprune = (float)r_hi + margin, prune2 = rprune * rprune;
   const double width = __dsub_rn(r_hi, r_lo);
@@ -502,6 +528,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
     const int4 ci = cunw[i];
     const double one_minus = __dsub_rn(1.0, lam0[i]);
     const float one_minus_f = (float)one_minus;
+    const double v_in = __dsub_rn(1.0, __dmul_rn(one_minus, 1.0));   // the value of a pair inside r_lo
     const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
     // the scan of a batch of cells' atom counts and the stream of their candidates
     auto walk = [&](int cnt, int beg, int t, int imgp) {
@@ -546,31 +573,27 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
         const float vf = fmaxf(0.f, 1.f - one_minus_f * fcut_f((sqrtf(r2f) - r_lo_f) * inv_w_f, mode));
         const bool inside = r2f < rhf2 - kBand;
         if constexpr (PHASE == 0) {
+          // a pair that cannot go below the current lambda_min,j (which only decreases) is never the minimum
+          if ((double)vf - 1e-4 >= __ldcg(&lam_min[j])) continue;
+          if (r2f < rlo2f - kBand) {
+            // surely inside r_lo: f_cut = 1, and the exact value 1 - (1 - lambda_0,i) needs no distance
+            if (v_in < __ldcg(&lam_min[j]))
+              atomicMin((unsigned long long*)&lam_min[j], (unsigned long long)__double_as_longlong(v_in));
+            if (vf < __ldcg(&vmin_f[j])) atomicMin((unsigned int*)&vmin_f[j], __float_as_uint(vf));
+            continue;
+          }
           if (inside && vf < __ldcg(&vmin_f[j])) atomicMin((unsigned int*)&vmin_f[j], __float_as_uint(vf));
           continue;
         }
+        if (r2f < rlo2f - kBand) continue;   // applied by the first pass
         // if even its lower bound cannot go below the current lambda_min,j (which only
         // decreases), or a surely-inside pair's estimate lies above the smallest one by
         // more than twice the error, the exact value cannot be the final minimum
         if ((double)vf - 1e-4 >= __ldcg(&lam_min[j])) continue;
         if (inside && vf > __ldcg(&vmin_f[j]) + 1e-4f) continue;
         const int img[3] = {off_x(ip), off_y(ip), off_z(ip)};
-        const int4 cj = cunw[j];
-        double d[3];
-        // image relative to the input positions: S = img + nwrap_i - nwrap_j
-        const int cu_i[3] = {ci.x, ci.y, ci.z}, cu_j[3] = {cj.x, cj.y, cj.z};
-        const int cwj[3] = {cell_x(cj.w), cell_y(cj.w), cell_z(cj.w)};
-        for (int q = 0; q < 3; ++q) {
-          int sd = 0;
-          if (S.periodic[q]) sd = img[q] + (cu_i[q] - cw[q]) / S.nc[q] - (cu_j[q] - cwj[q]) / S.nc[q];
-          const double shifted = sd == 0 ? x[3 * j + q] : __dadd_rn(x[3 * j + q], __dmul_rn((double)sd, S.L[q]));
-          d[q] = __dsub_rn(shifted, x[3 * i + q]);
-        }
-        const double r2 = norm2_exact(d);
-        if (!(r2 < rh2)) continue;
-        const double r = __dsqrt_rn(r2);
-        const double f = fcut_exact(__ddiv_rn(__dsub_rn(r, r_lo), width), mode);
-        const double v = __dsub_rn(1.0, __dmul_rn(one_minus, f));
+        double v;
+        if (!spread_value(x, S, i, j, ci, cunw[j], img, rh2, r_lo, width, one_minus, mode, v)) continue;
         atomicMin((unsigned long long*)&lam_min[j], (unsigned long long)__double_as_longlong(v));
       }
       __syncwarp();
