@@ -253,6 +253,7 @@ ap_status ensure_capacity(ap_ctx* c, int64_t n) {
   CK(dalloc(c->d_scan, m + 1));
   CK(dalloc(c->d_detected, m));
   CK(dalloc(c->d_vmin_f, m));
+  CK(dalloc(c->d_det1, m));
   CK(dalloc(c->d_precise, m));
   CK(dalloc(c->d_lam_int, m));
   void* q = c->d_q;
@@ -629,7 +630,7 @@ void ap_destroy(ap_ctx* c) {
   void* ptrs[] = {c->d_sys, c->d_atom_sys, c->d_cell, c->d_cunw, c->d_cell_start, c->d_cell_count, c->d_cell_atoms,
                   c->d_slot, c->d_sh32, c->d_sh32c, c->d_sh64, c->d_sh32b, c->d_org, c->d_vscale, c->d_nbr_eam, c->d_off_eam, c->d_cnt_eam,
                   c->d_lim_eam, c->d_split_eam, c->d_nbr_ace, c->d_off_ace, c->d_cnt_ace, c->d_csp, c->d_csp_slow, c->d_csp_avg, c->d_lam0, c->d_lam_min,
-                  c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected, c->d_vmin_f,
+                  c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected, c->d_vmin_f, c->d_det1,
                   c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_faccfix, c->d_efast, c->d_eprec,
                   c->d_eatom, c->d_eext, c->d_changeable, c->d_W32, c->d_W64, c->d_ace_list, c->d_ace_nin,
                   c->d_ace_a48, c->d_ace_dA, c->d_ace_e12, c->d_ace_de3, c->d_ace_e3, c->d_ace_dAb, c->d_ace_e12b,

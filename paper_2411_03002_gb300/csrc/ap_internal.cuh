@@ -106,6 +106,7 @@ struct DevScalars {
   int n_csp_slow;     // atoms handed from the FP32 CSP kernel to the exact one
   int ace_row_max;    // longest ACE row of the last ACE row build
   int n_stale_bad;    // atoms whose CSP the rows of an earlier build cannot decide (stale rows)
+  int n_det1;         // detected atoms the lambda spread's second pass visits
   unsigned long long row_total;   // ap_neighbor_total's result
   unsigned int max_disp2_bits;  // float bits of the largest squared displacement
   long long n_precise64;
@@ -240,6 +241,7 @@ struct ap_ctx {
   int* d_scan = nullptr;         // [n + 1] scan output
   int* d_detected = nullptr;     // [n] detected queue
   float* d_vmin_f = nullptr;     // [n] FP32 minima of the lambda spread's first pass
+  int* d_det1 = nullptr;         // [n] detected atoms the spread's second pass visits
   int* d_precise = nullptr;      // [n] internal precise queue
   double* d_lam_int = nullptr;   // [n] internal lambda (ap_step)
 

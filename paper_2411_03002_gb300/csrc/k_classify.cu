@@ -504,7 +504,8 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
     const uint8_t* __restrict__ ch, const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
     const float4* __restrict__ s32, const int4* __restrict__ cunw, const int* __restrict__ cstart,
     const int* __restrict__ catoms, const double* __restrict__ lam0, double r_lo, double r_hi, int mode, int sx,
-    int sy, int sz, double* __restrict__ lam_min, float margin, float* __restrict__ vmin_f) {
+    int sy, int sz, double* __restrict__ lam_min, float margin, float* __restrict__ vmin_f,
+    int* __restrict__ det1, int* __restrict__ n_det1) {
   // per warp: inclusive prefix of candidate counts, first catoms slot, stencil offset
   __shared__ int s_pre[kSpreadWarps][32], s_beg[kSpreadWarps][32], s_t[kSpreadWarps][32], s_img[kSpreadWarps][32];
   __shared__ int4 s_q[kSpreadWarps][64];   // per warp: queued cells (first slot, count, stencil index, image)
@@ -529,6 +530,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
     const double one_minus = __dsub_rn(1.0, lam0[i]);
     const float one_minus_f = (float)one_minus;
     const double v_in = __dsub_rn(1.0, __dmul_rn(one_minus, 1.0));   // the value of a pair inside r_lo
+    bool need = false;   // PHASE 0: a pair outside r_lo that can still go below lambda_min,j
     const int cw[3] = {cell_x(ci.w), cell_y(ci.w), cell_z(ci.w)};
     // the scan of a batch of cells' atom counts and the stream of their candidates
     auto walk = [&](int cnt, int beg, int t, int imgp) {
@@ -582,6 +584,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
             if (vf < __ldcg(&vmin_f[j])) atomicMin((unsigned int*)&vmin_f[j], __float_as_uint(vf));
             continue;
           }
+          need = true;   // the second pass may take this pair's exact value
           if (inside && vf < __ldcg(&vmin_f[j])) atomicMin((unsigned int*)&vmin_f[j], __float_as_uint(vf));
           continue;
         }
@@ -648,6 +651,11 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(
 #else
       walk(cnt, beg, t, imgp);
 #endif
+    }
+    // the second pass visits only the detected atoms with such a pair (lambda_min only
+    // decreases, so a pair screened out here stays out)
+    if constexpr (PHASE == 0) {
+      if (__any_sync(0xffffffffu, need) && lane == 0) det1[atomicAdd(n_det1, 1)] = i;
     }
   }
 }
@@ -732,16 +740,17 @@ void launch_spread(ap_ctx* c, const double* d_x, const uint8_t* d_ch, cudaStream
   const float margin = c->cells_stale ? (float)c->stale_m : 0.f;
   // +3.4e38 in every float: the FP32 minima start above any estimate
   cudaMemsetAsync(c->d_vmin_f, 0x7f, sizeof(float) * (size_t)c->n, s);
+  cudaMemsetAsync(&c->d_sc->n_det1, 0, sizeof(int), s);
   k_spread<0><<<grid, kSpreadWarps * 32, 0, s>>>(c->d_detected, &c->d_sc->n_detected, d_x, d_ch, c->d_sys,
                                                  c->d_atom_sys, c->d_sh32, c->d_cunw, c->d_cell_start,
                                                  c->d_cell_atoms, c->d_lam0, c->cfg.r_lo, c->cfg.r_hi,
                                                  c->cfg.fcut_mode, st[0], st[1], st[2], c->d_lam_min, margin,
-                                                 c->d_vmin_f);
-  k_spread<1><<<grid, kSpreadWarps * 32, 0, s>>>(c->d_detected, &c->d_sc->n_detected, d_x, d_ch, c->d_sys,
+                                                 c->d_vmin_f, c->d_det1, &c->d_sc->n_det1);
+  k_spread<1><<<grid, kSpreadWarps * 32, 0, s>>>(c->d_det1, &c->d_sc->n_det1, d_x, d_ch, c->d_sys,
                                                  c->d_atom_sys, c->d_sh32, c->d_cunw, c->d_cell_start,
                                                  c->d_cell_atoms, c->d_lam0, c->cfg.r_lo, c->cfg.r_hi,
                                                  c->cfg.fcut_mode, st[0], st[1], st[2], c->d_lam_min, margin,
-                                                 c->d_vmin_f);
+                                                 c->d_vmin_f, nullptr, nullptr);
   c->kernels += 2;
 }
 
