@@ -12,7 +12,7 @@ a 0.3 A-disordered hemisphere; the selector never saw it), with the stored model
   paper's Hyb1 zone (4, 12) A, and its RMS force error against full ACE on the
   label-positive atoms is at least 20 % lower.
 The thermalised slab (150 EAM MD steps) is measured too: there a CSP run whose zone is
-re-tuned matches the selector at equal cost (the design doc records the sweep).
+re-tuned matches the selector at equal cost, so no gain is asserted on it.
 """
 import dataclasses
 import os
