@@ -120,11 +120,13 @@ typedef struct {
                                 and takes the CSP from them where they decide it (12
                                 candidates inside r_search - 2 x that displacement; any
                                 atom that fails this makes the update rebuild after
-                                all).  Lambda and the forces equal those of a rebuild
-                                at the update.  Lists are kept only with
+                                all).  The precise queue's ACE rows (ace_rc + skin)
+                                are checked the same way against their own build and
+                                rebuilt alone when needed.  Lambda and the forces equal
+                                those of a rebuild at the update.  Lists are kept only with
                                 AP_DETECT_CSP, without the local thermostat, and when
                                 every periodic dimension of every system holds at least
-                                2 ceil((ace_rc + 2.8 skin)/h) + 1 cells (h the cell
+                                2 ceil((ace_rc + 2 skin)/h) + 1 cells (h the cell
                                 edge) or the offsets are stored; otherwise each update
                                 rebuilds (the per-step check stays). */
   /* Detector behind lambda_0 (Appendix B allows any detector whose f_cut argument
@@ -200,6 +202,7 @@ typedef struct {
   int64_t th_refused;        /* corrections refused for a negative radicand so far */
   double th_energy;          /* sum of the corrected Delta E so far (eV) */
   int64_t kept;              /* lambda updates that kept the lists (AP_REBUILD_SKIN) so far */
+  int64_t ace_rebuilds;      /* ACE row builds between lambda updates (AP_REBUILD_SKIN) so far */
 } ap_step_stats;
 
 /* ----------------------------------------------------------------- lifetime */

@@ -45,7 +45,7 @@ class ApConfig(ctypes.Structure):
 class ApStepStats(ctypes.Structure):
     _fields_ = [("step", I64), ("n_precise", I64), ("n_detected", I64), ("rebuilds", I64), ("e_pot", F64),
                 ("e_kin", F64), ("max_disp", F64), ("error_bits", I32), ("th_corrected", I64), ("th_refused", I64),
-                ("th_energy", F64), ("kept", I64)]
+                ("th_energy", F64), ("kept", I64), ("ace_rebuilds", I64)]
 
 
 class ApError(RuntimeError):

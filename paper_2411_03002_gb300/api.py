@@ -153,6 +153,7 @@ class StepStats:
     th_refused: int = 0
     th_energy: float = 0.0
     kept: int = 0
+    ace_rebuilds: int = 0
 
 
 class Context:
@@ -296,7 +297,7 @@ class Context:
         self._ck(self.lib.ap_step(self.h, n, _ptr(x), _ptr(v), _ptr(f), _ptr(mass), _ptr(fixed), _ptr(lam),
                                   int(nsteps), ctypes.byref(st), _stream(stream)))
         return StepStats(st.step, st.n_precise, st.n_detected, st.rebuilds, st.e_pot, st.e_kin, st.max_disp,
-                         st.error_bits, st.th_corrected, st.th_refused, st.th_energy, st.kept)
+                         st.error_bits, st.th_corrected, st.th_refused, st.th_energy, st.kept, st.ace_rebuilds)
 
     PHASES = ("neighbors", "classify", "eam", "ace", "other", "thermostat", "ace_adjoint", "eam_force", "ace_basis")
 

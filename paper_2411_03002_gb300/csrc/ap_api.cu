@@ -83,10 +83,10 @@ ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box
   int base = 0;
   bool stored = false;
   int spread[3] = {0, 0, 0}, spread_stale[3] = {0, 0, 0};
-  // Lists kept past a lambda update (skin criterion) take ACE rows from cells up to
-  // m = kKeepFrac skin old, reaching ace_rc + skin + 2m: pair cell offsets up to
-  // ceil((ace_rc + skin + 4m)/h).  Without stored offsets they are recovered from the
-  // wrapped cells, which needs 2 offset + 1 cells in every periodic dimension.
+  // With the skin criterion ACE rows (reaching ace_rc + skin) are built from cells up to
+  // m = skin/2 old: pair cell offsets up to ceil((ace_rc + skin + 2m)/h).  Without stored
+  // offsets they are recovered from the wrapped cells, which needs 2 offset + 1 cells in
+  // every periodic dimension.
   bool wide = true;
   for (int s = 0; s < n_sys; ++s) {
     SysInfo& I = sys[s];
@@ -110,7 +110,7 @@ ap_status set_systems(ap_ctx* c, int n_sys, const int64_t* offsets, const ap_box
       int sps = (int)std::ceil((g.r_hi + g.skin) / I.h[d]);   // atoms up to skin/2 from their cells
       if (!I.periodic[d]) sps = std::min(sps, nc);
       spread_stale[d] = std::max(spread_stale[d], sps);
-      const int reach = (int)std::ceil((g.ace_rc + (1.0 + 4.0 * kKeepFrac) * g.skin) / I.h[d]);
+      const int reach = (int)std::ceil((g.ace_rc + 2.0 * g.skin) / I.h[d]);
       if (I.periodic[d] && nc < 2 * reach + 1) wide = false;
     }
     I.cell_base = base;
@@ -237,7 +237,10 @@ ap_status ensure_capacity(ap_ctx* c, int64_t n) {
   CK(dalloc(c->d_vscale, m));
   CK(dalloc(c->d_cnt_eam, m));
   CK(dalloc(c->d_lim_eam, m));
-  if (c->cfg.rebuild_every == AP_REBUILD_SKIN) CK(dalloc(c->d_split_eam, m));
+  if (c->cfg.rebuild_every == AP_REBUILD_SKIN) {
+    CK(dalloc(c->d_split_eam, m));
+    CK(dalloc(c->d_sh32a, m));
+  }
   ap_status st = alloc_rows(c, true, true);
   if (st) return st;
   CK(dalloc(c->d_csp, m));
@@ -321,6 +324,8 @@ void build_async(ap_ctx* c, const double* d_x, const int32_t* d_species, cudaStr
   c->stale_m = 0.0;
   cudaMemcpyAsync(c->d_sh32b, c->d_sh32, sizeof(float4) * (size_t)c->n, cudaMemcpyDeviceToDevice, s);
   cudaMemsetAsync(&c->d_sc->max_disp2_bits, 0, sizeof(unsigned int), s);
+  // the ACE rows' reference shadows belong to the old cells: +3.4e38 until the next ACE build
+  cudaMemsetAsync(&c->d_sc->max_dispa2_bits, 0x7f, sizeof(unsigned int), s);
   c->rebuilds++;
 }
 
@@ -379,6 +384,14 @@ ap_status build_ace_checked(ap_ctx* c, const double* d_x, const int* d_queue, co
     return ensure_ace_records(c, c->h_sc->ace_row_max);
   }
   return AP_OK;
+}
+
+// The precise queue's ACE rows were just built at the current positions: their reference
+// shadows for the displacement check of the skin criterion (no-op otherwise).
+void ace_ref(ap_ctx* c, cudaStream_t s) {
+  if (!c->d_sh32a) return;
+  cudaMemcpyAsync(c->d_sh32a, c->d_sh32, sizeof(float4) * (size_t)c->n, cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(&c->d_sc->max_dispa2_bits, 0, sizeof(unsigned int), s);
 }
 
 // Queue length from the caller's device int64, clamped to [0, n].
@@ -628,7 +641,7 @@ void ap_destroy(ap_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   void* ptrs[] = {c->d_sys, c->d_atom_sys, c->d_cell, c->d_cunw, c->d_cell_start, c->d_cell_count, c->d_cell_atoms,
-                  c->d_slot, c->d_sh32, c->d_sh32c, c->d_sh64, c->d_sh32b, c->d_org, c->d_vscale, c->d_nbr_eam, c->d_off_eam, c->d_cnt_eam,
+                  c->d_slot, c->d_sh32, c->d_sh32c, c->d_sh64, c->d_sh32b, c->d_sh32a, c->d_org, c->d_vscale, c->d_nbr_eam, c->d_off_eam, c->d_cnt_eam,
                   c->d_lim_eam, c->d_split_eam, c->d_nbr_ace, c->d_off_ace, c->d_cnt_ace, c->d_csp, c->d_csp_slow, c->d_csp_avg, c->d_lam0, c->d_lam_min,
                   c->d_lam_avg, c->d_lam_prev, c->d_csp_hist, c->d_lam_hist, c->d_flag, c->d_scan, c->d_detected, c->d_vmin_f, c->d_det1,
                   c->d_precise, c->d_lam_int, c->d_q, c->d_xi, c->d_facc32, c->d_facc64, c->d_faccfix, c->d_efast, c->d_eprec,
@@ -915,6 +928,7 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
     }
     st = build_ace_checked(c, d_x, c->d_precise, &c->d_sc->n_precise, s);
     if (st) return st;
+    ace_ref(c, s);
     CK(cudaMemsetAsync(c->d_eprec, 0, sizeof(double) * (size_t)n, s));
     launch_eam(c, c->d_lam_int, c->d_efast, d_f, false, s);
     launch_ace(c, c->d_lam_int, c->d_precise, c->d_eprec, true, s);
@@ -941,7 +955,7 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
       launch_vv_first(c, d_x, d_v, d_f, d_mass, d_fixed, s);
     }
     const bool lam_step = c->step % g.lambda_every == 0;
-    bool build = false, keep = false;
+    bool build = false, keep = false, ace_only = false;
     double m = 0.0;   // the largest displacement since the last build (skin criterion)
     if (skin_rule) {
       PhaseTimer t(c, s, AP_PHASE_NEIGHBORS);
@@ -949,13 +963,21 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
       if (st) return st;
       st = check_err_bits(c);
       if (st) return st;
-      float d2;
+      float d2, d2a;
       std::memcpy(&d2, &c->h_sc->max_disp2_bits, sizeof(float));
+      std::memcpy(&d2a, &c->h_sc->max_dispa2_bits, sizeof(float));
       // from FP32 shadows (a few 1e-7 A per component): headroom
       m = std::sqrt((double)d2) * (1.0 + 1e-5) + 1e-5;
+      const double ma = std::sqrt((double)d2a) * (1.0 + 1e-5) + 1e-5;   // since the ACE row build
       build = m > 0.5 * g.skin;
       keep = lam_step && !build && keep_ok && m <= kKeepFrac * g.skin;
       build = build || (lam_step && !keep);
+      // the ACE rows reach ace_rc + skin at their build: rebuilt alone when an atom has moved
+      // more than skin/2 since then while the EAM lists still hold (from their cells, m old)
+      if (!build && !lam_step && ma > 0.5 * g.skin) {
+        if (c->stale_ok) ace_only = true;
+        else build = true;
+      }
     } else {
       const int rb = g.rebuild_every > 0 ? g.rebuild_every : g.lambda_every;
       build = lam_step || c->step % rb == 0;
@@ -1013,7 +1035,16 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
         // the new queue's ACE rows, with its storage sized first (synchronises)
         st = build_ace_checked(c, d_x, c->d_precise, &c->d_sc->n_precise, s);
         if (st) return st;
+        ace_ref(c, s);
       }
+    } else if (ace_only) {
+      PhaseTimer t(c, s, AP_PHASE_NEIGHBORS);
+      c->cells_stale = true;   // the atoms moved up to m since the cell build
+      c->stale_m = m;
+      st = build_ace_checked(c, d_x, c->d_precise, &c->d_sc->n_precise, s);
+      if (st) return st;
+      ace_ref(c, s);
+      c->ace_rebuilds++;
     }
     {
       PhaseTimer t(c, s, AP_PHASE_EAM);
@@ -1070,6 +1101,7 @@ ap_status ap_step(ap_ctx* c, int64_t n, double* d_x, double* d_v, double* d_f, c
     h_stats->th_refused = (int64_t)c->h_sc->th_bad;
     h_stats->th_energy = c->h_sc->th_e;
     h_stats->kept = c->kept;
+    h_stats->ace_rebuilds = c->ace_rebuilds;
   }
   return check_err_bits(c);
 }

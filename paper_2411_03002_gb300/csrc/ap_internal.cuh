@@ -109,6 +109,7 @@ struct DevScalars {
   int n_det1;         // detected atoms the lambda spread's second pass visits
   unsigned long long row_total;   // ap_neighbor_total's result
   unsigned int max_disp2_bits;  // float bits of the largest squared displacement
+  unsigned int max_dispa2_bits; // the same since the last ACE row build of the precise queue (skin criterion)
   long long n_precise64;
   double e_total;
   double e_kin;
@@ -198,6 +199,7 @@ struct ap_ctx {
   bool lam_ready = false;        // a classification exists for the current n
   int64_t rebuilds = 0;
   int64_t kept = 0;              // lambda updates that kept the lists (skin criterion)
+  int64_t ace_rebuilds = 0;      // ACE row builds between lambda updates (skin criterion)
 
   // per-atom state (device)
   int* d_cell = nullptr;         // global cell id (wrapped)
@@ -210,6 +212,7 @@ struct ap_ctx {
   float4* d_sh32c = nullptr;     // the same in cell order (the EAM row build's candidate stream)
   double4_32a* d_sh64 = nullptr;     // FP64 cell-relative shadow
   float4* d_sh32b = nullptr;     // [n] the FP32 shadows at the last build (displacement check)
+  float4* d_sh32a = nullptr;     // [n] the FP32 shadows at the last ACE row build (skin criterion only)
   double* d_org = nullptr;       // cell origins lo + c h of every system and dimension (SysInfo::org)
   double* d_vscale = nullptr;    // [n] 0.5 dt ACC / m_i of the current ap_step call
   int* d_nbr_eam = nullptr;      // [n][cap_eam]

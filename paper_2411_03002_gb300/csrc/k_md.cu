@@ -28,9 +28,9 @@ __global__ void k_vv_first(int n, double* __restrict__ x, double* __restrict__ v
                            const SysInfo* __restrict__ sys, const int* __restrict__ atom_sys,
                            const double* __restrict__ org, const int4* __restrict__ cunw, float4* __restrict__ s32,
                            double4_32a* __restrict__ s64,
-                           const float4* __restrict__ s32b, DevScalars* sc) {
+                           const float4* __restrict__ s32b, const float4* __restrict__ s32a, DevScalars* sc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float d2 = 0.f;
+  float d2 = 0.f, d2a = 0.f;   // squared displacement since the build / the ACE row build
   if (i < n) {
     double xx[3];
     const bool mobile = !(fixed && fixed[i]);
@@ -60,11 +60,21 @@ __global__ void k_vv_first(int n, double* __restrict__ x, double* __restrict__ v
       const float4 b = s32b[i];
       const float ex = s4.x - b.x, ey = s4.y - b.y, ez = s4.z - b.z;
       d2 = ex * ex + ey * ey + ez * ez;
+      if (s32a) {
+        const float4 ba = s32a[i];
+        const float ax = s4.x - ba.x, ay = s4.y - ba.y, az = s4.z - ba.z;
+        d2a = ax * ax + ay * ay + az * az;
+      }
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
   if ((threadIdx.x & 31) == 0 && d2 > 0.f) atomicMax(&sc->max_disp2_bits, __float_as_uint(d2));
+  if (s32a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d2a = fmaxf(d2a, __shfl_xor_sync(0xffffffffu, d2a, o));
+    if ((threadIdx.x & 31) == 0 && d2a > 0.f) atomicMax(&sc->max_dispa2_bits, __float_as_uint(d2a));
+  }
 }
 
 __global__ void k_vv_second(int n, double* __restrict__ v, const double* __restrict__ f,
@@ -171,7 +181,7 @@ void launch_vv_first(ap_ctx* c, double* d_x, double* d_v, const double* d_f, con
   k_vv_first<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, d_v, d_f, c->d_vscale, d_fixed, c->cfg.dt, c->d_sys,
                                              c->d_atom_sys, c->d_org, c->d_cunw, c->d_sh32,
                                              c->cfg.precision == AP_PREC_FP64 ? c->d_sh64 : nullptr, c->d_sh32b,
-                                             c->d_sc);
+                                             c->cfg.rebuild_every == AP_REBUILD_SKIN ? c->d_sh32a : nullptr, c->d_sc);
   c->kernels += 1;
 }
 

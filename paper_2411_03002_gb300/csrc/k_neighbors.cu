@@ -596,16 +596,15 @@ void launch_build_eam(ap_ctx* c, const double* d_x, cudaStream_t s) {
 }
 
 void launch_build_ace(ap_ctx* c, const double* d_x, const int* d_queue, const int* d_nq, cudaStream_t s) {
-  double r = c->cfg.ace_rc + c->cfg.skin;
-  // Cells older than the positions (ap_step kept the EAM lists past a lambda update): the
-  // atoms moved up to m = stale_m since the cell build.  The rows then reach 2 m further,
-  // so that they stay complete while no atom moves more than skin/2 from its position at
-  // the cell build (the EAM lists' own condition), and the stencil reaches r + 2 m.
+  const double r = c->cfg.ace_rc + c->cfg.skin;
+  // Cells older than the positions (ap_step kept the EAM lists): the atoms moved up to
+  // m = stale_m since the cell build, so a cell is pruned only beyond r + m and the
+  // stencil reaches r + 2 m.  The rows stay complete while no atom moves more than skin/2
+  // from its position at this build, which ap_step checks after every drift.
   int sten = kStencil;
   float margin = 0.f;
   if (c->cells_stale) {
     margin = (float)c->stale_m;
-    r += 2.0 * c->stale_m;
     for (const SysInfo& S : c->h_sys)
       for (int d = 0; d < 3; ++d) sten = std::max(sten, (int)std::ceil((r + 2.0 * c->stale_m) / S.h[d]));
   }

@@ -17,7 +17,9 @@ rebuilds at each update:
   lambda updates, no skin error, and the trajectory of a run that rebuilds every step;
 * a lone atom 7.5 A above the surface (fewer than 12 atoms within reach): the kept rows
   cannot decide its CSP, so every update rebuilds (no update is kept) and the run
-  equals the default one.
+  equals the default one;
+* the precise queue's ACE rows (ace_rc + skin) are checked against their own build: after
+  an outside neighbour build they are rebuilt alone, and the forces stay the oracle's.
 """
 import dataclasses
 
@@ -164,3 +166,20 @@ def test_lone_atom_sends_every_update_to_a_rebuild():
         assert (a.lam - b.lam).abs().max().item() < 1e-9
         assert image_gap(a.x.cpu().numpy(), b.x.cpu().numpy(), w.box).max() < 1e-9
     assert sa.kept == 0 and sa.rebuilds == sb.rebuilds, (sa.kept, sa.rebuilds, sb.rebuilds)
+
+
+def test_ace_rows_rebuilt_alone_after_an_outside_build():
+    """ap_build_neighbors between ap_step calls builds new cells and EAM rows but not the
+    precise queue's ACE rows: their displacement reference no longer applies, so the next
+    step rebuilds them alone (from the new cells), and the forces stay the oracle's."""
+    w = thermal_slab()
+    a = Run(w, ap.PREC_FP64, ap.REBUILD_SKIN)
+    sa = a.step(15)
+    a.ctx.build_neighbors(a.x, w.box)
+    sb = a.step(3)
+    assert sb.ace_rebuilds >= sa.ace_rebuilds + 1 and sb.error_bits == 0, (sa.ace_rebuilds, sb.ace_rebuilds)
+    fo = oracle_forces(w, a.x.cpu().numpy(), a.lam.cpu().numpy())
+    err = np.linalg.norm(a.f.cpu().numpy() - fo, axis=1)
+    lim = 1e-5 * (np.linalg.norm(fo, axis=1) + 0.01)
+    print(f"ACE rows rebuilt alone: {sb.ace_rebuilds}, max |dF| {err.max() * 1e3:.3g} meV/A")
+    assert np.all(err <= lim), (err / lim).max()
