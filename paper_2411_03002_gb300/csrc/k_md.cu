@@ -11,6 +11,7 @@ namespace {
 constexpr double kAcc = 1.602176634e-19 / 1.66053906660e-27 * 1e-20 / 1e-10;
 constexpr int kRedBlocks = 512;
 constexpr int kRedThreads = 256;
+constexpr int kVvThreads = 256;   // block size of k_vv_first (its block reduction)
 
 // Half-kick factor s_i = 0.5 dt ACC / m_i, once per ap_step call (FP64 division is
 // slow on this GPU; the kicks then need one FMA per component).
@@ -67,13 +68,27 @@ __global__ void k_vv_first(int n, double* __restrict__ x, double* __restrict__ v
       }
     }
   }
+  // block maxima first: one atomic per block and quantity (same-address atomics from every
+  // warp serialise in L2 and cost more than the rest of the kernel)
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
-  if ((threadIdx.x & 31) == 0 && d2 > 0.f) atomicMax(&sc->max_disp2_bits, __float_as_uint(d2));
-  if (s32a) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d2a = fmaxf(d2a, __shfl_xor_sync(0xffffffffu, d2a, o));
-    if ((threadIdx.x & 31) == 0 && d2a > 0.f) atomicMax(&sc->max_dispa2_bits, __float_as_uint(d2a));
+  for (int o = 16; o > 0; o >>= 1) {
+    d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    d2a = fmaxf(d2a, __shfl_xor_sync(0xffffffffu, d2a, o));
+  }
+  __shared__ float red[2][kVvThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = d2;
+    red[1][wid] = d2a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      d2 = fmaxf(d2, red[0][k]);
+      d2a = fmaxf(d2a, red[1][k]);
+    }
+    if (d2 > 0.f) atomicMax(&sc->max_disp2_bits, __float_as_uint(d2));
+    if (s32a && d2a > 0.f) atomicMax(&sc->max_dispa2_bits, __float_as_uint(d2a));
   }
 }
 
@@ -178,7 +193,7 @@ void launch_vscale(ap_ctx* c, const double* d_mass, cudaStream_t s) {
 void launch_vv_first(ap_ctx* c, double* d_x, double* d_v, const double* d_f, const double* d_mass,
                      const uint8_t* d_fixed, cudaStream_t s) {
   (void)d_mass;   // the half-kick factors come from launch_vscale
-  k_vv_first<<<nblk(c->n, 256), 256, 0, s>>>((int)c->n, d_x, d_v, d_f, c->d_vscale, d_fixed, c->cfg.dt, c->d_sys,
+  k_vv_first<<<nblk(c->n, kVvThreads), kVvThreads, 0, s>>>((int)c->n, d_x, d_v, d_f, c->d_vscale, d_fixed, c->cfg.dt, c->d_sys,
                                              c->d_atom_sys, c->d_org, c->d_cunw, c->d_sh32,
                                              c->cfg.precision == AP_PREC_FP64 ? c->d_sh64 : nullptr, c->d_sh32b,
                                              c->cfg.rebuild_every == AP_REBUILD_SKIN ? c->d_sh32a : nullptr, c->d_sc);

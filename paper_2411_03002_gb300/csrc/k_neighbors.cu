@@ -473,7 +473,8 @@ __global__ void __launch_bounds__(256) k_build_ace(const int* __restrict__ queue
                                  off ? off + (size_t)q * cap : nullptr, sten, margin, s_buf[wib]);
     if ((threadIdx.x & 31) == 0) {
       cnt[q] = c < cap ? c : cap;
-      atomicMax(&sc->ace_row_max, c < cap ? c : cap);
+      const int kept_c = c < cap ? c : cap;   // only a new maximum takes the (same-address) atomic
+      if (kept_c > __ldcg(&sc->ace_row_max)) atomicMax(&sc->ace_row_max, kept_c);
       if (c > cap) {
         atomicMax(&sc->need_ace, c);
         atomicOr(&sc->err, kErrCapacity);
