@@ -58,12 +58,12 @@ ACE_FLOP_PER_ATOM = ADJ_FLOP_PER_ATOM + BASIS_FLOP_PER_ATOM + 11400
 # DRAM bytes (read + write) per launch on this workload, from an ncu capture of the
 # current kernels on the 500k-atom case (60,000 precise atoms), scaled to 4,000,000 atoms
 # and 240,000 precise atoms (profiles/dram_traffic_slab50_mixed.md):
-#   k_ace_basis    51.1 MB read + 120.6 MB written (the pair records, 16 B per pair);
-#   k_ace_adjoint  185.7 MB read (mostly the basis kernel's pair records) + 2.2 MB written;
-#   k_eam_force    146.0 MB read + 8.3 MB written.
-ADJ_TRAFFIC_BYTES = 187.9e6 * 240000 / 60000
-BASIS_TRAFFIC_BYTES = 171.8e6 * 240000 / 60000
-EAM_FORCE_TRAFFIC_BYTES = 154.3e6 * 4000000 / 500000
+#   k_ace_basis    45.2 MB read + 120.4 MB written (the pair records, 16 B per pair);
+#   k_ace_adjoint  185.6 MB read (mostly the basis kernel's pair records) + 2.4 MB written;
+#   k_eam_force    146.0 MB read + 8.2 MB written.
+ADJ_TRAFFIC_BYTES = 188.0e6 * 240000 / 60000
+BASIS_TRAFFIC_BYTES = 165.6e6 * 240000 / 60000
+EAM_FORCE_TRAFFIC_BYTES = 154.2e6 * 4000000 / 500000
 # FP32 SIMT peak from unit counts: SMs (read from the device) x 128 FP32 lanes x 2 flop x the
 # maximum SM clock; reported for context beside the measured FFMA peak (ap_probe_peak), which
 # is the denominator of the ALU rooflines.
